@@ -1,0 +1,238 @@
+"""FP64 CPU oracle for the Galerkin ROM advection term (arXiv 2311.03694).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it to check and time the GPU library; the
+library itself never imports, links or calls it, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain loops in FP64); this module only
+compiles it with gcc and marshals numpy arrays.  Functions and the paper
+passage each one follows:
+
+* ``nonlinear_full``      c_i = sum_jk C_ijk u_j u_k          Sec. 2.2, eq. Cu, eq. nse_ode
+* ``nonlinear_cp``        c = A((B^T u) o (C^T u))            Sec. 3.1, eq. tc_ap
+* ``cp_skew_expand``      A1=[U W], A2=[V V], A3=[W -U]       Sec. 3.3, eq. skew_abc_struct
+* ``nonlinear_cp_skew``   eq. tc_ap on the expanded factors
+* ``cp_reconstruct``      Kruskal operator                    Sec. 2.3, eq. cpd
+* ``rom_step``            BDFk/EXTk step with cached Cholesky Sec. 2.2, eq. nse_d1
+* ``cr_als``, ``cr_als_skew``, ``cost_reduction``              Sec. 4, eq. compress_ratio; Sec. 3.1
+
+Index convention: C[i, j, k] with i the test index, j the advecting index
+and k the advected index.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile oracle.c into _oracle.so (gcc -O2, OpenMP over the test index)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Rom(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("form", ctypes.c_int), ("rank", ctypes.c_int64),
+        ("C", ctypes.c_void_p), ("fa", ctypes.c_void_p), ("fb", ctypes.c_void_p),
+        ("fc", ctypes.c_void_p), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+        ("L", ctypes.c_void_p), ("f", ctypes.c_void_p), ("nu", ctypes.c_double),
+        ("dt", ctypes.c_double), ("order", ctypes.c_int),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        i64, vp, dbl = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+        for name, args in {
+            "oracle_nonlinear_full_rows": [i64, i64, i64, vp, vp, vp],
+            "oracle_nonlinear_full": [i64, vp, vp, vp],
+            "oracle_nonlinear_cp": [i64, i64, vp, vp, vp, vp, vp],
+            "oracle_nonlinear_cp_skew": [i64, i64, vp, vp, vp, vp, vp],
+            "oracle_cp_skew_expand": [i64, i64, vp, vp, vp, vp, vp, vp],
+            "oracle_cp_reconstruct": [i64, i64, vp, vp, vp, vp],
+            "oracle_bdf_ext_coefficients": [ctypes.c_int, vp, vp],
+            "oracle_cholesky_solve": [i64, vp, vp, vp],
+            "oracle_set_threads": [ctypes.c_int],
+        }.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = None
+        lib.oracle_cholesky.argtypes = [i64, vp, vp]
+        lib.oracle_cholesky.restype = ctypes.c_int
+        lib.oracle_get_threads.argtypes = []
+        lib.oracle_get_threads.restype = ctypes.c_int
+        lib.oracle_rom_step.argtypes = [ctypes.POINTER(_Rom), vp, i64, vp, vp]
+        lib.oracle_rom_step.restype = ctypes.c_int
+        for name in ("oracle_cr_als", "oracle_cr_als_skew", "oracle_cost_reduction"):
+            fn = getattr(lib, name)
+            fn.argtypes = [i64, i64]
+            fn.restype = dbl
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def set_threads(t):
+    _load().oracle_set_threads(int(t))
+
+
+def get_threads():
+    return _load().oracle_get_threads()
+
+
+def nonlinear_full(C, u):
+    C, u = _f64(C), _f64(u)
+    n = u.shape[-1]
+    assert C.size == n ** 3
+    c = np.empty(n)
+    _load().oracle_nonlinear_full(n, _p(C), _p(u), _p(c))
+    return c
+
+
+def nonlinear_full_rows(C_rows, i0, u):
+    """c_i for the rows i0..i0+len(C_rows)-1, given only those tensor rows."""
+    C_rows, u = _f64(C_rows), _f64(u)
+    n = u.shape[-1]
+    rows = C_rows.size // (n * n)
+    c = np.empty(rows)
+    _load().oracle_nonlinear_full_rows(n, i0, i0 + rows, _p(C_rows), _p(u), _p(c))
+    return c
+
+
+def nonlinear_cp(A, B, Cf, u):
+    A, B, Cf, u = _f64(A), _f64(B), _f64(Cf), _f64(u)
+    n, r = A.shape
+    c = np.empty(n)
+    _load().oracle_nonlinear_cp(n, r, _p(A), _p(B), _p(Cf), _p(u), _p(c))
+    return c
+
+
+def nonlinear_cp_skew(U, V, W, u):
+    U, V, W, u = _f64(U), _f64(V), _f64(W), _f64(u)
+    n, r = U.shape
+    c = np.empty(n)
+    _load().oracle_nonlinear_cp_skew(n, r, _p(U), _p(V), _p(W), _p(u), _p(c))
+    return c
+
+
+def cp_skew_expand(U, V, W):
+    U, V, W = _f64(U), _f64(V), _f64(W)
+    n, r = U.shape
+    A1, A2, A3 = (np.empty((n, 2 * r)) for _ in range(3))
+    _load().oracle_cp_skew_expand(n, r, _p(U), _p(V), _p(W), _p(A1), _p(A2), _p(A3))
+    return A1, A2, A3
+
+
+def cp_reconstruct(A, B, Cf):
+    A, B, Cf = _f64(A), _f64(B), _f64(Cf)
+    n, r = A.shape
+    X = np.empty((n, n, n))
+    _load().oracle_cp_reconstruct(n, r, _p(A), _p(B), _p(Cf), _p(X))
+    return X
+
+
+def bdf_ext_coefficients(k):
+    beta, alpha = np.empty(4), np.empty(3)
+    _load().oracle_bdf_ext_coefficients(int(k), _p(beta), _p(alpha))
+    return beta, alpha
+
+
+def cholesky(H):
+    H = _f64(H)
+    n = H.shape[0]
+    L = np.empty((n, n))
+    if _load().oracle_cholesky(n, _p(H), _p(L)) != 0:
+        raise np.linalg.LinAlgError("matrix is not positive definite")
+    return L
+
+
+def cholesky_solve(L, b):
+    L, b = _f64(L), _f64(b)
+    x = np.empty(L.shape[0])
+    _load().oracle_cholesky_solve(L.shape[0], _p(L), _p(b), _p(x))
+    return x
+
+
+class Rom:
+    """A reduced model for the oracle stepper.
+
+    form: "full" (C is n x n x n), "cp" (factors A, B, Cf, each n x r) or
+    "cp_skew" (blocks U, V, W, each n x r).  A is the stiffness matrix (n x n,
+    or a length-n diagonal), B the mass matrix (None = identity), L an
+    optional explicit linear operator and f an optional constant forcing.
+    """
+
+    FORMS = {"full": 0, "cp": 1, "cp_skew": 2}
+
+    def __init__(self, form, n, A, nu, dt, order=3, C=None, factors=None, B=None, L=None, f=None):
+        self.n = int(n)
+        self._keep = []
+        Ad = _f64(A)
+        if Ad.ndim == 1:
+            Ad = np.diag(Ad)
+        s = _Rom()
+        s.n, s.form, s.nu, s.dt, s.order = self.n, self.FORMS[form], float(nu), float(dt), int(order)
+        s.rank = 0
+        s.A = self._hold(Ad)
+        s.B = self._hold(None if B is None else _f64(B))
+        s.L = self._hold(None if L is None else (np.diag(_f64(L)) if np.ndim(L) == 1 else _f64(L)))
+        s.f = self._hold(None if f is None else _f64(f))
+        s.C = self._hold(None if C is None else _f64(C))
+        if factors is not None:
+            fa, fb, fc = (_f64(x) for x in factors)
+            s.rank = fa.shape[1]
+            s.fa, s.fb, s.fc = self._hold(fa), self._hold(fb), self._hold(fc)
+        self._s = s
+
+    def _hold(self, a):
+        if a is None:
+            return None
+        self._keep.append(a)
+        return a.ctypes.data
+
+    def initial_history(self, u0):
+        h = np.zeros(6 * self.n + 1)
+        h[: self.n] = u0
+        return h
+
+    def step(self, hist, nsteps, want_energy=False, want_invariant=False):
+        """Advance hist (6n+1 doubles, modified in place) by nsteps steps."""
+        assert hist.dtype == np.float64 and hist.size == 6 * self.n + 1 and hist.flags.c_contiguous
+        e = np.empty(nsteps) if want_energy else None
+        inv = np.empty(nsteps) if want_invariant else None
+        rc = _load().oracle_rom_step(ctypes.byref(self._s), _p(hist), int(nsteps), _p(e), _p(inv))
+        if rc != 0:
+            raise np.linalg.LinAlgError("reduced operator is not positive definite")
+        return e, inv
+
+
+def cr_als(n, r):
+    return _load().oracle_cr_als(n, r)
+
+
+def cr_als_skew(n, r):
+    return _load().oracle_cr_als_skew(n, r)
+
+
+def cost_reduction(n, r):
+    return _load().oracle_cost_reduction(n, r)
