@@ -1,0 +1,168 @@
+/*
+ * grom.h — C ABI of the GB300 Galerkin reduced-order-model engine.
+ *
+ * The library evaluates the advection term of a Galerkin ROM and steps the
+ * reduced system with the semi-implicit BDFk/EXTk scheme of arXiv 2311.03694
+ * ("Accelerating Galerkin Reduced-Order Models for Turbulent Flows with
+ * Tensor Decomposition"), on one CUDA GPU (sm_103a).
+ *
+ *   model      B du/dt = -C(u)u - nu A u                       (Sec. 2.2, eq. nse_ode)
+ *   full form  [C(u)u]_i = sum_jk C_ijk u_j u_k                 (Sec. 2.2, eq. Cu; cost 2N^3)
+ *   CP form    [C(u)u]_i = sum_r a_ir (sum_j b_jr u_j)(sum_k c_kr u_k)   (Sec. 3.1, eq. tc_ap)
+ *   skew CP    A1 = [U W], A2 = [V V], A3 = [W -U]              (Sec. 3.3, eq. skew_abc_struct)
+ *   step       (beta0/dt B + nu A) u^{l+1} = -sum_i alpha_i (n^{l+1-i} + L u^{l+1-i} + f)
+ *                                            - B sum_i beta_i/dt u^{l+1-i}   (Sec. 2.2, eq. nse_d1)
+ *
+ * Index convention: a dense tensor is row-major, entry C[(i*n + j)*n + k],
+ * with i the test index, j the advecting index and k the advected index (the
+ * paper writes C_ikj with j and k named the other way round).  CP factors are
+ * n x rank row-major.  Vectors of a batch are batch x n row-major.
+ *
+ * Conventions for every call:
+ *  - Every call returns a grom_status; nothing throws across the ABI.  On an
+ *    error, grom_last_error() returns a message (thread-local, valid until
+ *    the next call on the same thread).
+ *  - Calls that take a stream enqueue work asynchronously on it; errors of
+ *    the enqueued kernels surface at the next synchronising call
+ *    (grom_traj_status, grom_get_state, grom_sync) as GROM_ERR_CUDA.
+ *  - Pointer arguments documented as "host or device" may point to either;
+ *    the library copies from them with cudaMemcpyDefault and never keeps them.
+ *  - Objects are not thread-safe: serialise calls on one object.
+ */
+#ifndef GROM_H
+#define GROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t grom_status;
+#define GROM_OK 0
+#define GROM_ERR_INVALID_ARG 1
+#define GROM_ERR_OOM 2
+#define GROM_ERR_CUDA 3
+#define GROM_ERR_NONFINITE 4
+#define GROM_ERR_TIMEOUT 5
+#define GROM_ERR_BUDGET 6
+#define GROM_ERR_UNSUPPORTED 7
+
+/* Form of the advection operator. */
+#define GROM_FORM_FULL 0    /* dense n^3 tensor (standard G-ROM, eq. Cu)          */
+#define GROM_FORM_CP 1      /* general CP factors fa=A1, fb=A2, fc=A3 (eq. tc_ap)  */
+#define GROM_FORM_CP_SKEW 2 /* skew CP blocks fa=U, fb=V, fc=W (eq. skew_abc_struct):
+                               evaluated as c = U(p o q) - W(p o s) with p = V^T u,
+                               q = W^T u, s = U^T u; paper rank 2*rank            */
+
+/* Storage (and arithmetic) type of the advection operator on the device.
+ * The state update, the reduced solve and the energy/invariant sums are FP64
+ * in every case. */
+#define GROM_F64 0   /* IEEE double; FP64 fused multiply-add                       */
+#define GROM_F32X2 1 /* each double split once into hi = rn(x), lo = rn(x - hi)
+                        (two floats, 8 bytes, 48 significant bits); products and
+                        sums use error-free FP32 transformations on the FP32 pipe */
+#define GROM_F32 2   /* rn(x) to float; FP32 accumulation                          */
+#define GROM_BF16 3  /* rn(x) to bfloat16; FP32 accumulation                       */
+
+typedef struct grom_rom grom_rom;
+typedef struct grom_traj grom_traj;
+
+typedef struct grom_desc {
+  int32_t n;       /* number of modes N >= 1                                       */
+  int32_t form;    /* GROM_FORM_*                                                  */
+  int32_t rank;    /* CP rank (columns of each factor); ignored for FULL          */
+  int32_t storage; /* GROM_F64, GROM_F32X2, GROM_F32, GROM_BF16                     */
+  /* FULL: n*n*n doubles, host or device; NULL together with defer_tensor = 1
+   * to upload the rows later with grom_upload_tensor_slab. */
+  const double* tensor;
+  /* CP forms: three n x rank factor matrices, host or device. */
+  const double* fa;
+  const double* fb;
+  const double* fc;
+  /* Stiffness A: n*n dense (stiffness) or its diagonal (stiffness_diag, n
+   * entries); exactly one must be given.  Host or device. */
+  const double* stiffness;
+  const double* stiffness_diag;
+  /* Mass B: n*n dense, its diagonal (mass_diag), or both NULL for identity. */
+  const double* mass;
+  const double* mass_diag;
+  /* Optional explicit linear operator L (n*n) and constant forcing f (n),
+   * both extrapolated with EXTk (NULL = zero).  In the paper's notation
+   * L = C1 + C2 restricted to modes 1..N and f collects -c0 and nu*a0
+   * (Sec. 2.2, eq. zeroth_contribution). */
+  const double* linear;
+  const double* linear_diag; /* diagonal of L (n entries) instead of `linear`  */
+  const double* forcing;
+  double nu;     /* viscosity 1/Re (> = 0)                                          */
+  double dt;     /* time step (> 0)                                                 */
+  int32_t order; /* BDF/EXT order k in 1..3; steps 1 and 2 use orders 1 and 2       */
+  int32_t defer_tensor; /* FULL only: 1 = rows come from grom_upload_tensor_slab  */
+  int32_t max_batch;    /* largest batch passed to grom_nonlinear/grom_traj_create
+                           (sizes the library's scratch); 0 means 1              */
+  int32_t reserved[4];  /* must be zero                                           */
+} grom_desc;
+
+/* Creates a ROM on the current CUDA device.  Every input is copied; the caller
+ * keeps ownership.  Operators are converted once (round to nearest even) to
+ * the storage type; H_k = beta0_k/dt B + nu A is factored in FP64 and its
+ * inverse cached for k = 1..order.  `stream` (cudaStream_t, may be NULL for
+ * the legacy default stream) is where all later work of this ROM runs.
+ * Errors: INVALID_ARG (bad sizes, pointers or combination), OOM, CUDA,
+ * UNSUPPORTED (n too large for the storage type, see grom_max_n). */
+grom_status grom_create(const grom_desc* desc, void* stream, grom_rom** out);
+
+/* Copies tensor rows i0..i1-1 (rows of n*n doubles, host or device) into a ROM
+ * created with defer_tensor = 1, converting them to the storage type.  All n
+ * rows must be uploaded before the first evaluation. */
+grom_status grom_upload_tensor_slab(grom_rom* rom, int32_t i0, int32_t i1, const double* rows);
+
+/* Frees the ROM.  Waits for its stream; trajectories of the ROM must be
+ * destroyed first. */
+grom_status grom_destroy(grom_rom* rom);
+
+/* Largest n supported for a storage type and form. */
+int32_t grom_max_n(int32_t form, int32_t storage);
+
+/* Evaluates c_b = C(u_b) u_b (positive sign) for b < batch.  u and c are
+ * DEVICE pointers to batch x n FP64 arrays owned by the caller; they must not
+ * overlap.  Asynchronous on the ROM's stream.  batch <= max_batch. */
+grom_status grom_nonlinear(grom_rom* rom, int32_t batch, const double* u, double* c);
+
+/* Creates `batch` trajectories of the ROM starting from u0 (batch x n FP64,
+ * host or device), with no steps taken. */
+grom_status grom_traj_create(grom_rom* rom, int32_t batch, const double* u0, grom_traj** out);
+grom_status grom_traj_destroy(grom_traj* traj);
+
+/* Advances every trajectory by nsteps steps of eq. nse_d1 (orders 1, 2, then
+ * desc.order).  energy and invariant are nullable DEVICE pointers to
+ * nsteps x batch doubles receiving, per step, E = 1/2 u^T B u of the new state
+ * and u^T C(u)u of the state the step started from.  Asynchronous; a
+ * non-finite state is recorded and reported by grom_traj_status. */
+grom_status grom_step(grom_traj* traj, int32_t nsteps, double* energy, double* invariant);
+
+/* Synchronises the ROM's stream and reports GROM_ERR_NONFINITE (first bad
+ * trajectory index in *first_bad, else -1) or GROM_OK. */
+grom_status grom_traj_status(grom_traj* traj, int32_t* first_bad);
+
+/* Checkpoint / resume.  hist is HOST memory of batch x (6n+1) doubles; per
+ * trajectory: u^l, u^{l-1}, u^{l-2}, n^l, n^{l-1}, n^{l-2} (n each) and the
+ * number of steps taken.  n^l is C(u^l)u^l of the newest state.  Get
+ * synchronises; set is ordered on the ROM's stream. */
+grom_status grom_get_state(grom_traj* traj, double* hist);
+grom_status grom_set_state(grom_traj* traj, const double* hist);
+
+/* Waits for all work of the ROM. */
+grom_status grom_sync(grom_rom* rom);
+
+/* Bytes of device memory held by the ROM (operators, caches and scratch). */
+int64_t grom_rom_bytes(const grom_rom* rom);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* grom_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GROM_H */

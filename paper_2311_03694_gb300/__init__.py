@@ -1,0 +1,246 @@
+"""Python binding of libgrom.so, the GB300 Galerkin ROM engine (include/grom.h).
+
+Argument marshalling only: every step of the contraction and of the reduced
+time-stepper runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams; numpy arrays are accepted where the ABI takes host or
+device pointers.  There is no CPU fallback: without the built library every
+call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+GROM_OK = 0
+ERRORS = {
+    1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "TIMEOUT", 6: "BUDGET", 7: "UNSUPPORTED",
+}
+FORMS = {"full": 0, "cp": 1, "cp_skew": 2}
+STORAGE = {"f64": 0, "f32x2": 1, "f32": 2, "bf16": 3}
+STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
+
+
+class GromError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERRORS.get(code, code), msg))
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("form", ctypes.c_int32), ("rank", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("tensor", ctypes.c_void_p), ("fa", ctypes.c_void_p), ("fb", ctypes.c_void_p), ("fc", ctypes.c_void_p),
+        ("stiffness", ctypes.c_void_p), ("stiffness_diag", ctypes.c_void_p),
+        ("mass", ctypes.c_void_p), ("mass_diag", ctypes.c_void_p),
+        ("linear", ctypes.c_void_p), ("linear_diag", ctypes.c_void_p), ("forcing", ctypes.c_void_p),
+        ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("order", ctypes.c_int32),
+        ("defer_tensor", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+    ]
+
+
+_lib = None
+
+EXPORTS = {
+    "grom_create": ([ctypes.POINTER(_Desc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "grom_upload_tensor_slab": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int32),
+    "grom_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "grom_max_n": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "grom_nonlinear": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_traj_create": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                         ctypes.c_int32),
+    "grom_traj_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "grom_step": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_traj_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int32),
+    "grom_get_state": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_set_state": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_sync": ([ctypes.c_void_p], ctypes.c_int32),
+    "grom_rom_bytes": ([ctypes.c_void_p], ctypes.c_int64),
+    "grom_last_error": ([], ctypes.c_char_p),
+}
+
+
+def lib_path():
+    return _build_mod.LIB
+
+
+def build(force=False, verbose=False):
+    """Compile the CUDA library for sm_103a (see build.py)."""
+    return _build_mod.build(force=force, verbose=verbose)
+
+
+def load(path=None):
+    """Load libgrom.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = path or lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libgrom.so is not built (call paper_2311_03694_gb300.build())")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(code):
+    if code != GROM_OK:
+        raise GromError(code, load().grom_last_error().decode())
+
+
+def _ptr(x):
+    """Pointer of a numpy array (host) or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags.c_contiguous, "need a contiguous float64 array"
+        return x.ctypes.data
+    assert str(x.dtype) == "torch.float64" and x.is_contiguous(), "need a contiguous float64 tensor"
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def max_n(form, storage):
+    return load().grom_max_n(FORMS[form], STORAGE[storage])
+
+
+class Rom:
+    """A reduced-order model on the GPU (wraps grom_create / grom_destroy).
+
+    form: "full" (tensor n^3), "cp" (factors A, B, C) or "cp_skew" (U, V, W).
+    storage: "f64", "f32x2", "f32" or "bf16".  stiffness may be a length-n
+    diagonal or an n x n matrix; mass None means identity.
+    """
+
+    def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,
+                 linear=None, forcing=None, nu=1e-2, dt=1e-3, order=3, max_batch=1, defer_tensor=False,
+                 stream=None):
+        lib = load()
+        keep = []
+
+        def arr(x):
+            if x is None:
+                return None
+            if isinstance(x, np.ndarray):
+                x = np.ascontiguousarray(x, dtype=np.float64)
+            keep.append(x)
+            return _ptr(x)
+
+        d = _Desc()
+        d.n, d.form, d.storage = int(n), FORMS[form], STORAGE[storage]
+        d.nu, d.dt, d.order, d.max_batch = float(nu), float(dt), int(order), int(max_batch)
+        d.defer_tensor = 1 if defer_tensor else 0
+        if form == "full":
+            d.tensor = arr(tensor)
+        else:
+            fa, fb, fc = factors
+            d.rank = int(fa.shape[1])
+            d.fa, d.fb, d.fc = arr(fa), arr(fb), arr(fc)
+        if stiffness is None:
+            raise ValueError("stiffness is required")
+        if np.ndim(stiffness) == 1:
+            d.stiffness_diag = arr(stiffness)
+        else:
+            d.stiffness = arr(stiffness)
+        if mass is not None:
+            if np.ndim(mass) == 1:
+                d.mass_diag = arr(mass)
+            else:
+                d.mass = arr(mass)
+        if linear is not None:
+            if np.ndim(linear) == 1:
+                d.linear_diag = arr(linear)
+            else:
+                d.linear = arr(linear)
+        d.forcing = arr(forcing)
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(lib.grom_create(ctypes.byref(d), ctypes.c_void_p(self._stream), ctypes.byref(h)))
+        self._h = h
+        self.n, self.form, self.storage, self.max_batch = int(n), form, storage, int(max_batch)
+        self.rank = int(d.rank)
+        self.order = int(order)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def upload_slab(self, i0, rows):
+        _check(load().grom_upload_tensor_slab(self._h, int(i0), int(i0) + rows.shape[0], _ptr(rows)))
+
+    def nonlinear(self, u, c):
+        """c = C(u)u for device tensors u, c of shape (batch, n), float64."""
+        batch = 1 if u.dim() == 1 else u.shape[0]
+        _check(load().grom_nonlinear(self._h, batch, _ptr(u), _ptr(c)))
+        return c
+
+    def sync(self):
+        _check(load().grom_sync(self._h))
+
+    @property
+    def nbytes(self):
+        return load().grom_rom_bytes(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().grom_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Trajectories:
+    """A batch of trajectories of one Rom (grom_traj_*)."""
+
+    def __init__(self, rom, u0):
+        u0 = np.ascontiguousarray(u0, dtype=np.float64) if isinstance(u0, np.ndarray) else u0
+        self.batch = 1 if u0.ndim == 1 else u0.shape[0]
+        self.rom = rom
+        h = ctypes.c_void_p()
+        _check(load().grom_traj_create(rom.handle, self.batch, _ptr(u0), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, nsteps, energy=None, invariant=None):
+        _check(load().grom_step(self._h, int(nsteps), _ptr(energy), _ptr(invariant)))
+
+    def status(self):
+        bad = ctypes.c_int32(-1)
+        code = load().grom_traj_status(self._h, ctypes.byref(bad))
+        if code not in (GROM_OK, 4):
+            _check(code)
+        return code, bad.value
+
+    def get_state(self):
+        out = np.empty((self.batch, 6 * self.rom.n + 1))
+        _check(load().grom_get_state(self._h, out.ctypes.data))
+        return out
+
+    def set_state(self, hist):
+        hist = np.ascontiguousarray(hist, dtype=np.float64).reshape(self.batch, 6 * self.rom.n + 1)
+        _check(load().grom_set_state(self._h, hist.ctypes.data))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().grom_traj_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

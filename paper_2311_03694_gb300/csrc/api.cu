@@ -1,0 +1,533 @@
+// C ABI of the Galerkin ROM library: object lifetime, uploads, dispatch.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "grom_internal.h"
+
+namespace grom {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+grom_status fail(grom_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+grom_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GROM_ERR_OOM : GROM_ERR_CUDA;
+}
+
+size_t k3_scratch_bytes(const K3Plan& p, int storage);
+cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index, cudaStream_t s);
+
+static const double kBeta0[3] = {1.0, 1.5, 11.0 / 6.0};
+
+// Host FP64 Cholesky of an SPD matrix and explicit inverse (dense path only).
+static bool spd_inverse(int64_t n, std::vector<double>& H, std::vector<double>& Hinv) {
+  std::vector<double> L((size_t)(n * n), 0.0);
+  for (int64_t j = 0; j < n; ++j) {
+    double d = H[j * n + j];
+    for (int64_t m = 0; m < j; ++m) d -= L[j * n + m] * L[j * n + m];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[j * n + j] = ljj;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double s = H[i * n + j];
+      for (int64_t m = 0; m < j; ++m) s -= L[i * n + m] * L[j * n + m];
+      L[i * n + j] = s / ljj;
+    }
+  }
+  Hinv.assign((size_t)(n * n), 0.0);
+  std::vector<double> x((size_t)n);
+  for (int64_t c = 0; c < n; ++c) {  // solve L L^T x = e_c
+    for (int64_t i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int64_t m = 0; m < i; ++m) s -= L[i * n + m] * x[m];
+      x[i] = s / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = x[i];
+      for (int64_t m = i + 1; m < n; ++m) s -= L[m * n + i] * x[m];
+      x[i] = s / L[i * n + i];
+    }
+    for (int64_t i = 0; i < n; ++i) Hinv[i * n + c] = x[i];
+  }
+  return true;
+}
+
+static grom_status fetch(std::vector<double>& dst, const double* src, size_t count) {
+  dst.resize(count);
+  GROM_CUDA_TRY(cudaMemcpy(dst.data(), src, count * sizeof(double), cudaMemcpyDefault));
+  return GROM_OK;
+}
+
+template <typename T>
+static grom_status dmalloc(T** p, size_t bytes, size_t* total) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? GROM_ERR_OOM : GROM_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  if (total) *total += bytes;
+  return GROM_OK;
+}
+
+static grom_status upload(double** dst, const double* src, size_t count, size_t* total, cudaStream_t s) {
+  grom_status st = dmalloc(dst, count * sizeof(double), total);
+  if (st) return st;
+  GROM_CUDA_TRY(cudaMemcpyAsync(*dst, src, count * sizeof(double), cudaMemcpyDefault, s));
+  return GROM_OK;
+}
+
+// Streams FP64 rows (rows of `width` doubles) through a staging buffer and
+// converts them into the storage layout.
+static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int64_t width, int64_t pitch,
+                               uint8_t* dst, int64_t dst_row_bytes) {
+  const int64_t stage_rows_max = std::max<int64_t>(1, (int64_t)(256ll << 20) / (width * 8));
+  double* stage = nullptr;
+  const int64_t srows = std::min(rows, stage_rows_max);
+  grom_status st = dmalloc(&stage, (size_t)(srows * width * 8), nullptr);
+  if (st) return st;
+  for (int64_t r0 = 0; r0 < rows; r0 += srows) {
+    const int64_t cnt = std::min(srows, rows - r0);
+    cudaError_t e = cudaMemcpyAsync(stage, src + r0 * width, (size_t)(cnt * width * 8), cudaMemcpyDefault, r->stream);
+    if (e == cudaSuccess) e = convert_rows_launch(stage, cnt, width, pitch, r->storage, dst + r0 * dst_row_bytes, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) {
+      cudaFree(stage);
+      return cuda_fail(e, "tensor upload");
+    }
+  }
+  cudaFree(stage);
+  return GROM_OK;
+}
+
+static void rom_free(grom_rom* r) {
+  if (!r) return;
+  void* ptrs[] = {r->op, r->hdiag, r->hinv, r->mass, r->mass_diag, r->linear, r->lin_diag, r->forcing, r->part, r->err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete[] r->row_seen;
+  delete r;
+}
+
+static bool full_ready(const grom_rom* r) { return r->form != GROM_FORM_FULL || r->rows_uploaded == r->n; }
+
+static K1Args k1_args(grom_rom* r) {
+  K1Args a{};
+  a.tensor = r->op;
+  a.part = r->part;
+  a.err = r->err;
+  return a;
+}
+
+static K3Args k3_args(grom_rom* r) {
+  K3Args a{};
+  a.fa = r->op;
+  a.fb = r->op + r->panel_bytes;
+  a.fc = r->op + 2 * r->panel_bytes;
+  a.form = r->form;
+  a.part = r->part;
+  return a;
+}
+
+}  // namespace grom
+
+using namespace grom;
+
+extern "C" {
+
+const char* grom_last_error(void) { return g_last_error.c_str(); }
+
+int32_t grom_max_n(int32_t form, int32_t storage) {
+  if (storage_elem_bytes(storage) == 0) return 0;
+  if (form == GROM_FORM_FULL) {
+    // a stored row (np elements) must fit one streaming stage
+    int64_t n = K1_MAX_ROW_BYTES / storage_elem_bytes(storage);
+    return (int32_t)std::min<int64_t>(n, 8192);
+  }
+  return 1 << 16;
+}
+
+grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
+  if (!d || !out) return fail(GROM_ERR_INVALID_ARG, "grom_create: null argument");
+  *out = nullptr;
+  for (int q = 0; q < 4; ++q)
+    if (d->reserved[q]) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
+  if (d->n < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: n must be >= 1");
+  if (d->form < GROM_FORM_FULL || d->form > GROM_FORM_CP_SKEW) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad form");
+  if (storage_elem_bytes(d->storage) == 0) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad storage type");
+  if (d->order < 1 || d->order > 3) return fail(GROM_ERR_INVALID_ARG, "grom_create: order must be 1, 2 or 3");
+  if (!(d->dt > 0.0) || !(d->nu >= 0.0) || !std::isfinite(d->dt) || !std::isfinite(d->nu))
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: need dt > 0 and nu >= 0");
+  if ((d->stiffness == nullptr) == (d->stiffness_diag == nullptr))
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: give exactly one of stiffness, stiffness_diag");
+  if (d->mass && d->mass_diag) return fail(GROM_ERR_INVALID_ARG, "grom_create: give at most one of mass, mass_diag");
+  if (d->linear && d->linear_diag) return fail(GROM_ERR_INVALID_ARG, "grom_create: give at most one of linear, linear_diag");
+  if (d->max_batch < 0) return fail(GROM_ERR_INVALID_ARG, "grom_create: max_batch must be >= 0");
+  if (d->n > grom_max_n(d->form, d->storage))
+    return fail(GROM_ERR_UNSUPPORTED, "grom_create: n exceeds grom_max_n for this form and storage");
+  if (d->form == GROM_FORM_FULL) {
+    if (!d->tensor && !d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: tensor is NULL");
+    if (d->tensor && d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: tensor given with defer_tensor");
+  } else {
+    if (d->rank < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: CP rank must be >= 1");
+    if (!d->fa || !d->fb || !d->fc) return fail(GROM_ERR_INVALID_ARG, "grom_create: CP factors are NULL");
+    if (d->storage == GROM_F32X2) return fail(GROM_ERR_UNSUPPORTED, "grom_create: F32X2 storage is for the full form");
+    if (d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: defer_tensor is for the full form");
+  }
+
+  grom_rom* r = new (std::nothrow) grom_rom();
+  if (!r) return fail(GROM_ERR_OOM, "grom_create: host allocation");
+  r->n = d->n;
+  r->form = d->form;
+  r->rank = d->rank;
+  r->storage = d->storage;
+  r->order = d->order;
+  r->nu = d->nu;
+  r->dt = d->dt;
+  r->max_batch = d->max_batch > 0 ? d->max_batch : 1;
+  r->stream = static_cast<cudaStream_t>(stream);
+  const int64_t n = r->n;
+  grom_status st = GROM_OK;
+  auto bail = [&](grom_status s) {
+    cudaStreamSynchronize(r->stream);
+    rom_free(r);
+    return s;
+  };
+  if (cudaGetDevice(&r->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(GROM_ERR_CUDA, "grom_create: no usable CUDA device"));
+  }
+
+  // ---------------------------------------------------- advection operator
+  if (r->form == GROM_FORM_FULL) {
+    r->np = padded_n(n);
+    r->k1 = k1_plan(n, r->storage, r->sm_count);
+    const size_t row_bytes = (size_t)r->k1.row_bytes;
+    r->op_bytes = (size_t)n * (size_t)n * row_bytes;
+    if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
+    r->part_bytes = (size_t)r->k1.grid * r->k1.maxseg * (K1_CONSUMERS / 32) * r->k1.nb_max * sizeof(double);
+    if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
+    if (d->tensor) {
+      if ((st = upload_rows(r, d->tensor, n * n, n, r->np, r->op, (int64_t)row_bytes))) return bail(st);
+      r->rows_uploaded = n;
+    } else {
+      r->row_seen = new (std::nothrow) uint8_t[(size_t)n]();
+      if (!r->row_seen) return bail(fail(GROM_ERR_OOM, "grom_create: host allocation"));
+    }
+  } else {
+    r->k3 = k3_plan(n, r->rank, r->storage, r->sm_count);
+    const int64_t rp = r->k3.rb;
+    r->panel_bytes = (size_t)n * rp * storage_elem_bytes(r->storage);
+    r->panel_bytes = (r->panel_bytes + 255) / 256 * 256;
+    r->op_bytes = 3 * r->panel_bytes;
+    if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
+    const double* f[3] = {d->fa, d->fb, d->fc};
+    for (int q = 0; q < 3; ++q)
+      if ((st = upload_rows(r, f[q], n, r->rank, rp, r->op + q * r->panel_bytes, rp * storage_elem_bytes(r->storage))))
+        return bail(st);
+    r->part_bytes = k3_scratch_bytes(r->k3, r->storage);
+    if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
+  }
+
+  // ------------------------------------------------------ linear operators
+  std::vector<double> A, Bm, mdiag, adiag;
+  const bool a_dense = d->stiffness != nullptr;
+  const bool b_dense = d->mass != nullptr;
+  if (a_dense) {
+    if ((st = fetch(A, d->stiffness, (size_t)(n * n)))) return bail(st);
+  } else if ((st = fetch(adiag, d->stiffness_diag, (size_t)n))) {
+    return bail(st);
+  }
+  if (b_dense) {
+    if ((st = fetch(Bm, d->mass, (size_t)(n * n)))) return bail(st);
+  } else if (d->mass_diag) {
+    if ((st = fetch(mdiag, d->mass_diag, (size_t)n))) return bail(st);
+  } else {
+    mdiag.assign((size_t)n, 1.0);
+  }
+  r->diagonal = !a_dense && !b_dense && !d->linear;
+  const bool h_diag = !a_dense && !b_dense;
+  if (h_diag) {
+    std::vector<double> hd((size_t)(3 * n));
+    for (int k = 0; k < 3; ++k)
+      for (int64_t i = 0; i < n; ++i) {
+        const double h = kBeta0[k] / r->dt * mdiag[i] + r->nu * adiag[i];
+        if (!(h > 0.0) || !std::isfinite(h)) return bail(fail(GROM_ERR_INVALID_ARG, "grom_create: H_k is not positive"));
+        hd[k * n + i] = 1.0 / h;
+      }
+    if ((st = upload(&r->hdiag, hd.data(), hd.size(), &r->total_bytes, r->stream))) return bail(st);
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "upload"));
+  } else {
+    std::vector<double> H((size_t)(n * n)), Hinv, all((size_t)(3 * n * n));
+    for (int k = 0; k < r->order; ++k) {
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+          const double b = b_dense ? Bm[i * n + j] : (i == j ? mdiag[i] : 0.0);
+          const double a = a_dense ? A[i * n + j] : (i == j ? adiag[i] : 0.0);
+          H[i * n + j] = kBeta0[k] / r->dt * b + r->nu * a;
+        }
+      if (!spd_inverse(n, H, Hinv)) return bail(fail(GROM_ERR_INVALID_ARG, "grom_create: H_k is not SPD"));
+      std::memcpy(all.data() + k * n * n, Hinv.data(), (size_t)(n * n) * sizeof(double));
+    }
+    if ((st = upload(&r->hinv, all.data(), all.size(), &r->total_bytes, r->stream))) return bail(st);
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "upload"));
+  }
+  if (b_dense) {
+    if ((st = upload(&r->mass, Bm.data(), Bm.size(), &r->total_bytes, r->stream))) return bail(st);
+  } else if (d->mass_diag) {
+    if ((st = upload(&r->mass_diag, mdiag.data(), mdiag.size(), &r->total_bytes, r->stream))) return bail(st);
+  }
+  if (d->linear && (st = upload(&r->linear, d->linear, (size_t)(n * n), &r->total_bytes, r->stream))) return bail(st);
+  if (d->linear_diag && (st = upload(&r->lin_diag, d->linear_diag, (size_t)n, &r->total_bytes, r->stream)))
+    return bail(st);
+  if (d->forcing && (st = upload(&r->forcing, d->forcing, (size_t)n, &r->total_bytes, r->stream))) return bail(st);
+  if ((st = dmalloc(&r->err, 2 * sizeof(int), &r->total_bytes))) return bail(st);
+  if (cudaMemsetAsync(r->err, 0, 2 * sizeof(int), r->stream) != cudaSuccess ||
+      cudaStreamSynchronize(r->stream) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+  *out = r;
+  return GROM_OK;
+}
+
+grom_status grom_upload_tensor_slab(grom_rom* r, int32_t i0, int32_t i1, const double* rows) {
+  if (!r || !rows) return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: null argument");
+  if (r->form != GROM_FORM_FULL || !r->row_seen)
+    return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: ROM was not created with defer_tensor");
+  if (i0 < 0 || i1 > r->n || i0 >= i1) return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: bad row range");
+  const int64_t n = r->n;
+  grom_status st = upload_rows(r, rows, (int64_t)(i1 - i0) * n, n, r->np,
+                               r->op + (size_t)i0 * n * (size_t)r->k1.row_bytes, r->k1.row_bytes);
+  if (st) return st;
+  for (int64_t i = i0; i < i1; ++i)
+    if (!r->row_seen[i]) {
+      r->row_seen[i] = 1;
+      ++r->rows_uploaded;
+    }
+  return GROM_OK;
+}
+
+grom_status grom_destroy(grom_rom* r) {
+  if (!r) return GROM_OK;
+  if (r->traj_count > 0) return fail(GROM_ERR_INVALID_ARG, "grom_destroy: trajectories still exist");
+  cudaStreamSynchronize(r->stream);
+  rom_free(r);
+  return GROM_OK;
+}
+
+grom_status grom_sync(grom_rom* r) {
+  if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_sync: null rom");
+  GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  int flags[2] = {0, 0};
+  GROM_CUDA_TRY(cudaMemcpy(flags, r->err, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (flags[0] & DEV_ERR_TIMEOUT) return fail(GROM_ERR_TIMEOUT, "a device-side wait timed out");
+  return GROM_OK;
+}
+
+int64_t grom_rom_bytes(const grom_rom* r) { return r ? (int64_t)r->total_bytes : 0; }
+
+grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* c) {
+  if (!r || !u || !c) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: null argument");
+  if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: batch out of range");
+  if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: tensor rows missing");
+  cudaError_t e;
+  if (r->form == GROM_FORM_FULL) {
+    K1Args a = k1_args(r);
+    a.u = u;
+    a.u_stride = r->n;
+    a.c = c;
+    a.c_stride = r->n;
+    e = k1_launch(r->k1, r->storage, a, batch, r->stream);
+  } else {
+    K3Args a = k3_args(r);
+    a.u = u;
+    a.u_stride = r->n;
+    a.c = c;
+    a.c_stride = r->n;
+    e = k3_launch(r->k3, r->storage, a, batch, r->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear launch");
+  return GROM_OK;
+}
+
+grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_traj** out) {
+  if (!r || !u0 || !out) return fail(GROM_ERR_INVALID_ARG, "grom_traj_create: null argument");
+  *out = nullptr;
+  if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_traj_create: batch out of range");
+  grom_traj* t = new (std::nothrow) grom_traj();
+  if (!t) return fail(GROM_ERR_OOM, "grom_traj_create: host allocation");
+  t->rom = r;
+  t->batch = batch;
+  const int64_t n = r->n;
+  auto bail = [&](grom_status s) {
+    cudaStreamSynchronize(r->stream);
+    if (t->hist) cudaFree(t->hist);
+    if (t->taken) cudaFree(t->taken);
+    if (t->work) cudaFree(t->work);
+    if (t->err) cudaFree(t->err);
+    delete t;
+    return s;
+  };
+  grom_status st;
+  if ((st = dmalloc(&t->hist, (size_t)batch * 6 * n * sizeof(double), nullptr))) return bail(st);
+  if ((st = dmalloc(&t->taken, (size_t)batch * sizeof(int64_t), nullptr))) return bail(st);
+  if ((st = dmalloc(&t->err, 2 * sizeof(int), nullptr))) return bail(st);
+  if (!r->diagonal && (st = dmalloc(&t->work, (size_t)batch * 4 * n * sizeof(double), nullptr))) return bail(st);
+  const int init[2] = {0, INT_MAX};
+  if (cudaMemsetAsync(t->hist, 0, (size_t)batch * 6 * n * sizeof(double), r->stream) != cudaSuccess ||
+      cudaMemsetAsync(t->taken, 0, (size_t)batch * sizeof(int64_t), r->stream) != cudaSuccess ||
+      cudaMemcpyAsync(t->err, init, sizeof(init), cudaMemcpyHostToDevice, r->stream) != cudaSuccess ||
+      cudaMemcpy2DAsync(t->hist, (size_t)6 * n * sizeof(double), u0, (size_t)n * sizeof(double),
+                        (size_t)n * sizeof(double), (size_t)batch, cudaMemcpyDefault, r->stream) != cudaSuccess ||
+      cudaStreamSynchronize(r->stream) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "grom_traj_create"));
+  ++r->traj_count;
+  *out = t;
+  return GROM_OK;
+}
+
+grom_status grom_traj_destroy(grom_traj* t) {
+  if (!t) return GROM_OK;
+  cudaStreamSynchronize(t->rom->stream);
+  cudaFree(t->hist);
+  cudaFree(t->taken);
+  if (t->work) cudaFree(t->work);
+  cudaFree(t->err);
+  --t->rom->traj_count;
+  delete t;
+  return GROM_OK;
+}
+
+static cudaError_t traj_nonlinear(grom_traj* t) {
+  grom_rom* r = t->rom;
+  if (r->form == GROM_FORM_FULL) {
+    K1Args a = k1_args(r);
+    a.hist = t->hist;
+    a.taken = t->taken;
+    a.hist_stride = 6 * (int64_t)r->n;
+    return k1_launch(r->k1, r->storage, a, t->batch, r->stream);
+  }
+  K3Args a = k3_args(r);
+  a.hist = t->hist;
+  a.taken = t->taken;
+  a.hist_stride = 6 * (int64_t)r->n;
+  return k3_launch(r->k3, r->storage, a, t->batch, r->stream);
+}
+
+static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
+  grom_rom* r = t->rom;
+  StepArgs a{};
+  a.n = r->n;
+  a.batch = t->batch;
+  a.order = r->order;
+  a.dt = r->dt;
+  a.nu = r->nu;
+  a.hist = t->hist;
+  a.hist_stride = 6 * (int64_t)r->n;
+  a.taken = t->taken;
+  for (int k = 0; k < 3; ++k) {
+    a.hdiag[k] = r->hdiag ? r->hdiag + k * r->n : nullptr;
+    a.hinv[k] = r->hinv ? r->hinv + (size_t)std::min(k, r->order - 1) * r->n * r->n : nullptr;
+  }
+  a.mass_diag = r->mass_diag;
+  a.lin_diag = r->lin_diag;
+  a.forcing = r->forcing;
+  a.mass = r->mass;
+  a.linear = r->linear;
+  a.work = t->work;
+  a.energy = energy;
+  a.invariant = invariant;
+  a.err = t->err;
+  a.first_bad = t->err + 1;
+  return a;
+}
+
+grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {
+  if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step: null trajectory");
+  if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step: nsteps < 0");
+  grom_rom* r = t->rom;
+  if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
+  StepArgs a = step_args(t, energy, invariant);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    cudaError_t e = traj_nonlinear(t);
+    if (e == cudaSuccess) e = step_launch_indexed(a, r->diagonal, s, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grom_step launch");
+  }
+  return GROM_OK;
+}
+
+grom_status grom_traj_status(grom_traj* t, int32_t* first_bad) {
+  if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_traj_status: null trajectory");
+  grom_status st = grom_sync(t->rom);
+  if (st) return st;
+  int flags[2];
+  GROM_CUDA_TRY(cudaMemcpy(flags, t->err, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (first_bad) *first_bad = (flags[0] & DEV_ERR_NONFINITE) ? flags[1] : -1;
+  if (flags[0] & DEV_ERR_NONFINITE) return fail(GROM_ERR_NONFINITE, "a trajectory state became non-finite");
+  return GROM_OK;
+}
+
+grom_status grom_get_state(grom_traj* t, double* hist) {
+  if (!t || !hist) return fail(GROM_ERR_INVALID_ARG, "grom_get_state: null argument");
+  grom_rom* r = t->rom;
+  if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_get_state: tensor rows missing");
+  const int64_t n = r->n, B = t->batch;
+  // n^l of the newest state, so the export is self-consistent
+  cudaError_t e = traj_nonlinear(t);
+  if (e != cudaSuccess) return cuda_fail(e, "grom_get_state");
+  grom_status st = grom_sync(r);
+  if (st) return st;
+  std::vector<double> ring((size_t)(B * 6 * n));
+  std::vector<int64_t> taken((size_t)B);
+  GROM_CUDA_TRY(cudaMemcpy(ring.data(), t->hist, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  GROM_CUDA_TRY(cudaMemcpy(taken.data(), t->taken, taken.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t l = taken[b];
+    double* dst = hist + b * (6 * n + 1);
+    for (int q = 0; q < 3; ++q) {
+      const int64_t m = ((l - q) % 3 + 3) % 3;
+      std::memcpy(dst + q * n, ring.data() + (b * 6 + m) * n, (size_t)n * sizeof(double));
+      std::memcpy(dst + (3 + q) * n, ring.data() + (b * 6 + 3 + m) * n, (size_t)n * sizeof(double));
+    }
+    dst[6 * n] = (double)l;
+  }
+  return GROM_OK;
+}
+
+grom_status grom_set_state(grom_traj* t, const double* hist) {
+  if (!t || !hist) return fail(GROM_ERR_INVALID_ARG, "grom_set_state: null argument");
+  grom_rom* r = t->rom;
+  const int64_t n = r->n, B = t->batch;
+  std::vector<double> ring((size_t)(B * 6 * n));
+  std::vector<int64_t> taken((size_t)B);
+  for (int64_t b = 0; b < B; ++b) {
+    const double* src = hist + b * (6 * n + 1);
+    const double lf = src[6 * n];
+    if (!(lf >= 0.0) || lf != std::floor(lf) || lf > 9.0e15)
+      return fail(GROM_ERR_INVALID_ARG, "grom_set_state: bad step count");
+    const int64_t l = (int64_t)lf;
+    taken[b] = l;
+    for (int q = 0; q < 3; ++q) {
+      const int64_t m = ((l - q) % 3 + 3) % 3;
+      std::memcpy(ring.data() + (b * 6 + m) * n, src + q * n, (size_t)n * sizeof(double));
+      std::memcpy(ring.data() + (b * 6 + 3 + m) * n, src + (3 + q) * n, (size_t)n * sizeof(double));
+    }
+  }
+  GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  GROM_CUDA_TRY(cudaMemcpy(t->hist, ring.data(), ring.size() * sizeof(double), cudaMemcpyHostToDevice));
+  GROM_CUDA_TRY(cudaMemcpy(t->taken, taken.data(), taken.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return GROM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Internal definitions of the GB300 Galerkin ROM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/grom.h"
+
+namespace grom {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+grom_status fail(grom_status code, const std::string& msg);
+grom_status cuda_fail(cudaError_t e, const char* what);
+
+#define GROM_CUDA_TRY(expr)                                       \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return ::grom::cuda_fail(_e, #expr);   \
+  } while (0)
+
+// Device-side error flags (bit mask in a device int).
+constexpr int DEV_ERR_TIMEOUT = 1;
+constexpr int DEV_ERR_NONFINITE = 2;
+
+// ------------------------------------------------------------- layout
+// The stored tensor pads the advected index k to np = round_up(n, 64) with
+// zeros, so every stored row starts on a 128-byte boundary for every
+// storage type and the streaming kernels never see a ragged row.
+inline int64_t padded_n(int64_t n) { return (n + 63) / 64 * 64; }
+
+inline int storage_elem_bytes(int storage) {
+  switch (storage) {
+    case GROM_F64: return 8;
+    case GROM_F32X2: return 8;
+    case GROM_F32: return 4;
+    case GROM_BF16: return 2;
+  }
+  return 0;
+}
+
+// ----------------------------------------------------------- K1 streaming
+constexpr int K1_CONSUMERS = 256;                 // consumer threads (8 warps)
+constexpr int K1_THREADS = K1_CONSUMERS + 32;     // + one producer warp
+constexpr int K1_STAGES = 6;
+constexpr int K1_STAGE_BYTES = 32768;
+constexpr int K1_MAX_ROW_BYTES = K1_STAGE_BYTES;
+
+struct K1Plan {
+  int64_t n, np;
+  int64_t row_bytes;   // np * element bytes
+  int64_t rpc;         // rows per chunk (all in one test index i)
+  int64_t cpi;         // chunks per test index
+  int64_t T;           // total chunks = n * cpi
+  int grid;            // persistent CTAs
+  int maxseg;          // max test-index segments per CTA
+  int qm;              // vector positions per consumer thread per row (1,2,4,8)
+  int nb_max;          // trajectories per pass
+  size_t smem;         // dynamic shared memory
+};
+
+struct K1Args {
+  const uint8_t* tensor;  // stored tensor (storage layout)
+  const double* u;        // batch x n (FP64), first trajectory of this pass
+  int64_t u_stride;       // doubles between trajectories
+  double* part;           // scratch: grid x maxseg x NB partials
+  double* c;              // batch x n output
+  int64_t c_stride;
+  int nb;                 // active trajectories in this pass (<= NB)
+  int* err;               // device error flags
+  // Optional per-trajectory ring addressing for the stepper: when `taken` is
+  // non-null, the u of trajectory b is hist + b*hist_stride + (taken[b]%3)*n
+  // and c is written to hist + b*hist_stride + (3 + taken[b]%3)*n.
+  double* hist;
+  const int64_t* taken;
+  int64_t hist_stride;
+  const int32_t* active;  // nullable: trajectories with active[b]==0 are skipped
+};
+
+K1Plan k1_plan(int64_t n, int storage, int sm_count);
+cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a, int batch, cudaStream_t s);
+
+// ------------------------------------------------------------- K3 (CP)
+constexpr int K3_THREADS = 256;
+struct K3Plan {
+  int64_t n, r, rb, nblk;  // rank, columns per block, blocks
+  int nb_max;
+  size_t smem;
+};
+struct K3Args {
+  const uint8_t* fa;  // panel layout [nblk][n][rb] per factor
+  const uint8_t* fb;
+  const uint8_t* fc;
+  int form;           // GROM_FORM_CP or GROM_FORM_CP_SKEW
+  const double* u;
+  int64_t u_stride;
+  double* part;       // nblk x NB x n partial outputs
+  double* c;
+  int64_t c_stride;
+  int nb;
+  double* hist;
+  const int64_t* taken;
+  int64_t hist_stride;
+  const int32_t* active;
+};
+K3Plan k3_plan(int64_t n, int64_t r, int storage, int sm_count);
+cudaError_t k3_launch(const K3Plan& plan, int storage, const K3Args& a, int batch, cudaStream_t s);
+
+// --------------------------------------------------------------- stepper
+struct StepArgs {
+  int64_t n;
+  int batch;
+  int order;
+  double dt, nu;
+  double* hist;          // batch x 6 x n ring (u slots 0..2, n slots 3..5)
+  int64_t hist_stride;   // 6 * n
+  int64_t* taken;        // batch
+  const int32_t* active; // nullable
+  // diagonal path
+  const double* hdiag[3];   // 1 / (beta0_k/dt b_i + nu a_i), k = 1..3
+  const double* mass_diag;  // nullable (identity)
+  const double* lin_diag;   // nullable
+  const double* forcing;    // nullable
+  // dense path
+  const double* hinv[3];    // n x n inverses of H_k (nullable when diagonal)
+  const double* mass;       // dense B (nullable)
+  const double* linear;     // dense L (nullable)
+  double* work;             // batch x 4 x n scratch for the dense path
+  // outputs
+  double* energy;           // nullable, (step) x batch
+  double* invariant;        // nullable
+  int* err;                 // device error flags
+  int* first_bad;           // first non-finite trajectory (atomicMin)
+};
+cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s);
+
+// ------------------------------------------------------------ conversion
+cudaError_t convert_rows_launch(const double* src, int64_t rows, int64_t n, int64_t np,
+                                int storage, uint8_t* dst, cudaStream_t s);
+cudaError_t convert_panels_launch(const double* src, int64_t n, int64_t r, int64_t rb,
+                                  int storage, uint8_t* dst, cudaStream_t s);
+
+}  // namespace grom
+
+// ------------------------------------------------------------ ROM objects
+struct grom_rom {
+  int n = 0, form = 0, rank = 0, storage = 0, order = 3, max_batch = 1;
+  int64_t np = 0;
+  double nu = 0, dt = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 0;
+  uint8_t* op = nullptr;  // stored tensor, or three CP factor panel sets
+  size_t op_bytes = 0;
+  size_t panel_bytes = 0;
+  int64_t rows_uploaded = 0;
+  uint8_t* row_seen = nullptr;  // host bitmap of uploaded rows (deferred tensor)
+  bool diagonal = true;
+  double* hdiag = nullptr;      // 3 x n
+  double* hinv = nullptr;       // 3 x n x n (dense path)
+  double* mass = nullptr;       // n x n
+  double* mass_diag = nullptr;  // n
+  double* linear = nullptr;     // n x n
+  double* lin_diag = nullptr;   // n
+  double* forcing = nullptr;    // n
+  double* part = nullptr;       // streaming / CP partials
+  size_t part_bytes = 0;
+  int* err = nullptr;           // device flags [0] = mask, [1] = first bad
+  grom::K1Plan k1{};
+  grom::K3Plan k3{};
+  size_t total_bytes = 0;
+  int traj_count = 0;
+};
+
+struct grom_traj {
+  grom_rom* rom = nullptr;
+  int batch = 0;
+  double* hist = nullptr;   // batch x 6 x n
+  int64_t* taken = nullptr; // batch
+  double* work = nullptr;   // dense-path scratch batch x 4 x n
+  int* err = nullptr;       // [0] mask, [1] first bad trajectory
+};

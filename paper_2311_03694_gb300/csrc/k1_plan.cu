@@ -1,0 +1,88 @@
+// K1 launch planning: chunking, persistent grid, trajectories per pass.
+#include "k1_stream.cuh"
+
+namespace grom {
+
+cudaError_t k1_dispatch_f64(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1_dispatch_f32x2(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1_dispatch_f32(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1_dispatch_bf16(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+
+static int pow2_ceil(int64_t x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static int acc_regs(int storage) {
+  switch (storage) {
+    case GROM_F64: return 4;    // 2 elements x 2 words
+    case GROM_F32X2: return 8;  // 4 elements x (S, s)
+    case GROM_F32: return 4;
+    case GROM_BF16: return 8;
+  }
+  return 64;
+}
+
+static int epv(int storage) {
+  switch (storage) {
+    case GROM_F64: return 2;
+    case GROM_F32X2: return 4;
+    case GROM_F32: return 4;
+    case GROM_BF16: return 8;
+  }
+  return 1;
+}
+
+K1Plan k1_plan(int64_t n, int storage, int sm_count) {
+  K1Plan p{};
+  p.n = n;
+  p.np = padded_n(n);
+  p.row_bytes = p.np * storage_elem_bytes(storage);
+  p.rpc = K1_STAGE_BYTES / p.row_bytes;
+  if (p.rpc < 1) p.rpc = 1;
+  if (p.rpc > n) p.rpc = n;
+  p.cpi = (n + p.rpc - 1) / p.rpc;
+  p.T = n * p.cpi;
+  int64_t grid = sm_count;  // one persistent CTA per SM (the stage ring fills most of shared memory)
+  if (grid > p.T) grid = p.T;
+  if (grid < 1) grid = 1;
+  p.grid = (int)grid;
+  const int64_t per = (p.T + grid - 1) / grid;
+  p.maxseg = (int)((per + p.cpi - 1) / p.cpi + 1);
+  const int64_t P = p.np / epv(storage);
+  p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
+  const int u_bytes_per_traj = (int)(p.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
+  const int base = 1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16;
+  const int budget = 227 * 1024 - base;
+  int nb = 8;
+  while (nb > 1 && (acc_regs(storage) * p.qm * nb > 64 || nb * u_bytes_per_traj > budget)) nb >>= 1;
+  p.nb_max = nb;
+  p.smem = (size_t)base + (size_t)nb * u_bytes_per_traj;
+  return p;
+}
+
+cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a0, int batch, cudaStream_t s) {
+  for (int b0 = 0; b0 < batch; b0 += plan.nb_max) {
+    K1Args a = a0;
+    const int rem = batch - b0;
+    a.nb = rem < plan.nb_max ? rem : plan.nb_max;
+    const int nb = pow2_ceil(a.nb);
+    K1Plan pl = plan;
+    // shared memory for the template width actually launched
+    const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
+    pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
+    cudaError_t e;
+    switch (storage) {
+      case GROM_F64: e = k1_dispatch_f64(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_F32X2: e = k1_dispatch_f32x2(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_F32: e = k1_dispatch_f32(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_BF16: e = k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace grom

@@ -1,0 +1,394 @@
+// K1: single/few-trajectory dense advection contraction, HBM streaming.
+//
+//   c_i = sum_j u_j sum_k C_ijk u_k            (Sec. 2.2, eq. Cu; 2N^3 flops, N^3 words)
+//
+// The stored tensor is a sequence of N^2 rows (i, j) of np elements (k padded
+// with zeros).  A persistent grid splits the rows into chunks of whole rows
+// that never straddle a test index i, and each CTA streams a contiguous range
+// of chunks through a ring of shared-memory stages filled by bulk TMA copies
+// (cp.async.bulk, completion on an mbarrier).  One producer warp issues the
+// copies; eight consumer warps read the stages.
+//
+// The consumers accumulate per advected index: each thread owns fixed
+// positions k of the row and keeps acc_k = sum_j C_ijk u_j over the rows j of
+// the current test index (u_j is a shared-memory broadcast), so no reduction
+// happens per row.  When the test index changes, each thread folds its
+// accumulators into sum_k u_k acc_k and every warp writes one partial per
+// trajectory; a finalize kernel sums the partials of each i in a fixed order
+// (deterministic, no atomics).
+#pragma once
+
+#include "grom_internal.h"
+#include "ptx.cuh"
+
+namespace grom {
+
+template <int ST>
+struct K1Traits;
+template <>
+struct K1Traits<GROM_F64> {
+  static constexpr int EPV = 2;          // elements per 16-byte vector
+  static constexpr int U_BYTES = 8;      // shared-memory bytes of u per element
+  static constexpr int ACC_WORDS = 2;    // 32-bit registers per accumulator
+};
+template <>
+struct K1Traits<GROM_F32X2> {
+  static constexpr int EPV = 4;  // per plane (hi plane, then lo plane, per row)
+  static constexpr int U_BYTES = 8;
+  static constexpr int ACC_WORDS = 2;
+};
+template <>
+struct K1Traits<GROM_F32> {
+  static constexpr int EPV = 4;
+  static constexpr int U_BYTES = 4;
+  static constexpr int ACC_WORDS = 1;
+};
+template <>
+struct K1Traits<GROM_BF16> {
+  static constexpr int EPV = 8;
+  static constexpr int U_BYTES = 4;
+  static constexpr int ACC_WORDS = 1;
+};
+
+// Row layout of the stored tensor: a row of np elements occupies
+// np * elem_bytes bytes.  F32X2 rows are [hi(np floats) | lo(np floats)].
+// Vector positions per row (16-byte vectors, per plane for F32X2):
+template <int ST>
+__host__ __device__ inline int64_t k1_positions(int64_t np) {
+  return np / K1Traits<ST>::EPV;
+}
+
+__device__ __forceinline__ void chunk_decode(int64_t c, int64_t cpi, int64_t rpc, int64_t n, int64_t& i,
+                                             int64_t& j0, int64_t& rows) {
+  i = c / cpi;
+  j0 = (c - i * cpi) * rpc;
+  rows = n - j0 < rpc ? n - j0 : rpc;
+}
+
+// Accumulator types.
+template <int ST>
+struct Acc;
+template <>
+struct Acc<GROM_F64> {
+  double v;
+  __device__ void zero() { v = 0.0; }
+};
+template <>
+struct Acc<GROM_F32X2> {
+  float S, s;
+  __device__ void zero() { S = 0.f; s = 0.f; }
+};
+template <>
+struct Acc<GROM_F32> {
+  float v;
+  __device__ void zero() { v = 0.f; }
+};
+template <>
+struct Acc<GROM_BF16> {
+  float v;
+  __device__ void zero() { v = 0.f; }
+};
+
+// Error-free accumulation of hi*u (double-single arithmetic on the FP32 pipe):
+// p + e = hi*uh exactly (FMA residual), t ~ hi*ul + lo*uh (lo*ul is below
+// 2^-48 relative and dropped), (S, s) += p + (e + t) with Knuth's TwoSum on
+// the leading part.  Intrinsics with explicit rounding keep the compiler from
+// contracting or reassociating the transformation.
+__device__ __forceinline__ void ds_fma(float hi, float lo, float uh, float ul, float& S, float& s) {
+  const float p = __fmul_rn(hi, uh);
+  const float e = __fmaf_rn(hi, uh, -p);
+  const float t = __fmaf_rn(hi, ul, __fmul_rn(lo, uh));
+  const float S1 = __fadd_rn(S, p);
+  const float bb = __fsub_rn(S1, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(S1, bb)), __fsub_rn(p, bb));
+  S = S1;
+  s = __fadd_rn(s, __fadd_rn(err, __fadd_rn(e, t)));
+}
+
+template <int ST, int QM, int NB>
+__global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan pl, const K1Args a, const int b0) {
+  using TR = K1Traits<ST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stages = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + K1_STAGES * K1_STAGE_BYTES);
+  uint64_t* empty = full + K1_STAGES;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + K1_STAGES);
+  uint8_t* ureg = reinterpret_cast<uint8_t*>(empty + K1_STAGES) + 16;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n = pl.n, np = pl.np, row_bytes = pl.row_bytes;
+  const int64_t G = gridDim.x;
+  const int64_t c0 = (int64_t)blockIdx.x * pl.T / G, c1 = ((int64_t)blockIdx.x + 1) * pl.T / G;
+
+  if (tid == 0) {
+    for (int s = 0; s < K1_STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], K1_CONSUMERS / 32);
+    }
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+
+  // u of the NB trajectories of this pass, zero-padded to np, in the
+  // arithmetic type of the storage.
+  for (int64_t idx = tid; idx < (int64_t)NB * np; idx += K1_THREADS) {
+    const int b = (int)(idx / np);
+    const int64_t k = idx - (int64_t)b * np;
+    double v = 0.0;
+    const int bg = b0 + b;
+    if (b < a.nb && k < n && (a.active == nullptr || a.active[bg])) {
+      const double* ub = a.taken ? a.hist + bg * a.hist_stride + (a.taken[bg] % 3) * n : a.u + bg * a.u_stride;
+      v = ub[k];
+    }
+    if constexpr (ST == GROM_F64) {
+      reinterpret_cast<double*>(ureg)[idx] = v;
+    } else if constexpr (ST == GROM_F32X2) {
+      const float h = __double2float_rn(v);
+      reinterpret_cast<float*>(ureg)[idx] = h;
+      reinterpret_cast<float*>(ureg)[(int64_t)NB * np + idx] = __double2float_rn(v - (double)h);
+    } else {
+      reinterpret_cast<float*>(ureg)[idx] = __double2float_rn(v);
+    }
+  }
+  __syncthreads();
+
+  if (warp == K1_CONSUMERS / 32) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int64_t c = c0; c < c1; ++c, ++it) {
+        const int s = (int)(it % K1_STAGES);
+        const uint32_t ph = (uint32_t)((it / K1_STAGES) & 1);
+        if (it >= K1_STAGES && !ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(a.err, DEV_ERR_TIMEOUT);
+          break;
+        }
+        int64_t i, j0, rows;
+        chunk_decode(c, pl.cpi, pl.rpc, n, i, j0, rows);
+        const uint32_t bytes = (uint32_t)(rows * row_bytes);
+        ptx::mbar_arrive_expect_tx(&full[s], bytes);
+        ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * n + j0) * row_bytes, bytes, &full[s]);
+      }
+      // Let every copy this CTA issued land before the CTA can exit.
+      const int64_t issued = it;
+      for (int64_t q = issued > K1_STAGES ? issued - K1_STAGES : 0; q < issued; ++q) {
+        if (!ptx::mbar_wait(&full[q % K1_STAGES], (uint32_t)((q / K1_STAGES) & 1), nullptr))
+          atomicOr(a.err, DEV_ERR_TIMEOUT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int64_t P = k1_positions<ST>(np);
+    int64_t rpr, ro, pos0;
+    bool act;
+    if (P >= K1_CONSUMERS) {
+      rpr = 1; ro = 0; pos0 = tid; act = true;
+    } else {
+      rpr = K1_CONSUMERS / P; ro = tid / P; pos0 = tid % P; act = ro < rpr;
+    }
+    Acc<ST> acc[QM][TR::EPV][NB];
+#pragma unroll
+    for (int q = 0; q < QM; ++q)
+#pragma unroll
+      for (int e = 0; e < TR::EPV; ++e)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[q][e][b].zero();
+
+    const int64_t first_i = c0 / pl.cpi;
+    int64_t cur_i = -1;
+
+    auto flush = [&](int64_t i_seg) {
+      double contrib[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) contrib[b] = 0.0;
+      if (act) {
+#pragma unroll
+        for (int q = 0; q < QM; ++q) {
+          const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
+          if (pos < P) {
+#pragma unroll
+            for (int e = 0; e < TR::EPV; ++e) {
+              const int64_t k = pos * TR::EPV + e;
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                if constexpr (ST == GROM_F64) {
+                  contrib[b] = fma(reinterpret_cast<const double*>(ureg)[b * np + k], acc[q][e][b].v, contrib[b]);
+                } else if constexpr (ST == GROM_F32X2) {
+                  const double uk = (double)reinterpret_cast<const float*>(ureg)[b * np + k] +
+                                    (double)reinterpret_cast<const float*>(ureg)[(int64_t)NB * np + b * np + k];
+                  contrib[b] = fma(uk, (double)acc[q][e][b].S + (double)acc[q][e][b].s, contrib[b]);
+                } else {
+                  contrib[b] = fma((double)reinterpret_cast<const float*>(ureg)[b * np + k], (double)acc[q][e][b].v,
+                                   contrib[b]);
+                }
+                acc[q][e][b].zero();
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        double v = contrib[b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        contrib[b] = v;
+      }
+      if (lane == 0) {
+        const int64_t seg = i_seg - first_i;
+        double* dst = a.part + (((int64_t)blockIdx.x * pl.maxseg + seg) * (K1_CONSUMERS / 32) + warp) * NB;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) dst[b] = contrib[b];
+      }
+    };
+
+    int64_t it = 0;
+    for (int64_t c = c0; c < c1; ++c, ++it) {
+      int64_t i, j0, rows;
+      chunk_decode(c, pl.cpi, pl.rpc, n, i, j0, rows);
+      if (i != cur_i) {
+        if (cur_i >= 0) flush(cur_i);
+        cur_i = i;
+      }
+      const int s = (int)(it % K1_STAGES);
+      const uint32_t ph = (uint32_t)((it / K1_STAGES) & 1);
+      if (!ptx::mbar_wait(&full[s], ph, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(a.err, DEV_ERR_TIMEOUT);
+        break;
+      }
+      const uint8_t* st = stages + (size_t)s * K1_STAGE_BYTES;
+      if (act) {
+        for (int64_t rr = ro; rr < rows; rr += rpr) {
+          const int64_t j = j0 + rr;
+          const uint8_t* rowp = st + rr * row_bytes;
+          if constexpr (ST == GROM_F64) {
+            double uj[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(ureg)[b * np + j];
+#pragma unroll
+            for (int q = 0; q < QM; ++q) {
+              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
+              if (pos < P) {
+                const double2 x = *reinterpret_cast<const double2*>(rowp + pos * 16);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                  acc[q][0][b].v = fma(x.x, uj[b], acc[q][0][b].v);
+                  acc[q][1][b].v = fma(x.y, uj[b], acc[q][1][b].v);
+                }
+              }
+            }
+          } else if constexpr (ST == GROM_F32X2) {
+            float uh[NB], ul[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              uh[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
+              ul[b] = reinterpret_cast<const float*>(ureg)[(int64_t)NB * np + b * np + j];
+            }
+#pragma unroll
+            for (int q = 0; q < QM; ++q) {
+              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
+              if (pos < P) {
+                const float4 h = *reinterpret_cast<const float4*>(rowp + pos * 16);
+                const float4 l = *reinterpret_cast<const float4*>(rowp + np * 4 + pos * 16);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                  ds_fma(h.x, l.x, uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
+                  ds_fma(h.y, l.y, uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
+                  ds_fma(h.z, l.z, uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
+                  ds_fma(h.w, l.w, uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
+                }
+              }
+            }
+          } else if constexpr (ST == GROM_F32) {
+            float uj[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
+#pragma unroll
+            for (int q = 0; q < QM; ++q) {
+              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
+              if (pos < P) {
+                const float4 x = *reinterpret_cast<const float4*>(rowp + pos * 16);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                  acc[q][0][b].v = fmaf(x.x, uj[b], acc[q][0][b].v);
+                  acc[q][1][b].v = fmaf(x.y, uj[b], acc[q][1][b].v);
+                  acc[q][2][b].v = fmaf(x.z, uj[b], acc[q][2][b].v);
+                  acc[q][3][b].v = fmaf(x.w, uj[b], acc[q][3][b].v);
+                }
+              }
+            }
+          } else {  // BF16
+            float uj[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
+#pragma unroll
+            for (int q = 0; q < QM; ++q) {
+              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
+              if (pos < P) {
+                const uint4 w = *reinterpret_cast<const uint4*>(rowp + pos * 16);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                  const float x0 = __uint_as_float(ws[h] << 16);
+                  const float x1 = __uint_as_float(ws[h] & 0xffff0000u);
+#pragma unroll
+                  for (int b = 0; b < NB; ++b) {
+                    acc[q][2 * h][b].v = fmaf(x0, uj[b], acc[q][2 * h][b].v);
+                    acc[q][2 * h + 1][b].v = fmaf(x1, uj[b], acc[q][2 * h + 1][b].v);
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[s]);
+    }
+    if (cur_i >= 0 && !*abort_flag) flush(cur_i);
+  }
+  __syncthreads();
+}
+
+// Sums the per-warp partials of every test index in CTA order.
+template <int NB>
+__global__ void k1_finalize_kernel(const K1Plan pl, const K1Args a, const int b0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = pl.n;
+  if (idx >= n * a.nb) return;
+  const int b = (int)(idx / n);
+  const int64_t i = idx - (int64_t)b * n;
+  const int bg = b0 + b;
+  if (a.active && !a.active[bg]) return;
+  const int64_t G = pl.grid, T = pl.T;
+  // CTA that owns chunk c: the largest g with floor(g*T/G) <= c.
+  auto owner = [&](int64_t c) { return ((c + 1) * G - 1) / T; };
+  const int64_t g_lo = owner(i * pl.cpi), g_hi = owner((i + 1) * pl.cpi - 1);
+  double s = 0.0;
+  for (int64_t g = g_lo; g <= g_hi; ++g) {
+    const int64_t first_i = (g * T / G) / pl.cpi;
+    const double* src = a.part + ((g * pl.maxseg + (i - first_i)) * (K1_CONSUMERS / 32)) * NB + b;
+#pragma unroll
+    for (int w = 0; w < K1_CONSUMERS / 32; ++w) s += src[w * NB];
+  }
+  double* dst = a.taken ? a.hist + bg * a.hist_stride + (3 + a.taken[bg] % 3) * n : a.c + bg * a.c_stride;
+  dst[i] = s;
+}
+
+template <int ST, int QM, int NB>
+cudaError_t k1_launch_one(const K1Plan& pl, const K1Args& a, int b0, cudaStream_t s) {
+  auto kern = k1_stream_kernel<ST, QM, NB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<pl.grid, K1_THREADS, pl.smem, s>>>(pl, a, b0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t total = pl.n * a.nb;
+  k1_finalize_kernel<NB><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pl, a, b0);
+  return cudaGetLastError();
+}
+
+}  // namespace grom

@@ -1,0 +1,249 @@
+// K4-K6: the BDFk/EXTk reduced step (Sec. 2.2, eq. nse_d1), FP64.
+//
+// History ring per trajectory (6 slots of n doubles): u^{m} lives in slot
+// m mod 3 and n^{m} = C(u^m)u^m in slot 3 + m mod 3, where m counts steps
+// taken.  A step at l = taken uses order k = min(l + 1, order):
+//   rhs = -sum_{q<k} alpha_q (n^{l-q} + L u^{l-q} + f) - B sum_{q<k} beta_{q+1}/dt u^{l-q}
+//   u^{l+1} = H_k^{-1} rhs,  H_k = beta0_k/dt B + nu A
+// and writes u^{l+1} over u^{l-2} (slot (l+1) mod 3).  It also returns the
+// energy 1/2 u^T B u of the new state, the invariant u^T n of the old state
+// and flags non-finite states.
+#include "grom_internal.h"
+
+namespace grom {
+
+__constant__ double c_beta[3][4] = {
+    {1.0, -1.0, 0.0, 0.0},
+    {1.5, -2.0, 0.5, 0.0},
+    {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0},
+};
+__constant__ double c_alpha[3][3] = {
+    {1.0, 0.0, 0.0},
+    {2.0, -1.0, 0.0},
+    {3.0, -3.0, 1.0},
+};
+
+constexpr int STEP_THREADS = 256;
+
+// Deterministic block sum of two values (fixed tree), result in thread 0.
+__device__ __forceinline__ void block_sum2(double& x, double& y, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, off);
+    y += __shfl_down_sync(0xffffffffu, y, off);
+  }
+  if (lane == 0) {
+    sh[warp] = x;
+    sh[32 + warp] = y;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    x = lane < nw ? sh[lane] : 0.0;
+    y = lane < nw ? sh[32 + lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, off);
+      y += __shfl_down_sync(0xffffffffu, y, off);
+    }
+  }
+}
+
+__device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
+  atomicOr(a.err, DEV_ERR_NONFINITE);
+  atomicMin(a.first_bad, b);
+}
+
+// Fused step for diagonal A, B (or identity) and L: one CTA per trajectory.
+__global__ void __launch_bounds__(STEP_THREADS) k_step_diag(const StepArgs a, const int step_index) {
+  __shared__ double sh[64];
+  __shared__ int bad;
+  const int b = blockIdx.x;
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  double* h = a.hist + b * a.hist_stride;
+  const double* u_old[3];
+  const double* n_old[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int64_t m = ((l - q) % 3 + 3) % 3;
+    u_old[q] = h + m * n;
+    n_old[q] = h + (3 + m) * n;
+  }
+  double* u_new = h + ((l + 1) % 3) * n;
+  const double* hd = a.hdiag[k - 1];
+  const double inv_dt = 1.0 / a.dt;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  double e_part = 0.0, i_part = 0.0;
+  int my_bad = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double mb = a.mass_diag ? a.mass_diag[i] : 1.0;
+    const double ld = a.lin_diag ? a.lin_diag[i] : 0.0;
+    const double f = a.forcing ? a.forcing[i] : 0.0;
+    double ext = 0.0, bdf = 0.0;
+    double uq[3];
+    for (int q = 0; q < k; ++q) {
+      uq[q] = u_old[q][i];
+      ext += c_alpha[k - 1][q] * (n_old[q][i] + ld * uq[q] + f);
+      bdf += c_beta[k - 1][q + 1] * inv_dt * uq[q];
+    }
+    const double rhs = -ext - mb * bdf;
+    const double un = rhs * hd[i];
+    i_part += uq[0] * n_old[0][i];
+    e_part += mb * un * un;
+    if (!isfinite(un)) my_bad = 1;
+    u_new[i] = un;
+  }
+  if (my_bad) bad = 1;
+  block_sum2(e_part, i_part, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e_part;
+    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = i_part;
+    if (bad) report_nonfinite(a, b);
+    a.taken[b] = l + 1;
+  }
+}
+
+// ------------------------------------------------------------ dense path
+// work layout per trajectory: [y | t | z | v] (n each)
+
+__global__ void k_step_prep(const StepArgs a) {
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  const double* h = a.hist + b * a.hist_stride;
+  double* w = a.work + (int64_t)b * 4 * n;
+  double y = 0.0, t = 0.0, z = 0.0;
+  const double f = a.forcing ? a.forcing[i] : 0.0;
+  for (int q = 0; q < k; ++q) {
+    const int64_t m = ((l - q) % 3 + 3) % 3;
+    const double uq = h[m * n + i];
+    y -= c_alpha[k - 1][q] * (h[(3 + m) * n + i] + f);
+    t += c_beta[k - 1][q + 1] / a.dt * uq;
+    z += c_alpha[k - 1][q] * uq;
+  }
+  if (!a.mass) y -= (a.mass_diag ? a.mass_diag[i] : 1.0) * t;
+  if (!a.linear && a.lin_diag) y -= a.lin_diag[i] * z;
+  w[i] = y;
+  w[n + i] = t;
+  w[2 * n + i] = z;
+}
+
+// out[b] (+)= sign * M x[b]; one warp per row.  mode: 0 = L z -> y, 1 = B t -> y,
+// 2 = H_k^{-1} y -> v, 3 = B v -> t (for the energy).
+__global__ void k_step_gemv(const StepArgs a, const int mode) {
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= n) return;
+  double* w = a.work + (int64_t)b * 4 * n;
+  const double* M;
+  const double* x;
+  if (mode == 0) {
+    M = a.linear; x = w + 2 * n;
+  } else if (mode == 1) {
+    M = a.mass; x = w + n;
+  } else if (mode == 2) {
+    const int64_t l = a.taken[b];
+    const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+    M = a.hinv[k - 1]; x = w;
+  } else {
+    M = a.mass; x = w + 3 * n;
+  }
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s = fma(M[i * n + j], x[j], s);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    if (mode == 0 || mode == 1) w[i] -= s;        // y -= L z, y -= B t
+    else if (mode == 2) w[3 * n + i] = s;         // v = H^-1 y
+    else w[n + i] = s;                            // t = B v
+  }
+}
+
+__global__ void __launch_bounds__(STEP_THREADS) k_step_finish(const StepArgs a, const int step_index, const int use_hdiag) {
+  __shared__ double sh[64];
+  __shared__ int bad;
+  const int b = blockIdx.x;
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  double* h = a.hist + b * a.hist_stride;
+  double* w = a.work + (int64_t)b * 4 * n;
+  const int64_t m0 = l % 3;
+  double* u_new = h + ((l + 1) % 3) * n;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  double e_part = 0.0, i_part = 0.0;
+  int my_bad = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double un = use_hdiag ? w[i] * a.hdiag[k - 1][i] : w[3 * n + i];
+    i_part += h[m0 * n + i] * h[(3 + m0) * n + i];
+    const double bu = a.mass ? w[n + i] : (a.mass_diag ? a.mass_diag[i] : 1.0) * un;
+    e_part += un * bu;
+    if (!isfinite(un)) my_bad = 1;
+    u_new[i] = un;
+  }
+  if (my_bad) bad = 1;
+  block_sum2(e_part, i_part, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e_part;
+    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = i_part;
+    if (bad) report_nonfinite(a, b);
+    a.taken[b] = l + 1;
+  }
+}
+
+// v = hdiag_k * y for the energy pass when H is diagonal but B is dense.
+__global__ void k_step_hdiag(const StepArgs a) {
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  double* w = a.work + (int64_t)b * 4 * n;
+  w[3 * n + i] = w[i] * a.hdiag[k - 1][i];
+}
+
+cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index, cudaStream_t s) {
+  if (diagonal) {
+    k_step_diag<<<a.batch, STEP_THREADS, 0, s>>>(a, step_index);
+    return cudaGetLastError();
+  }
+  const int64_t n = a.n;
+  dim3 ge((unsigned)((n + 255) / 256), (unsigned)a.batch);
+  dim3 gw((unsigned)((n + 7) / 8), (unsigned)a.batch);
+  k_step_prep<<<ge, 256, 0, s>>>(a);
+  if (a.linear) k_step_gemv<<<gw, 256, 0, s>>>(a, 0);
+  if (a.mass) k_step_gemv<<<gw, 256, 0, s>>>(a, 1);
+  const bool hdense = a.hinv[0] != nullptr;
+  if (hdense) {
+    k_step_gemv<<<gw, 256, 0, s>>>(a, 2);
+  } else if (a.mass) {
+    k_step_hdiag<<<ge, 256, 0, s>>>(a);
+  }
+  if (a.mass) k_step_gemv<<<gw, 256, 0, s>>>(a, 3);
+  k_step_finish<<<a.batch, STEP_THREADS, 0, s>>>(a, step_index, (hdense || a.mass) ? 0 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s) {
+  return step_launch_indexed(a, diagonal, 0, s);
+}
+
+}  // namespace grom
