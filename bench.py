@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the Galerkin ROM hot path on GB300.
+
+Workload (seeded, synthetic; stands in for the paper's 2D/3D LDC and MFU
+operators, which are not available): N = 1024 modes, the CP-structured skew
+advection tensor C_ijk = sum_r V_jr (U_ir W_kr - W_ir U_kr) + skew residual at
+1e-3 relative norm with R = N, A = diag((i/N)^2), B = I, nu = 1e-2,
+dt = 1e-3, initial state u_i ~ N(0,1)/i.
+
+One bench step is one BDF3/EXT3 step (advection term, extrapolation, cached
+reduced solve, energy/invariant, history rotation) of one trajectory of the
+headline model: the full G-ROM with the tensor stored in BF16, FP32
+accumulation and FP64 state update.  The same step is also timed for the
+other storage types and for the CPD-ROM (skew CP factors, rank N) and
+reported under "variants"; each result carries its error against the FP64
+oracle.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With --impl reference the FP64 CPU oracle is timed on the host cores for the
+same metric and workload.  Under torchrun every rank runs an independent
+replica (the path shards by trajectory and needs no collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ROM steps/s at N=1024 (full vs CPD, FP64 vs BF16), HBM/TC roofline %, p99 latency"
+UNIT = "steps/s"
+NU, DT = 1e-2, 1e-3
+HEADLINE = ("full", "bf16")
+VARIANTS = [("full", "bf16"), ("full", "f32"), ("full", "f32x2"), ("full", "f64"), ("cp_skew", "bf16"),
+            ("cp_skew", "f32"), ("cp_skew", "f64")]
+TOL = {"f64": 1e-12, "f32x2": 1e-12, "f32": 1e-5, "bf16": 2e-2}
+STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="grom", choices=["grom", "reference"])
+    p.add_argument("--n", type=int, default=1024)
+    p.add_argument("--rank", type=int, default=0, help="CP rank (default N)")
+    p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64,cp_skew:bf16")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--json-out", default="")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        busy = [r for r in rows if (num(r[8]) or 0) > 0] or rows
+        sm = [num(r[0]) for r in busy if num(r[0]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in busy:
+            for name, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][1]),
+                "samples": len(busy), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- workload
+def workload(n, rank, seed, device):
+    """FP64 tensor (device), skew CP factors, stiffness and initial state."""
+    import synth
+
+    U, V, W, s, _ = synth.cp_workload(n, rank, 2)
+    C = synth.cp_tensor_device(U, V, W, seed, s, device)
+    a = synth.diag_stiffness(n)
+    return C, (U, V, W), a
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def kernel_traffic(kernel_key):
+    """dram bytes per launch of a kernel from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh).get(kernel_key)
+    if not d:
+        return None
+    h = hashlib.sha256()
+    for f in d["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return d["bytes_per_launch"] if h.hexdigest() == d["source_sha256"] else None
+
+
+# ------------------------------------------------------------------ timing
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def time_variant(grom, torch, rom, u0, steps, warmup, flush=None):
+    """ms per step of grom_step(1) timed with CUDA events on the ROM's stream."""
+    tr = grom.Trajectories(rom, u0)
+    stream = torch.cuda.current_stream()
+    tr.step(warmup)
+    torch.cuda.synchronize()
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        per = None
+    else:
+        per = []
+        for _ in range(steps):
+            flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tr.step(1)
+            e1.record(stream)
+            per.append((e0, e1))
+        torch.cuda.synchronize()
+        per = [a.elapsed_time(b) for a, b in per]
+        ms = float(np.mean(per))
+    code, _ = tr.status()
+    tr.close()
+    return ms, code, per
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args):
+    import oracle
+    import synth
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    n = args.n
+    rank = args.rank or n
+    dev = "cuda" if _cuda_ok() else "cpu"
+    if dev == "cuda":
+        C, _, a = workload(n, rank, synth.seed_for(2), dev)
+        Ch = C.cpu().numpy()
+        del C
+    else:
+        U, V, W, s, seed = synth.cp_workload(n, rank, 2)
+        Ch = synth.cp_tensor(U, V, W, seed, s)
+        a = synth.diag_stiffness(n)
+    u0 = synth.initial_condition(n, synth.seed_for(2))[0]
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    rom = oracle.Rom("full", n, a, NU, DT, C=Ch)
+    h = rom.initial_history(u0)
+    t0 = time.perf_counter()
+    rom.step(h, max(1, args.warmup))
+    t_w = (time.perf_counter() - t0) / max(1, args.warmup)
+    steps = args.steps
+    budget = 150.0
+    if steps * t_w > budget:
+        steps = max(3, int(budget / t_w))
+    t0 = time.perf_counter()
+    rom.step(h, steps)
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    sample = "%d BDF3/EXT3 steps of the N=%d FP64 full G-ROM (of %d requested)" % (steps, n, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(n, rank),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def _cuda_ok():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def _config(n, rank):
+    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage, FP32 accumulation, FP64 state; "
+                        "CP-structured skew tensor (R=%d) + 1e-3 skew residual; one trajectory per GPU" % (n, rank),
+            "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT,
+            "l2": "inputs larger than L2 (full tensor %.2f GB per step)" % (n ** 3 * 2 / 1e9)}
+
+
+# -------------------------------------------------------------------- main
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import oracle
+    import synth
+    import paper_2311_03694_gb300 as grom
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank_id = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    grom.build()
+    n = args.n
+    R = args.rank or n
+    seed = synth.seed_for(2)
+    C, factors, a = workload(n, R, seed, "cuda")
+    u0 = synth.initial_condition(n, seed, traj=rank_id)  # one trajectory per replica
+    hbm_peak, tc_peak, peak_kind = peaks()
+
+    def make_rom(form, storage):
+        if form == "full":
+            return grom.Rom(n, "full", storage, tensor=C, stiffness=a, nu=NU, dt=DT)
+        return grom.Rom(n, form, storage, factors=factors, stiffness=a, nu=NU, dt=DT)
+
+    # ---------------------------------------------------- headline, timed
+    rom = make_rom(*HEADLINE)
+    tr = grom.Trajectories(rom, u0)
+    stream = torch.cuda.current_stream()
+    tr.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    rom.profile(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    k1_ms, k1_launches = rom.profile_read()
+    rom.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    code, bad = tr.status()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1e3 / ms  # all replicas' steps per second
+
+    # roofline of the dominant kernel (K1 streaming contraction)
+    k1_avg_ms = k1_ms / max(1, k1_launches)
+    alg_bytes = float(n) ** 3 * STORAGE_BYTES[HEADLINE[1]]
+    achieved = alg_bytes / (k1_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": kernel_traffic("k1_stream_bf16_n%d" % n),
+                "kernel": "k1_stream_kernel<BF16> (+finalize excluded)", "peak_kind": peak_kind,
+                "kernel_ms": k1_avg_ms, "kernel_launches": k1_launches,
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # ------------------------------------------------------------- e2e
+    pin_in = torch.empty((1, n), dtype=torch.float64).pin_memory()
+    tr.step_host(0, None, pin_in.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2 = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+    e2[0].record(stream)
+    for _ in range(args.steps):
+        tr.step_host(1, pin_in, pin_in)  # state in from pinned host memory, new state back out
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    e2e_ms = max(e2[0].elapsed_time(e2[1]), 1e3 * wall) / args.steps
+    e2e = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+           "api": "grom_step_host(traj, 1, u_in=pinned host, u_out=pinned host)"}
+    tr.close()
+    launches_per_step = 3  # K1 streaming kernel, K1 finalize, fused BDF3/EXT3 step
+
+    # -------------------------------------------- errors vs the FP64 oracle
+    cores = os.cpu_count() or 1
+    Ch = None
+    errors = {}
+    cpu_baseline = None
+    if rank_id == 0:
+        oracle.set_threads(cores)
+        Ch = C.cpu().numpy()
+        t_ref = time.perf_counter()
+        c_full = oracle.nonlinear_full(Ch, u0[0])
+        t_ref = time.perf_counter() - t_ref
+        c_cp = oracle.nonlinear_cp_skew(*factors, u0[0])
+
+    # ------------------------------------------------------------ variants
+    wanted = VARIANTS if args.variants == "all" else (
+        [] if args.variants == "none" else [tuple(v.split(":")) for v in args.variants.split(",")])
+    flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device="cuda")
+    variants = {}
+    for form, storage in wanted:
+        vrom = make_rom(form, storage)
+        key = "%s_%s" % ("full" if form == "full" else "cpd", storage)
+        vsteps = max(10, min(args.steps, 200))
+        if form == "full":
+            vms, vcode, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
+            entry = {"ms_per_step": vms, "steps_per_s": 1e3 / vms, "l2": "tensor > L2"}
+        else:
+            vms, vcode, per = time_variant(grom, torch, vrom, u0, vsteps, 3, flush=flush)
+            wms, _, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
+            entry = {"ms_per_step": vms, "steps_per_s": 1e3 / vms, "l2": "flushed before every step",
+                     "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+                     "warm_l2_ms_per_step": wms, "warm_l2_steps_per_s": 1e3 / wms}
+        if rank_id == 0:
+            ud = torch.from_numpy(u0.copy()).cuda()
+            cd = torch.empty_like(ud)
+            vrom.nonlinear(ud, cd)
+            torch.cuda.synchronize()
+            ref = c_full if form == "full" else c_cp
+            entry["eval_rel_err_vs_fp64_oracle"] = rel(cd.cpu().numpy()[0], ref)
+            entry["tolerance"] = TOL[storage]
+            if form != "full":
+                entry["cp_vs_full_model_gap"] = rel(ref, c_full)
+        entry["status"] = grom.ERRORS.get(vcode, "OK") if vcode else "OK"
+        variants[key] = entry
+        vrom.close()
+    del flush
+
+    # ---------------------------------------------- CPU baseline (oracle)
+    if rank_id == 0 and not args.no_cpu_baseline:
+        a_rom = oracle.Rom("full", n, a, NU, DT, C=Ch)
+        h = a_rom.initial_history(u0[0])
+        t0 = time.perf_counter()
+        a_rom.step(h, 1)
+        t1 = time.perf_counter() - t0
+        k = int(max(1, min(200, args.cpu_seconds / max(t1, 1e-6))))
+        t0 = time.perf_counter()
+        a_rom.step(h, k)
+        tk = time.perf_counter() - t0
+        cpu_baseline = {"value": k / tk, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                        "sample": "%d BDF3/EXT3 steps (after 1 untimed) of the N=%d FP64 full G-ROM on the "
+                                  "host cores, OpenMP over the test index" % (k, n)}
+        # trajectory error of each full-form storage type after 1 + k steps
+        for storage in ("bf16", "f32", "f32x2", "f64"):
+            key = "full_%s" % storage
+            if key not in variants:
+                continue
+            vrom = make_rom("full", storage)
+            vt = grom.Trajectories(vrom, u0)
+            vt.step(1 + k)
+            hv = vt.get_state()[0]
+            variants[key]["traj_rel_err_after_%d_steps" % (1 + k)] = rel(hv[:n], h[:n])
+            vt.close()
+            vrom.close()
+        errors["oracle_full_eval_seconds"] = t_ref
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": _config(n, R),
+        "roofline": roofline,
+        "cpu_baseline": cpu_baseline,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "status": grom.ERRORS.get(code, "OK") if code else "OK",
+        "variants": variants,
+    }
+    if errors:
+        line["oracle"] = errors
+    if rank_id == 0:
+        out = json.dumps(line)
+        print(out)
+        if args.json_out:
+            with open(args.json_out, "w") as fh:
+                fh.write(out + "\n")
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,14 @@ grom_status grom_traj_destroy(grom_traj* traj);
  * non-finite state is recorded and reported by grom_traj_status. */
 grom_status grom_step(grom_traj* traj, int32_t nsteps, double* energy, double* invariant);
 
+/* Host round trip of a stepping call: if u_in is non-NULL it replaces the
+ * newest state u^l of every trajectory (batch x n, host or device; the older
+ * history is kept, as when an observed state is fed back in an online loop),
+ * then nsteps steps are taken, then, if u_out is non-NULL, the newest state is
+ * copied to it (batch x n, host or device).  Synchronous when either pointer
+ * is host memory. */
+grom_status grom_step_host(grom_traj* traj, int32_t nsteps, const double* u_in, double* u_out);
+
 /* Synchronises the ROM's stream and reports GROM_ERR_NONFINITE (first bad
  * trajectory index in *first_bad, else -1) or GROM_OK. */
 grom_status grom_traj_status(grom_traj* traj, int32_t* first_bad);
@@ -157,6 +165,14 @@ grom_status grom_sync(grom_rom* rom);
 
 /* Bytes of device memory held by the ROM (operators, caches and scratch). */
 int64_t grom_rom_bytes(const grom_rom* rom);
+
+/* Kernel timing: while enabled, the library records CUDA events on the ROM's
+ * stream around every launch of its main contraction kernel (K1 streaming
+ * kernel for the full form, the CP projection+expansion for CP forms).
+ * grom_profile_read synchronises and returns the summed device time in ms and
+ * the number of timed launches since the last enable. */
+grom_status grom_profile_enable(grom_rom* rom, int32_t enable);
+grom_status grom_profile_read(grom_rom* rom, double* total_ms, int64_t* launches);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* grom_last_error(void);

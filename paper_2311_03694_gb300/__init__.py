@@ -58,6 +58,10 @@ EXPORTS = {
     "grom_set_state": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "grom_sync": ([ctypes.c_void_p], ctypes.c_int32),
     "grom_rom_bytes": ([ctypes.c_void_p], ctypes.c_int64),
+    "grom_step_host": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
+    "grom_profile_read": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+                          ctypes.c_int32),
     "grom_last_error": ([], ctypes.c_char_p),
 }
 
@@ -188,6 +192,15 @@ class Rom:
     def sync(self):
         _check(load().grom_sync(self._h))
 
+    def profile(self, enable=True):
+        _check(load().grom_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(summed device ms, launches) of the main contraction kernel since enable."""
+        ms, cnt = ctypes.c_double(), ctypes.c_int64()
+        _check(load().grom_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
     @property
     def nbytes(self):
         return load().grom_rom_bytes(self._h)
@@ -217,6 +230,10 @@ class Trajectories:
 
     def step(self, nsteps, energy=None, invariant=None):
         _check(load().grom_step(self._h, int(nsteps), _ptr(energy), _ptr(invariant)))
+
+    def step_host(self, nsteps, u_in=None, u_out=None):
+        """grom_step_host: feed u_in (optional), step, copy the new state to u_out."""
+        _check(load().grom_step_host(self._h, int(nsteps), _ptr(u_in), _ptr(u_out)))
 
     def status(self):
         bad = ctypes.c_int32(-1)

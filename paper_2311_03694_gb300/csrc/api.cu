@@ -116,11 +116,32 @@ static void rom_free(grom_rom* r) {
   void* ptrs[] = {r->op, r->hdiag, r->hinv, r->mass, r->mass_diag, r->linear, r->lin_diag, r->forcing, r->part, r->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
   delete[] r->row_seen;
   delete r;
 }
 
 static bool full_ready(const grom_rom* r) { return r->form != GROM_FORM_FULL || r->rows_uploaded == r->n; }
+
+// Next start/stop event pair for kernel timing (nullptr when disabled).
+static bool prof_pair(grom_rom* r, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  if (!r->prof) return true;
+  if (2 * r->prof_used + 2 > r->prof_ev.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return false;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return false;
+    }
+    r->prof_ev.push_back(a);
+    r->prof_ev.push_back(b);
+  }
+  *e0 = r->prof_ev[2 * r->prof_used];
+  *e1 = r->prof_ev[2 * r->prof_used + 1];
+  ++r->prof_used;
+  return true;
+}
 
 static K1Args k1_args(grom_rom* r) {
   K1Args a{};
@@ -348,6 +369,7 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.u_stride = r->n;
     a.c = c;
     a.c_stride = r->n;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
     e = k1_launch(r->k1, r->storage, a, batch, r->stream);
   } else {
     K3Args a = k3_args(r);
@@ -355,7 +377,11 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.u_stride = r->n;
     a.c = c;
     a.c_stride = r->n;
+    cudaEvent_t e0, e1;
+    if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
+    if (e0) cudaEventRecord(e0, r->stream);
     e = k3_launch(r->k3, r->storage, a, batch, r->stream);
+    if (e1) cudaEventRecord(e1, r->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear launch");
   return GROM_OK;
@@ -376,6 +402,7 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
     if (t->taken) cudaFree(t->taken);
     if (t->work) cudaFree(t->work);
     if (t->err) cudaFree(t->err);
+    if (t->io) cudaFree(t->io);
     delete t;
     return s;
   };
@@ -383,6 +410,7 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
   if ((st = dmalloc(&t->hist, (size_t)batch * 6 * n * sizeof(double), nullptr))) return bail(st);
   if ((st = dmalloc(&t->taken, (size_t)batch * sizeof(int64_t), nullptr))) return bail(st);
   if ((st = dmalloc(&t->err, 2 * sizeof(int), nullptr))) return bail(st);
+  if ((st = dmalloc(&t->io, (size_t)batch * n * sizeof(double), nullptr))) return bail(st);
   if (!r->diagonal && (st = dmalloc(&t->work, (size_t)batch * 4 * n * sizeof(double), nullptr))) return bail(st);
   const int init[2] = {0, INT_MAX};
   if (cudaMemsetAsync(t->hist, 0, (size_t)batch * 6 * n * sizeof(double), r->stream) != cudaSuccess ||
@@ -404,6 +432,7 @@ grom_status grom_traj_destroy(grom_traj* t) {
   cudaFree(t->taken);
   if (t->work) cudaFree(t->work);
   cudaFree(t->err);
+  cudaFree(t->io);
   --t->rom->traj_count;
   delete t;
   return GROM_OK;
@@ -416,13 +445,19 @@ static cudaError_t traj_nonlinear(grom_traj* t) {
     a.hist = t->hist;
     a.taken = t->taken;
     a.hist_stride = 6 * (int64_t)r->n;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
     return k1_launch(r->k1, r->storage, a, t->batch, r->stream);
   }
   K3Args a = k3_args(r);
   a.hist = t->hist;
   a.taken = t->taken;
   a.hist_stride = 6 * (int64_t)r->n;
-  return k3_launch(r->k3, r->storage, a, t->batch, r->stream);
+  cudaEvent_t e0, e1;
+  if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
+  if (e0) cudaEventRecord(e0, r->stream);
+  cudaError_t e = k3_launch(r->k3, r->storage, a, t->batch, r->stream);
+  if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, r->stream);
+  return e;
 }
 
 static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
@@ -464,6 +499,52 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
     if (e == cudaSuccess) e = step_launch_indexed(a, r->diagonal, s, r->stream);
     if (e != cudaSuccess) return cuda_fail(e, "grom_step launch");
   }
+  return GROM_OK;
+}
+
+grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, double* u_out) {
+  if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step_host: null trajectory");
+  grom_rom* r = t->rom;
+  const int64_t n = r->n;
+  const size_t bytes = (size_t)t->batch * n * sizeof(double);
+  if (u_in) {
+    GROM_CUDA_TRY(cudaMemcpyAsync(t->io, u_in, bytes, cudaMemcpyDefault, r->stream));
+    GROM_CUDA_TRY(state_io_launch(t->hist, t->taken, n, t->batch, t->io, true, r->stream));
+  }
+  grom_status st = grom_step(t, nsteps, nullptr, nullptr);
+  if (st) return st;
+  if (u_out) {
+    GROM_CUDA_TRY(state_io_launch(t->hist, t->taken, n, t->batch, t->io, false, r->stream));
+    GROM_CUDA_TRY(cudaMemcpyAsync(u_out, t->io, bytes, cudaMemcpyDefault, r->stream));
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, u_out) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+    }
+  }
+  return GROM_OK;
+}
+
+grom_status grom_profile_enable(grom_rom* r, int32_t enable) {
+  if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_profile_enable: null rom");
+  GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  r->prof = enable != 0;
+  r->prof_used = 0;
+  return GROM_OK;
+}
+
+grom_status grom_profile_read(grom_rom* r, double* total_ms, int64_t* launches) {
+  if (!r || !total_ms || !launches) return fail(GROM_ERR_INVALID_ARG, "grom_profile_read: null argument");
+  GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  double sum = 0.0;
+  for (size_t q = 0; q < r->prof_used; ++q) {
+    float ms = 0.f;
+    GROM_CUDA_TRY(cudaEventElapsedTime(&ms, r->prof_ev[2 * q], r->prof_ev[2 * q + 1]));
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = (int64_t)r->prof_used;
+  r->prof_used = 0;
   return GROM_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/grom.h"
 
@@ -78,6 +79,7 @@ struct K1Args {
   const int64_t* taken;
   int64_t hist_stride;
   const int32_t* active;  // nullable: trajectories with active[b]==0 are skipped
+  cudaEvent_t ev0, ev1;   // nullable: recorded around the streaming kernel
 };
 
 K1Plan k1_plan(int64_t n, int storage, int sm_count);
@@ -136,6 +138,9 @@ struct StepArgs {
   int* first_bad;           // first non-finite trajectory (atomicMin)
 };
 cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s);
+// Copies u (batch x n, device) into / out of the newest-state slot of the ring.
+cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int batch, double* u, bool inject,
+                            cudaStream_t s);
 
 // ------------------------------------------------------------ conversion
 cudaError_t convert_rows_launch(const double* src, int64_t rows, int64_t n, int64_t np,
@@ -172,6 +177,9 @@ struct grom_rom {
   grom::K3Plan k3{};
   size_t total_bytes = 0;
   int traj_count = 0;
+  bool prof = false;                 // kernel timing enabled
+  std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
+  size_t prof_used = 0;              // pairs recorded since enable
 };
 
 struct grom_traj {
@@ -181,4 +189,5 @@ struct grom_traj {
   int64_t* taken = nullptr; // batch
   double* work = nullptr;   // dense-path scratch batch x 4 x n
   int* err = nullptr;       // [0] mask, [1] first bad trajectory
+  double* io = nullptr;     // batch x n staging for grom_step_host
 };

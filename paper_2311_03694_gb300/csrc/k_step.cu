@@ -242,6 +242,24 @@ cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index
   return cudaGetLastError();
 }
 
+__global__ void k_state_io(double* hist, const int64_t* taken, int64_t n, int batch, double* u, int inject) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * batch) return;
+  const int64_t b = t / n, i = t - b * n;
+  double* slot = hist + b * 6 * n + (taken[b] % 3) * n;
+  if (inject)
+    slot[i] = u[t];
+  else
+    u[t] = slot[i];
+}
+
+cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int batch, double* u, bool inject,
+                            cudaStream_t s) {
+  const int64_t total = n * batch;
+  k_state_io<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(hist, taken, n, batch, u, inject ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s) {
   return step_launch_indexed(a, diagonal, 0, s);
 }

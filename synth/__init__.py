@@ -159,3 +159,30 @@ def arrivals(count, rate, seed, hmin=100, hmax=10000):
         horizons.append(int(np.exp(np.log(hmin) + u2 * (np.log(hmax) - np.log(hmin)))))
         variant.append(lib.synth_draw_u64(seed, STREAM_ARRIVAL, 4 * q + 2))
     return np.array(times), np.array(horizons, dtype=np.int64), np.array(variant, dtype=np.uint64)
+
+
+def cp_tensor_device(U, V, W, seed, resid_scale, device, block=64):
+    """The CP-structured tensor assembled on a torch device (FP64).
+
+    Same recipe as cp_tensor; the CP part is summed by the device's FP64
+    matrix multiply, so entries agree with the host build to FP64 rounding of
+    that sum.  Used for tensors too large to assemble quickly on the host.
+    """
+    import torch
+
+    n, rank = U.shape
+    Ud, Vd, Wd = (torch.from_numpy(np.ascontiguousarray(x)).to(device) for x in (U, V, W))
+    C = torch.empty((n, n, n), dtype=torch.float64, device=device)
+    for b0 in range(0, n, block):
+        b1 = min(n, b0 + block)
+        t1 = (Ud[b0:b1, None, :] * Vd[None]).reshape(-1, rank) @ Wd.T
+        t2 = (Wd[b0:b1, None, :] * Vd[None]).reshape(-1, rank) @ Ud.T
+        C[b0:b1] = (t1 - t2).reshape(b1 - b0, n, n)
+        del t1, t2
+    if resid_scale != 0.0:
+        G = torch.from_numpy(normal(seed, STREAM_G, 0, n ** 3)).to(device).reshape(n, n, n)
+        for b0 in range(0, n, block):
+            b1 = min(n, b0 + block)
+            C[b0:b1] += resid_scale * (G[b0:b1] - G[:, :, b0:b1].permute(2, 1, 0))
+        del G
+    return C
