@@ -174,6 +174,36 @@ int64_t grom_rom_bytes(const grom_rom* rom);
 grom_status grom_profile_enable(grom_rom* rom, int32_t enable);
 grom_status grom_profile_read(grom_rom* rom, double* total_ms, int64_t* launches);
 
+/* Allocation-free dense contraction for callers that cannot let a library
+ * allocate device memory: programs whose HBM is owned by another allocator
+ * (a framework's caching allocator, a fixed start-up budget) and real-time
+ * loops where an allocation could synchronise the device or stall.  The paper
+ * has no counterpart; this is an integration entry point.
+ *
+ * Computes c = C(u)u for ONE trajectory on `stream` (asynchronously) with the
+ * same streaming kernel as grom_nonlinear, without any ROM object: tensor, u
+ * and c are caller-owned DEVICE pointers.  `tensor` (16-byte aligned) is in
+ * the stored layout: n*n rows, row (i*n + j) holding C_ijk for k < np and
+ * zeros for n <= k < np, np = n rounded up to a multiple of 64, elements of
+ * the `storage` type (GROM_F64 double, GROM_F32 float, GROM_BF16 bfloat16;
+ * GROM_F32X2 rows are np floats hi = rn(C) followed by np floats
+ * lo = rn(C - hi)).  For n a multiple of 64 an F64/F32/BF16 tensor is plain
+ * row-major n^3.
+ *
+ * Scratch: a fixed 1 MiB file-scope device array inside the library (held by
+ * every GPU that loads the library until the process exits), enough for any
+ * n <= grom_max_n on up to ~1000 SMs; a size that needs more is rejected with
+ * GROM_ERR_UNSUPPORTED.  The call makes no cudaMalloc/cudaFree and calls no
+ * allocating library routine.  Its first call on each device resolves the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's partial sums, so calls that overlap on
+ * the GPU (other streams, other host threads) race: serialise them.  A
+ * device-side wait that times out leaves c unspecified; it is not reported
+ * (the call does not synchronise). */
+grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, const void* tensor, const double* u,
+                                        double* c, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* grom_last_error(void);
 

@@ -62,6 +62,8 @@ EXPORTS = {
     "grom_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "grom_profile_read": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                           ctypes.c_int32),
+    "grom_nonlinear_full_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "grom_last_error": ([], ctypes.c_char_p),
 }
 
@@ -117,6 +119,41 @@ def _stream_handle(stream):
 
 def max_n(form, storage):
     return load().grom_max_n(FORMS[form], STORAGE[storage])
+
+
+def nonlinear_full_noalloc(n, storage, tensor, u, c, stream=None):
+    """grom_nonlinear_full_noalloc: c = C(u)u for one trajectory without any
+    library allocation.  tensor is a device tensor already in the stored
+    layout (see include/grom.h and stored_layout()); u, c are float64 device
+    tensors of n entries."""
+    _check(load().grom_nonlinear_full_noalloc(int(n), STORAGE[storage], tensor.data_ptr(), _ptr(u), _ptr(c),
+                                              ctypes.c_void_p(_stream_handle(stream))))
+    return c
+
+
+def stored_layout(C, storage):
+    """The stored device layout of a dense FP64 torch tensor C (n, n, n):
+    k padded with zeros to a multiple of 64, converted to the storage type
+    (F32X2 rows are [hi | lo]).  Returns a flat uint8 view of the bytes."""
+    import torch
+
+    n = C.shape[0]
+    np_ = (n + 63) // 64 * 64
+    P = torch.zeros((n, n, np_), dtype=torch.float64, device=C.device)
+    P[:, :, :n] = C
+    if storage == "f64":
+        out = P
+    elif storage == "f32":
+        out = P.to(torch.float32)
+    elif storage == "bf16":
+        out = P.to(torch.bfloat16)
+    elif storage == "f32x2":
+        hi = P.to(torch.float32)
+        lo = (P - hi.to(torch.float64)).to(torch.float32)
+        out = torch.cat([hi, lo], dim=2)
+    else:
+        raise ValueError(storage)
+    return out.contiguous().view(torch.uint8).reshape(-1)
 
 
 class Rom:
