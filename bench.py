@@ -58,6 +58,7 @@ def parse_args():
     p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64,cp_skew:bf16")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('' to skip)")
     p.add_argument("--json-out", default="")
     return p.parse_args()
 
@@ -135,8 +136,8 @@ def peaks():
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
-    return 6800.0, 1900.0, "fallback"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", 0) or 0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
 
 
 def kernel_traffic(kernel_key):
@@ -284,7 +285,7 @@ def main():
     seed = synth.seed_for(2)
     C, factors, a = workload(n, R, seed, "cuda")
     u0 = synth.initial_condition(n, seed, traj=rank_id)  # one trajectory per replica
-    hbm_peak, tc_peak, peak_kind = peaks()
+    hbm_peak, tc_peak, tc_sustained, peak_kind = peaks()
 
     def make_rom(form, storage):
         if form == "full":
@@ -395,6 +396,46 @@ def main():
         vrom.close()
     del flush
 
+    # ------------------------------------------- batched trajectories (K2)
+    batched = {}
+    if args.batches:
+        for B in [int(x) for x in args.batches.split(",")]:
+            brom = grom.Rom(n, "full", "bf16", tensor=C, stiffness=a, nu=NU, dt=DT, max_batch=B)
+            U0 = synth.initial_condition(n, seed, 0, B)
+            btr = grom.Trajectories(brom, U0)
+            btr.step(2)
+            torch.cuda.synchronize()
+            bsteps = 10
+            brom.profile(True)
+            e0b, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0b.record(stream)
+            btr.step(bsteps)
+            e1b.record(stream)
+            torch.cuda.synchronize()
+            kms, kl = brom.profile_read()
+            brom.profile(False)
+            bms = e0b.elapsed_time(e1b) / bsteps
+            kavg = kms / max(1, kl)
+            flops = 2.0 * float(n) ** 3 * B
+            entry = {"ms_per_step": bms, "trajectory_steps_per_s": B * 1e3 / bms,
+                     "kernel": "k2_tc_kernel (tcgen05, KR hi/lo)" if B > 8 else "k1_stream_kernel",
+                     "kernel_ms": kavg, "alg_tflops": flops / (kavg * 1e-3) / 1e12,
+                     "tc_frac_of_sustained_bf16": flops / (kavg * 1e-3) / 1e12 / tc_sustained,
+                     "hbm_frac": float(n) ** 3 * 2 / (kavg * 1e-3) / 1e9 / hbm_peak}
+            if rank_id == 0:
+                # evaluate the whole batch through the batched kernel, check three trajectories
+                uf = torch.from_numpy(U0.copy()).cuda()
+                cf = torch.empty_like(uf)
+                brom.nonlinear(uf, cf)
+                torch.cuda.synchronize()
+                errs = [rel(cf[b].cpu().numpy(), oracle.nonlinear_full(Ch, U0[b])) for b in range(min(3, B))]
+                entry["eval_rel_err_vs_fp64_oracle_max3"] = max(errs)
+            code_b, _ = btr.status()
+            entry["status"] = grom.ERRORS.get(code_b, "OK") if code_b else "OK"
+            batched["B%d" % B] = entry
+            btr.close()
+            brom.close()
+
     # ---------------------------------------------- CPU baseline (oracle)
     if rank_id == 0 and not args.no_cpu_baseline:
         a_rom = oracle.Rom("full", n, a, NU, DT, C=Ch)
@@ -435,6 +476,7 @@ def main():
         "clocks": clocks,
         "status": grom.ERRORS.get(code, "OK") if code else "OK",
         "variants": variants,
+        "batched": batched,
     }
     if errors:
         line["oracle"] = errors

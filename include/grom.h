@@ -166,6 +166,15 @@ grom_status grom_sync(grom_rom* rom);
 /* Bytes of device memory held by the ROM (operators, caches and scratch). */
 int64_t grom_rom_bytes(const grom_rom* rom);
 
+/* Choice of the dense-contraction kernel (full form).  AUTO picks the
+ * tensor-core kernel for BF16 storage and batches above 8 trajectories, else
+ * the streaming kernel. */
+#define GROM_KERNEL_AUTO 0
+#define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass   */
+#define GROM_KERNEL_TENSOR 2 /* K2: tcgen05 GEMM over the Khatri-Rao product of the states
+                                (BF16 storage only)                                          */
+grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
+
 /* Kernel timing: while enabled, the library records CUDA events on the ROM's
  * stream around every launch of its main contraction kernel (K1 streaming
  * kernel for the full form, the CP projection+expansion for CP forms).

@@ -59,6 +59,7 @@ EXPORTS = {
     "grom_sync": ([ctypes.c_void_p], ctypes.c_int32),
     "grom_rom_bytes": ([ctypes.c_void_p], ctypes.c_int64),
     "grom_step_host": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_set_kernel": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "grom_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "grom_profile_read": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                           ctypes.c_int32),
@@ -228,6 +229,10 @@ class Rom:
 
     def sync(self):
         _check(load().grom_sync(self._h))
+
+    def set_kernel(self, kernel):
+        """Override the dense-contraction kernel: "auto", "stream" (K1) or "tensor" (K2)."""
+        _check(load().grom_set_kernel(self._h, {"auto": 0, "stream": 1, "tensor": 2}[kernel]))
 
     def profile(self, enable=True):
         _check(load().grom_profile_enable(self._h, 1 if enable else 0))

@@ -27,6 +27,7 @@ SOURCES = [
     "k1_f32.cu",
     "k1_bf16.cu",
     "k1_static.cu",
+    "k2_tc.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]

@@ -113,7 +113,8 @@ static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int
 
 static void rom_free(grom_rom* r) {
   if (!r) return;
-  void* ptrs[] = {r->op, r->hdiag, r->hinv, r->mass, r->mass_diag, r->linear, r->lin_diag, r->forcing, r->part, r->err};
+  void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
+                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -141,6 +142,13 @@ static bool prof_pair(grom_rom* r, cudaEvent_t* e0, cudaEvent_t* e1) {
   *e1 = r->prof_ev[2 * r->prof_used + 1];
   ++r->prof_used;
   return true;
+}
+
+static bool use_k2(const grom_rom* r, int batch) {
+  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok) return false;
+  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
+  if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
+  return batch > 8;
 }
 
 static K1Args k1_args(grom_rom* r) {
@@ -240,6 +248,20 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
     r->part_bytes = (size_t)r->k1.grid * r->k1.maxseg * (K1_CONSUMERS / 32) * r->k1.nb_max * sizeof(double);
     if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
+    if (r->storage == GROM_BF16) {
+      r->k2_ok = k2_make_tmap(&r->k2_tmap, r->op, n, r->np);
+      if (r->k2_ok) {
+        // scratch for the largest plan over the batch sizes this ROM accepts
+        size_t need = 0;
+        for (int b = 16;; b = b < 256 ? b + 16 : b * 2) {
+          const int bb = b < r->max_batch ? b : r->max_batch;
+          need = std::max(need, k2_scratch_bytes(k2_plan(n, bb, r->sm_count)));
+          if (bb >= r->max_batch) break;
+        }
+        r->k2_scratch_bytes = need;
+        if ((st = dmalloc(&r->k2_scratch, need, &r->total_bytes))) return bail(st);
+      }
+    }
     if (d->tensor) {
       if ((st = upload_rows(r, d->tensor, n * n, n, r->np, r->op, (int64_t)row_bytes))) return bail(st);
       r->rows_uploaded = n;
@@ -363,7 +385,18 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
   if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: batch out of range");
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: tensor rows missing");
   cudaError_t e;
-  if (r->form == GROM_FORM_FULL) {
+  if (use_k2(r, batch)) {
+    K2Args a{};
+    a.u = u;
+    a.u_stride = r->n;
+    a.c = c;
+    a.c_stride = r->n;
+    a.batch = batch;
+    a.scratch = r->k2_scratch;
+    a.err = r->err;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
+    e = k2_launch(k2_plan(r->n, batch, r->sm_count), &r->k2_tmap, a, r->stream);
+  } else if (r->form == GROM_FORM_FULL) {
     K1Args a = k1_args(r);
     a.u = u;
     a.u_stride = r->n;
@@ -440,6 +473,17 @@ grom_status grom_traj_destroy(grom_traj* t) {
 
 static cudaError_t traj_nonlinear(grom_traj* t) {
   grom_rom* r = t->rom;
+  if (use_k2(r, t->batch)) {
+    K2Args a{};
+    a.hist = t->hist;
+    a.taken = t->taken;
+    a.hist_stride = 6 * (int64_t)r->n;
+    a.batch = t->batch;
+    a.scratch = r->k2_scratch;
+    a.err = r->err;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
+    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), &r->k2_tmap, a, r->stream);
+  }
   if (r->form == GROM_FORM_FULL) {
     K1Args a = k1_args(r);
     a.hist = t->hist;
@@ -522,6 +566,16 @@ grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, dou
       GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
     }
   }
+  return GROM_OK;
+}
+
+grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
+  if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: null rom");
+  if (kernel < GROM_KERNEL_AUTO || kernel > GROM_KERNEL_TENSOR)
+    return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
+  if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
+    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form");
+  r->kernel_choice = kernel;
   return GROM_OK;
 }
 

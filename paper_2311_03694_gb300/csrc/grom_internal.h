@@ -1,6 +1,7 @@
 // Internal definitions of the GB300 Galerkin ROM library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -84,6 +85,38 @@ struct K1Args {
 
 K1Plan k1_plan(int64_t n, int storage, int sm_count);
 cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a, int batch, cudaStream_t s);
+
+// ------------------------------------------------- K2 (tensor cores, BF16)
+struct K2Plan {
+  int64_t n, np;
+  int btile;       // trajectories per column tile (multiple of 16, <= 256)
+  int col_tiles;   // column tiles
+  int i_tiles;     // 128-row tiles of the test index
+  int splits;      // split of the K range (advecting index j) across CTAs
+  int stages_a;    // pipeline depth of the C tiles
+  int stages_b;    // pipeline depth of the KR tiles (hi and lo)
+  int tmem_cols;   // allocated tensor-memory columns
+  int64_t bp;      // padded batch
+  size_t smem;
+};
+struct K2Args {
+  const double* u;
+  int64_t u_stride;
+  double* c;
+  int64_t c_stride;
+  double* hist;
+  const int64_t* taken;
+  int64_t hist_stride;
+  const int32_t* active;
+  int batch;
+  void* scratch;  // k2_scratch_bytes(plan)
+  int* err;
+  cudaEvent_t ev0, ev1;
+};
+K2Plan k2_plan(int64_t n, int batch, int sm_count);
+size_t k2_scratch_bytes(const K2Plan& p);
+bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np);
+cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s);
 
 // ------------------------------------------------------------- K3 (CP)
 constexpr int K3_THREADS = 256;
@@ -177,6 +210,11 @@ struct grom_rom {
   grom::K3Plan k3{};
   size_t total_bytes = 0;
   int traj_count = 0;
+  int kernel_choice = 0;             // GROM_KERNEL_* override
+  bool k2_ok = false;                // tensor map built (BF16 full form)
+  CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
+  void* k2_scratch = nullptr;        // K2 state copy + split-K partials
+  size_t k2_scratch_bytes = 0;
   bool prof = false;                 // kernel timing enabled
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
   size_t prof_used = 0;              // pairs recorded since enable

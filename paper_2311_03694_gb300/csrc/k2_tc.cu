@@ -1,0 +1,349 @@
+// K2: batched dense contraction on the tcgen05 tensor cores (BF16 storage).
+//
+// For B trajectories the contraction is one GEMM (Sec. 2.2, eq. Cu, written
+// with the mode-1 matricisation of C):
+//   Cout[i, b] = sum_{(j,k)} C_(1)[i, (j,k)] * KR[(j,k), b],  KR[(j,k), b] = u_bj u_bk
+// with M = n (test index), N = B, K = n * np.  KR, the Khatri-Rao product of
+// the states, is never materialised: each K-tile of 64 covers one advecting
+// index j and 64 advected indices k, so its KR tile is u_bj * u_b[k0:k0+64],
+// generated in registers (FP32 products) and written into shared memory in the
+// 128-byte swizzled K-major layout the tensor core reads.  Each product p is
+// stored as two BF16 tiles hi = rn(p), lo = rn(p - hi) and both are
+// multiplied (two MMAs per K step): rounding p to BF16 alone would add an
+// error of the size of the tensor's own BF16 rounding, which on
+// cancellation-heavy states pushes the result past the BF16 tolerance; with
+// the split the Khatri-Rao operand is exact to ~2^-17.
+//
+// CTA (10 warps): warp 0 issues TMA loads of 128 x 64 BF16 tiles of C; warp
+// 1 owns the tensor memory and issues tcgen05.mma (M=128, N=btile, K=16) into
+// an FP32 accumulator in TMEM; warps 2-9 generate the KR tiles (one row b
+// each) and afterwards read the accumulator back (tcgen05.ld) and store FP32
+// partial sums.  Stages are recycled through mbarriers signalled by
+// tcgen05.commit.  The K range is split across CTAs by ranges of j; a reduce
+// kernel sums the splits in a fixed order (deterministic) into FP64.
+// K-tiles are ordered with the advected block outer and j inner, so each
+// generator thread keeps its 64 u_bk values in registers across j.
+#include <cudaTypedefs.h>
+
+#include "grom_internal.h"
+#include "tc.cuh"
+
+namespace grom {
+
+constexpr int K2_THREADS = 320;
+constexpr int K2_GEN_WARPS = 8;
+constexpr int K2_A_BYTES = 128 * 128;  // 128 rows x 64 bf16
+
+struct K2Dev {
+  int64_t n, np;
+  int btile, col_tiles, i_tiles, splits, stages_a, stages_b, tmem_cols;
+  int64_t bp;  // padded batch = col_tiles * btile
+  float* ub;   // bp x np FP32 copy of the states (zero padded)
+  float* part; // splits x n x bp FP32 partials
+  int* err;
+};
+
+__device__ __forceinline__ void k2_abort(volatile int* abort_flag, int* err) {
+  *abort_flag = 1;
+  atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_constant__ CUtensorMap tmap, const K2Dev p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int SA = p.stages_a, SB = p.stages_b;
+  const int half_bytes = p.btile * 128;   // one BF16 KR tile (hi or lo)
+  const int b_bytes = 2 * half_bytes;      // hi tile, then lo tile
+  uint8_t* sa = smem;                                  // SA x 16 KB
+  uint8_t* sb = smem + (size_t)SA * K2_A_BYTES;        // SB x (hi | lo)
+  uint64_t* full_a = reinterpret_cast<uint64_t*>(sb + (size_t)SB * b_bytes);
+  uint64_t* empty_a = full_a + SA;
+  uint64_t* full_b = empty_a + SA;
+  uint64_t* empty_b = full_b + SB;
+  uint64_t* accum = empty_b + SB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // tile coordinates
+  const int split = blockIdx.x % p.splits;
+  const int rest = blockIdx.x / p.splits;
+  const int col_tile = rest % p.col_tiles;
+  const int i_tile = rest / p.col_tiles;
+  const int64_t j0 = (int64_t)split * p.n / p.splits, j1 = ((int64_t)split + 1) * p.n / p.splits;
+  const int64_t nj = j1 - j0;
+  const int64_t kblocks = p.np / 64;
+  const int64_t T = nj * kblocks;  // K-tiles of this CTA
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SA; ++s) {
+      ptx::mbar_init(&full_a[s], 1);
+      ptx::mbar_init(&empty_a[s], 1);
+    }
+    for (int s = 0; s < SB; ++s) {
+      ptx::mbar_init(&full_b[s], K2_GEN_WARPS);
+      ptx::mbar_init(&empty_b[s], 1);
+    }
+    ptx::mbar_init(accum, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap);
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, (uint32_t)p.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int64_t t = 0;
+      for (; t < T; ++t) {
+        const int s = (int)(t % SA);
+        const uint32_t ph = (uint32_t)((t / SA) & 1);
+        if (t >= SA && !ptx::mbar_wait(&empty_a[s], ph ^ 1u, abort_flag)) {
+          k2_abort(abort_flag, p.err);
+          break;
+        }
+        const int64_t kb = t / nj, j = j0 + (t - kb * nj);
+        ptx::mbar_arrive_expect_tx(&full_a[s], K2_A_BYTES);
+        tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, (int32_t)(j * p.np + kb * 64), i_tile * 128, &full_a[s]);
+      }
+      for (int64_t q = t > SA ? t - SA : 0; q < t; ++q)
+        if (!ptx::mbar_wait(&full_a[q % SA], (uint32_t)((q / SA) & 1), nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(128, p.btile);
+      for (int64_t t = 0; t < T; ++t) {
+        const int s = (int)(t % SA), r = (int)(t % SB);
+        if (!ptx::mbar_wait(&full_a[s], (uint32_t)((t / SA) & 1), abort_flag) ||
+            !ptx::mbar_wait(&full_b[r], (uint32_t)((t / SB) & 1), abort_flag)) {
+          k2_abort(abort_flag, p.err);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint64_t ad = tc::sw128_kmajor_desc(sa + (size_t)s * K2_A_BYTES);
+        const uint64_t bh = tc::sw128_kmajor_desc(sb + (size_t)r * b_bytes);
+        const uint64_t bl = tc::sw128_kmajor_desc(sb + (size_t)r * b_bytes + half_bytes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // 4 x K=16 inside the 128-byte swizzle span
+          tc::mma_bf16(tmem, ad + 2 * k, bh + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
+          tc::mma_bf16(tmem, ad + 2 * k, bl + 2 * k, idesc, 1u);
+        }
+        tc::commit(&empty_a[s]);
+        tc::commit(&empty_b[r]);
+      }
+      tc::commit(accum);  // arrives once every issued MMA has completed
+    }
+  } else {
+    // ------------------------------------------------ KR generators (8 warps)
+    const int g = threadIdx.x - 64;  // row b of the KR tile
+    const bool row_on = g < p.btile;
+    const int64_t bglob = (int64_t)col_tile * p.btile + g;
+    const float* urow = p.ub + bglob * p.np;
+    float uk[64];
+    int64_t cur_kb = -1;
+    for (int64_t t = 0; t < T; ++t) {
+      const int r = (int)(t % SB);
+      const uint32_t ph = (uint32_t)((t / SB) & 1);
+      const int64_t kb = t / nj, j = j0 + (t - kb * nj);
+      if (row_on && kb != cur_kb) {
+        const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float4 v = src[q];
+          uk[4 * q] = v.x; uk[4 * q + 1] = v.y; uk[4 * q + 2] = v.z; uk[4 * q + 3] = v.w;
+        }
+        cur_kb = kb;
+      }
+      if (t >= SB && !ptx::mbar_wait(&empty_b[r], ph ^ 1u, abort_flag)) {
+        k2_abort(abort_flag, p.err);
+        break;
+      }
+      if (row_on) {
+        const float uj = urow[j];
+        uint8_t* row_hi = sb + (size_t)r * b_bytes + (size_t)g * 128;
+        uint8_t* row_lo = row_hi + half_bytes;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          uint32_t wh[4], wl[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float p0 = uk[8 * c + 2 * h] * uj, p1 = uk[8 * c + 2 * h + 1] * uj;
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
+            const float2 hf = __bfloat1622float2(hi);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - hf.x, p1 - hf.y);
+            wh[h] = *reinterpret_cast<const uint32_t*>(&hi);
+            wl[h] = *reinterpret_cast<const uint32_t*>(&lo);
+          }
+          const int off = (c ^ (g & 7)) << 4;
+          *reinterpret_cast<uint4*>(row_hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+          *reinterpret_cast<uint4*>(row_lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        }
+      }
+      ptx::fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&full_b[r]);
+    }
+    // -------------------------------------------------------------- epilogue
+    if (warp >= 2 && warp < 6) {
+      const bool ok = ptx::mbar_wait(accum, 0, nullptr);
+      if (!ok) atomicOr(p.err, DEV_ERR_TIMEOUT);
+      tc::fence_after_sync();
+      const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are readable by this warp
+      const int64_t i = (int64_t)i_tile * 128 + 32 * q + lane;
+      if (ok && !*abort_flag) {
+        for (int c0 = 0; c0 < p.btile; c0 += 32) {
+          uint32_t rr[32];
+          tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, rr);
+          tc::tmem_ld_wait();
+          if (i < p.n) {
+            float* dst = p.part + ((int64_t)split * p.n + i) * p.bp + (int64_t)col_tile * p.btile + c0;
+            const int m = p.btile - c0 < 32 ? p.btile - c0 : 32;
+            if (m == 32) {
+#pragma unroll
+              for (int v = 0; v < 8; ++v)
+                reinterpret_cast<float4*>(dst)[v] =
+                    make_float4(__uint_as_float(rr[4 * v]), __uint_as_float(rr[4 * v + 1]),
+                                __uint_as_float(rr[4 * v + 2]), __uint_as_float(rr[4 * v + 3]));
+            } else {
+#pragma unroll
+              for (int v = 0; v < 32; ++v)
+                if (v < m) dst[v] = __uint_as_float(rr[v]);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+  }
+}
+
+// ub[b][k] = u_b[k] (FP32), zero for padding rows/columns and inactive trajectories.
+__global__ void k2_prep_kernel(const K2Dev p, const double* u, int64_t u_stride, const double* hist,
+                               const int64_t* taken, int64_t hist_stride, const int32_t* active, int batch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.bp * p.np) return;
+  const int64_t b = t / p.np, k = t - b * p.np;
+  float v = 0.f;
+  if (b < batch && k < p.n && (active == nullptr || active[b])) {
+    const double* ub = taken ? hist + b * hist_stride + (taken[b] % 3) * p.n : u + b * u_stride;
+    v = __double2float_rn(ub[k]);
+  }
+  p.ub[t] = v;
+}
+
+// c[b][i] = sum over splits of the FP32 partials, in split order, in FP64.
+__global__ void k2_reduce_kernel(const K2Dev p, double* c, int64_t c_stride, double* hist, const int64_t* taken,
+                                 int64_t hist_stride, const int32_t* active, int batch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)batch * p.n) return;
+  const int64_t i = t / batch, b = t - i * batch;  // consecutive threads: consecutive b (coalesced reads)
+  if (active && !active[b]) return;
+  double s = 0.0;
+  for (int q = 0; q < p.splits; ++q) s += (double)p.part[((int64_t)q * p.n + i) * p.bp + b];
+  double* dst = taken ? hist + b * hist_stride + (3 + taken[b] % 3) * p.n : c + b * c_stride;
+  dst[i] = s;
+}
+
+// ------------------------------------------------------------------- host
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(n * np), (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(n * np * 2)};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(tensor), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+K2Plan k2_plan(int64_t n, int batch, int sm_count) {
+  K2Plan p{};
+  p.n = n;
+  p.np = padded_n(n);
+  int btile = (batch + 15) / 16 * 16;
+  if (btile > 256) btile = 256;
+  p.btile = btile;
+  p.col_tiles = (batch + btile - 1) / btile;
+  p.i_tiles = (int)((n + 127) / 128);
+  const int tiles = p.col_tiles * p.i_tiles;
+  int splits = sm_count / tiles;
+  if (splits < 1) splits = 1;
+  if (splits > n) splits = (int)n;
+  p.splits = splits;
+  const int b_bytes = 2 * btile * 128;  // hi and lo KR tiles
+  p.stages_b = btile >= 128 ? 2 : 4;
+  int sa = (int)((200 * 1024 - p.stages_b * b_bytes) / K2_A_BYTES);
+  if (sa > 8) sa = 8;
+  if (sa < 2) sa = 2;
+  p.stages_a = sa;
+  int cols = 32;
+  while (cols < btile) cols <<= 1;
+  p.tmem_cols = cols;
+  p.smem = 1024 + (size_t)sa * K2_A_BYTES + (size_t)p.stages_b * b_bytes + (size_t)(2 * sa + 2 * p.stages_b + 1) * 8 + 16;
+  p.bp = (int64_t)p.col_tiles * btile;
+  return p;
+}
+
+size_t k2_scratch_bytes(const K2Plan& p) {
+  return 4 * ((size_t)p.bp * p.np + (size_t)p.splits * p.n * p.bp);
+}
+
+cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
+  K2Dev d{};
+  d.n = p.n;
+  d.np = p.np;
+  d.btile = p.btile;
+  d.col_tiles = p.col_tiles;
+  d.i_tiles = p.i_tiles;
+  d.splits = p.splits;
+  d.stages_a = p.stages_a;
+  d.stages_b = p.stages_b;
+  d.tmem_cols = p.tmem_cols;
+  d.bp = p.bp;
+  d.ub = reinterpret_cast<float*>(a.scratch);
+  d.part = d.ub + p.bp * p.np;
+  d.err = a.err;
+  const int64_t prep = p.bp * p.np;
+  k2_prep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(d, a.u, a.u_stride, a.hist, a.taken, a.hist_stride,
+                                                                a.active, a.batch);
+  cudaError_t e = cudaFuncSetAttribute(k2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  if (a.ev0) cudaEventRecord(a.ev0, s);
+  k2_tc_kernel<<<(unsigned)(p.i_tiles * p.col_tiles * p.splits), K2_THREADS, p.smem, s>>>(*tmap, d);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.ev1) cudaEventRecord(a.ev1, s);
+  const int64_t red = (int64_t)a.batch * p.n;
+  k2_reduce_kernel<<<(unsigned)((red + 255) / 256), 256, 0, s>>>(d, a.c, a.c_stride, a.hist, a.taken, a.hist_stride,
+                                                                 a.active, a.batch);
+  return cudaGetLastError();
+}
+
+}  // namespace grom
