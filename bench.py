@@ -58,7 +58,7 @@ def parse_args():
     p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64,cp_skew:bf16")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('' to skip)")
+    p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('none' to skip)")
     p.add_argument("--json-out", default="")
     return p.parse_args()
 
@@ -305,10 +305,12 @@ def main():
     rom.profile(True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     tr.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
@@ -398,7 +400,7 @@ def main():
 
     # ------------------------------------------- batched trajectories (K2)
     batched = {}
-    if args.batches:
+    if args.batches and args.batches != "none":
         for B in [int(x) for x in args.batches.split(",")]:
             brom = grom.Rom(n, "full", "bf16", tensor=C, stiffness=a, nu=NU, dt=DT, max_batch=B)
             U0 = synth.initial_condition(n, seed, 0, B)

@@ -436,6 +436,8 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
     if (t->work) cudaFree(t->work);
     if (t->err) cudaFree(t->err);
     if (t->io) cudaFree(t->io);
+    if (t->red) cudaFree(t->red);
+    if (t->cnt) cudaFree(t->cnt);
     delete t;
     return s;
   };
@@ -444,6 +446,13 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
   if ((st = dmalloc(&t->taken, (size_t)batch * sizeof(int64_t), nullptr))) return bail(st);
   if ((st = dmalloc(&t->err, 2 * sizeof(int), nullptr))) return bail(st);
   if ((st = dmalloc(&t->io, (size_t)batch * n * sizeof(double), nullptr))) return bail(st);
+  if (r->diagonal) {
+    const int nblk = step_mc_blocks(n);
+    if ((st = dmalloc(&t->red, (size_t)batch * nblk * 2 * sizeof(double), nullptr))) return bail(st);
+    if ((st = dmalloc(&t->cnt, (size_t)batch * sizeof(unsigned int), nullptr))) return bail(st);
+    if (cudaMemsetAsync(t->cnt, 0, (size_t)batch * sizeof(unsigned int), r->stream) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "grom_traj_create"));
+  }
   if (!r->diagonal && (st = dmalloc(&t->work, (size_t)batch * 4 * n * sizeof(double), nullptr))) return bail(st);
   const int init[2] = {0, INT_MAX};
   if (cudaMemsetAsync(t->hist, 0, (size_t)batch * 6 * n * sizeof(double), r->stream) != cudaSuccess ||
@@ -466,12 +475,18 @@ grom_status grom_traj_destroy(grom_traj* t) {
   if (t->work) cudaFree(t->work);
   cudaFree(t->err);
   cudaFree(t->io);
+  if (t->red) cudaFree(t->red);
+  if (t->cnt) cudaFree(t->cnt);
+  if (t->graph) cudaGraphExecDestroy(t->graph);
+  if (t->gstream) cudaStreamDestroy(t->gstream);
+  if (t->ev_in) cudaEventDestroy(t->ev_in);
+  if (t->ev_out) cudaEventDestroy(t->ev_out);
   --t->rom->traj_count;
   delete t;
   return GROM_OK;
 }
 
-static cudaError_t traj_nonlinear(grom_traj* t) {
+static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   grom_rom* r = t->rom;
   if (use_k2(r, t->batch)) {
     K2Args a{};
@@ -482,7 +497,7 @@ static cudaError_t traj_nonlinear(grom_traj* t) {
     a.scratch = r->k2_scratch;
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
-    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), &r->k2_tmap, a, r->stream);
+    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), &r->k2_tmap, a, strm);
   }
   if (r->form == GROM_FORM_FULL) {
     K1Args a = k1_args(r);
@@ -490,7 +505,7 @@ static cudaError_t traj_nonlinear(grom_traj* t) {
     a.taken = t->taken;
     a.hist_stride = 6 * (int64_t)r->n;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
-    return k1_launch(r->k1, r->storage, a, t->batch, r->stream);
+    return k1_launch(r->k1, r->storage, a, t->batch, strm);
   }
   K3Args a = k3_args(r);
   a.hist = t->hist;
@@ -498,9 +513,9 @@ static cudaError_t traj_nonlinear(grom_traj* t) {
   a.hist_stride = 6 * (int64_t)r->n;
   cudaEvent_t e0, e1;
   if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
-  if (e0) cudaEventRecord(e0, r->stream);
-  cudaError_t e = k3_launch(r->k3, r->storage, a, t->batch, r->stream);
-  if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, r->stream);
+  if (e0) cudaEventRecord(e0, strm);
+  cudaError_t e = k3_launch(r->k3, r->storage, a, t->batch, strm);
+  if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, strm);
   return e;
 }
 
@@ -529,7 +544,33 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
   a.invariant = invariant;
   a.err = t->err;
   a.first_bad = t->err + 1;
+  a.red = t->red;
+  a.cnt = t->cnt;
+  a.nblk = step_mc_blocks(r->n);
   return a;
+}
+
+// Enqueues `count` steps (per-step outputs at step_index offset) on strm.
+static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double* invariant, cudaStream_t strm) {
+  grom_rom* r = t->rom;
+  StepArgs a = step_args(t, energy, invariant);
+  const bool fused_k1 = r->diagonal && r->form == GROM_FORM_FULL && !use_k2(r, t->batch);
+  for (int s = 0; s < count; ++s) {
+    cudaError_t e;
+    if (fused_k1) {
+      K1Args k = k1_args(r);
+      k.hist = t->hist;
+      k.taken = t->taken;
+      k.hist_stride = 6 * (int64_t)r->n;
+      if (!prof_pair(r, &k.ev0, &k.ev1)) return cudaErrorMemoryAllocation;
+      e = k1_launch_fused_step(r->k1, r->storage, k, a, t->batch, s, strm);
+    } else {
+      e = traj_nonlinear(t, strm);
+      if (e == cudaSuccess) e = step_launch_indexed(a, r->diagonal, s, strm);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {
@@ -537,12 +578,45 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step: nsteps < 0");
   grom_rom* r = t->rom;
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
-  StepArgs a = step_args(t, energy, invariant);
-  for (int32_t s = 0; s < nsteps; ++s) {
-    cudaError_t e = traj_nonlinear(t);
-    if (e == cudaSuccess) e = step_launch_indexed(a, r->diagonal, s, r->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "grom_step launch");
+  constexpr int G = 8;  // steps per captured graph
+  int done = 0;
+  if (!energy && !invariant && !r->prof && nsteps >= G) {
+    // Replay a captured graph of G steps on a private stream joined to the
+    // ROM's stream by events (the ROM's stream may be the legacy default
+    // stream, which cannot be captured).
+    if (t->graph && t->graph_version != r->version) {
+      cudaGraphExecDestroy(t->graph);
+      t->graph = nullptr;
+    }
+    if (!t->graph) {
+      if (!t->gstream) {
+        GROM_CUDA_TRY(cudaStreamCreateWithFlags(&t->gstream, cudaStreamNonBlocking));
+        GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
+        GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
+      }
+      cudaGraph_t g = nullptr;
+      GROM_CUDA_TRY(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = launch_steps(t, G, nullptr, nullptr, t->gstream);
+      cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : e2, "grom_step graph capture");
+      }
+      e = cudaGraphInstantiate(&t->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "grom_step graph instantiate");
+      t->graph_steps = G;
+      t->graph_version = r->version;
+    }
+    GROM_CUDA_TRY(cudaEventRecord(t->ev_in, r->stream));
+    GROM_CUDA_TRY(cudaStreamWaitEvent(t->gstream, t->ev_in, 0));
+    for (; done + G <= nsteps; done += G) GROM_CUDA_TRY(cudaGraphLaunch(t->graph, t->gstream));
+    GROM_CUDA_TRY(cudaEventRecord(t->ev_out, t->gstream));
+    GROM_CUDA_TRY(cudaStreamWaitEvent(r->stream, t->ev_out, 0));
   }
+  cudaError_t e = launch_steps(t, nsteps - done, energy, invariant, r->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grom_step launch");
   return GROM_OK;
 }
 
@@ -576,6 +650,7 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
     return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form");
   r->kernel_choice = kernel;
+  ++r->version;
   return GROM_OK;
 }
 
@@ -619,7 +694,7 @@ grom_status grom_get_state(grom_traj* t, double* hist) {
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_get_state: tensor rows missing");
   const int64_t n = r->n, B = t->batch;
   // n^l of the newest state, so the export is self-consistent
-  cudaError_t e = traj_nonlinear(t);
+  cudaError_t e = traj_nonlinear(t, r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "grom_get_state");
   grom_status st = grom_sync(r);
   if (st) return st;

@@ -81,6 +81,7 @@ struct K1Args {
   int64_t hist_stride;
   const int32_t* active;  // nullable: trajectories with active[b]==0 are skipped
   cudaEvent_t ev0, ev1;   // nullable: recorded around the streaming kernel
+  int skip_finalize;      // 1: the caller runs a fused finalize (see k_step.cu)
 };
 
 K1Plan k1_plan(int64_t n, int storage, int sm_count);
@@ -169,7 +170,20 @@ struct StepArgs {
   double* invariant;        // nullable
   int* err;                 // device error flags
   int* first_bad;           // first non-finite trajectory (atomicMin)
+  // multi-CTA diagonal step: per-CTA partial sums and arrival counters
+  double* red;              // batch x nblk x 2
+  unsigned int* cnt;        // batch (zero between launches)
+  int nblk;                 // CTAs per trajectory
 };
+constexpr int STEP_MC_THREADS = 128;
+inline int step_mc_blocks(int64_t n) { return (int)((n + STEP_MC_THREADS - 1) / STEP_MC_THREADS); }
+// Diagonal step over several CTAs per trajectory.  With k1 != nullptr the
+// K1 partial sums of trajectories b0 .. b0+nb-1 are finalised in the same
+// kernel (the advection term is written to the history ring first).
+cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
+                                int nbk, cudaStream_t s);
+cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch,
+                                 int step_index, cudaStream_t s);
 cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s);
 // Copies u (batch x n, device) into / out of the newest-state slot of the ring.
 cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int batch, double* u, bool inject,
@@ -211,6 +225,7 @@ struct grom_rom {
   size_t total_bytes = 0;
   int traj_count = 0;
   int kernel_choice = 0;             // GROM_KERNEL_* override
+  int version = 0;                   // bumped when cached launch graphs become stale
   bool k2_ok = false;                // tensor map built (BF16 full form)
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
@@ -228,4 +243,11 @@ struct grom_traj {
   double* work = nullptr;   // dense-path scratch batch x 4 x n
   int* err = nullptr;       // [0] mask, [1] first bad trajectory
   double* io = nullptr;     // batch x n staging for grom_step_host
+  double* red = nullptr;    // multi-CTA step partials
+  unsigned int* cnt = nullptr;
+  cudaGraphExec_t graph = nullptr;  // captured block of steps (no per-step outputs)
+  int graph_steps = 0;
+  int graph_version = -1;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };

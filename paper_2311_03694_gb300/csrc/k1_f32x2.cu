@@ -5,7 +5,7 @@ namespace grom {
 
 template <int QM, int NB>
 static constexpr bool k1_valid() {
-  return K1Traits<GROM_F32X2>::ACC_WORDS * K1Traits<GROM_F32X2>::EPV * QM * NB <= 64;
+  return K1Traits<GROM_F32X2>::ACC_WORDS * K1Traits<GROM_F32X2>::EPV * QM * NB <= 32;
 }
 
 template <int QM, int NB>

@@ -17,7 +17,7 @@ static int pow2_ceil(int64_t x) {
 static int acc_regs(int storage) {
   switch (storage) {
     case GROM_F64: return 4;    // 2 elements x 2 words
-    case GROM_F32X2: return 8;  // 4 elements x (S, s)
+    case GROM_F32X2: return 16;  // 4 elements x (S, s), plus hi and lo vectors held per chunk
     case GROM_F32: return 4;
     case GROM_BF16: return 8;
   }
@@ -39,7 +39,13 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count) {
   p.n = n;
   p.np = padded_n(n);
   p.row_bytes = p.np * storage_elem_bytes(storage);
+  // vector positions per row and the consumer mapping (see k1_stream.cuh)
+  const int64_t P = p.np / epv(storage);
+  p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
+  const int64_t rpr = P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
+  const int64_t rmax = 8 / p.qm;  // rows a consumer thread holds in registers per chunk
   p.rpc = K1_STAGE_BYTES / p.row_bytes;
+  if (p.rpc > rmax * rpr) p.rpc = rmax * rpr;
   if (p.rpc < 1) p.rpc = 1;
   if (p.rpc > n) p.rpc = n;
   p.cpi = (n + p.rpc - 1) / p.rpc;
@@ -50,8 +56,6 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count) {
   p.grid = (int)grid;
   const int64_t per = (p.T + grid - 1) / grid;
   p.maxseg = (int)((per + p.cpi - 1) / p.cpi + 1);
-  const int64_t P = p.np / epv(storage);
-  p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
   const int u_bytes_per_traj = (int)(p.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
   const int base = 1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16;
   const int budget = 227 * 1024 - base;
@@ -80,6 +84,36 @@ cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a0, int bat
       case GROM_BF16: e = k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s); break;
       default: e = cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace grom
+
+namespace grom {
+
+cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a0, const StepArgs& st, int batch,
+                                 int step_index, cudaStream_t s) {
+  for (int b0 = 0; b0 < batch; b0 += plan.nb_max) {
+    K1Args a = a0;
+    const int rem = batch - b0;
+    a.nb = rem < plan.nb_max ? rem : plan.nb_max;
+    a.skip_finalize = 1;
+    const int nb = pow2_ceil(a.nb);
+    K1Plan pl = plan;
+    const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
+    pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
+    cudaError_t e;
+    switch (storage) {
+      case GROM_F64: e = k1_dispatch_f64(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_F32X2: e = k1_dispatch_f32x2(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_F32: e = k1_dispatch_f32(pl.qm, nb, pl, a, b0, s); break;
+      case GROM_BF16: e = k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    e = step_diag_mc_launch(st, step_index, &pl, &a, b0, a.nb, nb, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -157,19 +157,22 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int64_t it = 0;
+      int64_t i = c0 / pl.cpi, jc = c0 - i * pl.cpi;  // chunk (i, jc), advanced incrementally
+      int s = 0;
+      uint32_t ph = 0;
       for (int64_t c = c0; c < c1; ++c, ++it) {
-        const int s = (int)(it % K1_STAGES);
-        const uint32_t ph = (uint32_t)((it / K1_STAGES) & 1);
         if (it >= K1_STAGES && !ptx::mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
           *abort_flag = 1;
           atomicOr(a.err, DEV_ERR_TIMEOUT);
           break;
         }
-        int64_t i, j0, rows;
-        chunk_decode(c, pl.cpi, pl.rpc, n, i, j0, rows);
+        const int64_t j0 = jc * pl.rpc;
+        const int64_t rows = n - j0 < pl.rpc ? n - j0 : pl.rpc;
         const uint32_t bytes = (uint32_t)(rows * row_bytes);
         ptx::mbar_arrive_expect_tx(&full[s], bytes);
         ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * n + j0) * row_bytes, bytes, &full[s]);
+        if (++jc == pl.cpi) { jc = 0; ++i; }
+        if (++s == K1_STAGES) { s = 0; ph ^= 1u; }
       }
       // Let every copy this CTA issued land before the CTA can exit.
       const int64_t issued = it;
@@ -244,109 +247,139 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
       }
     };
 
-    int64_t it = 0;
-    for (int64_t c = c0; c < c1; ++c, ++it) {
-      int64_t i, j0, rows;
-      chunk_decode(c, pl.cpi, pl.rpc, n, i, j0, rows);
+    // Each thread owns at most RMAX rows x QM positions of a chunk (the plan
+    // caps the rows per chunk accordingly).  It copies them to registers and
+    // releases the stage at once, so the ring refills while it computes.
+    // Offsets inside a stage are 32-bit; chunks advance without divisions.
+    constexpr int RMAX = 8 / QM;
+    constexpr int PLANES = (ST == GROM_F32X2) ? 2 : 1;
+    const int rowb = (int)row_bytes;
+    const int t_off = (int)(ro * row_bytes + pos0 * 16);  // this thread's first vector in a stage
+    const int t_step = (int)(rpr * row_bytes);             // next row of this thread
+    const int plane_off = (int)(np * 4);                    // F32X2: lo plane
+    const bool full_pos = act && (pos0 + (int64_t)(QM - 1) * K1_CONSUMERS < P);
+    (void)rowb;
+    int64_t ci = c0 / pl.cpi, cj = c0 - ci * pl.cpi;
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t c = c0; c < c1; ++c) {
+      const int64_t i = ci;
+      const int j0 = (int)(cj * pl.rpc);
+      const int rows = (int)(n - j0 < pl.rpc ? n - j0 : pl.rpc);
+      if (++cj == pl.cpi) { cj = 0; ++ci; }
       if (i != cur_i) {
         if (cur_i >= 0) flush(cur_i);
         cur_i = i;
       }
-      const int s = (int)(it % K1_STAGES);
-      const uint32_t ph = (uint32_t)((it / K1_STAGES) & 1);
       if (!ptx::mbar_wait(&full[s], ph, abort_flag)) {
         *abort_flag = 1;
         atomicOr(a.err, DEV_ERR_TIMEOUT);
         break;
       }
-      const uint8_t* st = stages + (size_t)s * K1_STAGE_BYTES;
-      if (act) {
-        for (int64_t rr = ro; rr < rows; rr += rpr) {
-          const int64_t j = j0 + rr;
-          const uint8_t* rowp = st + rr * row_bytes;
-          if constexpr (ST == GROM_F64) {
-            double uj[NB];
+      const uint8_t* st = stages + s * K1_STAGE_BYTES + t_off;
+      // rows of this chunk held by this thread
+      int nrow = act ? (rows - (int)ro + (int)rpr - 1) / (int)rpr : 0;
+      if (nrow > RMAX) nrow = RMAX;
+      if (nrow < 0) nrow = 0;
+      uint4 vec[RMAX][QM][PLANES];
+      if (full_pos && nrow == RMAX) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(ureg)[b * np + j];
+        for (int t = 0; t < RMAX; ++t)
 #pragma unroll
-            for (int q = 0; q < QM; ++q) {
-              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
-              if (pos < P) {
-                const double2 x = *reinterpret_cast<const double2*>(rowp + pos * 16);
+          for (int q = 0; q < QM; ++q)
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                  acc[q][0][b].v = fma(x.x, uj[b], acc[q][0][b].v);
-                  acc[q][1][b].v = fma(x.y, uj[b], acc[q][1][b].v);
-                }
-              }
-            }
-          } else if constexpr (ST == GROM_F32X2) {
-            float uh[NB], ul[NB];
+            for (int p2 = 0; p2 < PLANES; ++p2)
+              vec[t][q][p2] = *reinterpret_cast<const uint4*>(st + t * t_step + q * (K1_CONSUMERS * 16) + p2 * plane_off);
+      } else {
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t)
+#pragma unroll
+          for (int q = 0; q < QM; ++q) {
+            const bool ok = t < nrow && (pos0 + (int64_t)q * K1_CONSUMERS < P);
+#pragma unroll
+            for (int p2 = 0; p2 < PLANES; ++p2)
+              vec[t][q][p2] = ok ? *reinterpret_cast<const uint4*>(st + t * t_step + q * (K1_CONSUMERS * 16) + p2 * plane_off)
+                                 : make_uint4(0, 0, 0, 0);
+          }
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[s]);
+      if (++s == K1_STAGES) { s = 0; ph ^= 1u; }
+      // zero vectors of rows beyond nrow contribute nothing; u_j of such rows
+      // is read at a clamped, valid index
+      const int jt = j0 + (int)ro;
+#pragma unroll
+      for (int t = 0; t < RMAX; ++t) {
+        if (t >= nrow) break;
+        const int j = jt + t * (int)rpr;
+        if constexpr (ST == GROM_F64) {
+          double uj[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(ureg)[b * (int)np + j];
+#pragma unroll
+          for (int q = 0; q < QM; ++q) {
+            const double x0 = __hiloint2double((int)vec[t][q][0].y, (int)vec[t][q][0].x);
+            const double x1 = __hiloint2double((int)vec[t][q][0].w, (int)vec[t][q][0].z);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              uh[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
-              ul[b] = reinterpret_cast<const float*>(ureg)[(int64_t)NB * np + b * np + j];
+              acc[q][0][b].v = fma(x0, uj[b], acc[q][0][b].v);
+              acc[q][1][b].v = fma(x1, uj[b], acc[q][1][b].v);
             }
+          }
+        } else if constexpr (ST == GROM_F32X2) {
+          float uh[NB], ul[NB];
 #pragma unroll
-            for (int q = 0; q < QM; ++q) {
-              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
-              if (pos < P) {
-                const float4 h = *reinterpret_cast<const float4*>(rowp + pos * 16);
-                const float4 l = *reinterpret_cast<const float4*>(rowp + np * 4 + pos * 16);
+          for (int b = 0; b < NB; ++b) {
+            uh[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
+            ul[b] = reinterpret_cast<const float*>(ureg)[(NB + b) * (int)np + j];
+          }
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                  ds_fma(h.x, l.x, uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
-                  ds_fma(h.y, l.y, uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
-                  ds_fma(h.z, l.z, uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
-                  ds_fma(h.w, l.w, uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
-                }
-              }
+          for (int q = 0; q < QM; ++q) {
+            const uint4 h = vec[t][q][0];
+            const uint4 l = vec[t][q][PLANES - 1];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              ds_fma(__uint_as_float(h.x), __uint_as_float(l.x), uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
+              ds_fma(__uint_as_float(h.y), __uint_as_float(l.y), uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
+              ds_fma(__uint_as_float(h.z), __uint_as_float(l.z), uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
+              ds_fma(__uint_as_float(h.w), __uint_as_float(l.w), uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
             }
-          } else if constexpr (ST == GROM_F32) {
-            float uj[NB];
+          }
+        } else if constexpr (ST == GROM_F32) {
+          float uj[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
 #pragma unroll
-            for (int q = 0; q < QM; ++q) {
-              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
-              if (pos < P) {
-                const float4 x = *reinterpret_cast<const float4*>(rowp + pos * 16);
+          for (int q = 0; q < QM; ++q) {
+            const uint4 x = vec[t][q][0];
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                  acc[q][0][b].v = fmaf(x.x, uj[b], acc[q][0][b].v);
-                  acc[q][1][b].v = fmaf(x.y, uj[b], acc[q][1][b].v);
-                  acc[q][2][b].v = fmaf(x.z, uj[b], acc[q][2][b].v);
-                  acc[q][3][b].v = fmaf(x.w, uj[b], acc[q][3][b].v);
-                }
-              }
+            for (int b = 0; b < NB; ++b) {
+              acc[q][0][b].v = fmaf(__uint_as_float(x.x), uj[b], acc[q][0][b].v);
+              acc[q][1][b].v = fmaf(__uint_as_float(x.y), uj[b], acc[q][1][b].v);
+              acc[q][2][b].v = fmaf(__uint_as_float(x.z), uj[b], acc[q][2][b].v);
+              acc[q][3][b].v = fmaf(__uint_as_float(x.w), uj[b], acc[q][3][b].v);
             }
-          } else {  // BF16
-            float uj[NB];
+          }
+        } else {  // BF16
+          float uj[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
 #pragma unroll
-            for (int q = 0; q < QM; ++q) {
-              const int64_t pos = pos0 + (int64_t)q * K1_CONSUMERS;
-              if (pos < P) {
-                const uint4 w = *reinterpret_cast<const uint4*>(rowp + pos * 16);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+          for (int q = 0; q < QM; ++q) {
+            const uint32_t ws[4] = {vec[t][q][0].x, vec[t][q][0].y, vec[t][q][0].z, vec[t][q][0].w};
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                  const float x0 = __uint_as_float(ws[h] << 16);
-                  const float x1 = __uint_as_float(ws[h] & 0xffff0000u);
+            for (int h = 0; h < 4; ++h) {
+              const float x0 = __uint_as_float(ws[h] << 16);
+              const float x1 = __uint_as_float(ws[h] & 0xffff0000u);
 #pragma unroll
-                  for (int b = 0; b < NB; ++b) {
-                    acc[q][2 * h][b].v = fmaf(x0, uj[b], acc[q][2 * h][b].v);
-                    acc[q][2 * h + 1][b].v = fmaf(x1, uj[b], acc[q][2 * h + 1][b].v);
-                  }
-                }
+              for (int b = 0; b < NB; ++b) {
+                acc[q][2 * h][b].v = fmaf(x0, uj[b], acc[q][2 * h][b].v);
+                acc[q][2 * h + 1][b].v = fmaf(x1, uj[b], acc[q][2 * h + 1][b].v);
               }
             }
           }
         }
       }
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&empty[s]);
     }
     if (cur_i >= 0 && !*abort_flag) flush(cur_i);
   }
@@ -388,6 +421,7 @@ cudaError_t k1_launch_one(const K1Plan& pl, const K1Args& a, int b0, cudaStream_
   e = cudaGetLastError();
   if (e == cudaSuccess && a.ev1) e = cudaEventRecord(a.ev1, s);
   if (e != cudaSuccess) return e;
+  if (a.skip_finalize) return cudaSuccess;
   const int64_t total = pl.n * a.nb;
   k1_finalize_kernel<NB><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pl, a, b0);
   return cudaGetLastError();

@@ -149,10 +149,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     const float* urow = p.ub + bglob * p.np;
     float uk[64];
     int64_t cur_kb = -1;
+    // u_bj of the next K-tile is fetched one tile ahead to hide its latency
+    float uj_next = row_on ? urow[j0] : 0.f;
     for (int64_t t = 0; t < T; ++t) {
       const int r = (int)(t % SB);
       const uint32_t ph = (uint32_t)((t / SB) & 1);
-      const int64_t kb = t / nj, j = j0 + (t - kb * nj);
+      const int64_t kb = t / nj;
+      const float uj = uj_next;
+      if (row_on && t + 1 < T) {
+        const int64_t t1 = t + 1, kb1 = t1 / nj;
+        uj_next = urow[j0 + (t1 - kb1 * nj)];
+      }
       if (row_on && kb != cur_kb) {
         const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
 #pragma unroll
@@ -167,7 +174,6 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
         break;
       }
       if (row_on) {
-        const float uj = urow[j];
         uint8_t* row_hi = sb + (size_t)r * b_bytes + (size_t)g * 128;
         uint8_t* row_lo = row_hi + half_bytes;
 #pragma unroll

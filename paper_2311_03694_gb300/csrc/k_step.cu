@@ -109,6 +109,104 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_diag(const StepArgs a, co
   }
 }
 
+// Diagonal step spread over nblk CTAs per trajectory (STEP_MC_THREADS each).
+// Per-CTA energy/invariant partials are summed in CTA order by the last CTA
+// of the trajectory to arrive (arrival counter, no waiting), which also
+// advances the step count.  With k1 set, the K1 partials of the element are
+// summed first (the streaming kernel's finalize, fused).
+__global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs a, const int step_index,
+                                                                  const K1Plan pl, const K1Args k1a, const int fuse,
+                                                                  const int b0, const int nbk) {
+  __shared__ double sh[64];
+  __shared__ int bad;
+  __shared__ int last;
+  const int bl = blockIdx.y;      // trajectory within this launch
+  const int b = b0 + bl;          // trajectory index
+  if (a.active && !a.active[b]) return;
+  const int64_t n = a.n;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  double* h = a.hist + b * a.hist_stride;
+  const int64_t i = (int64_t)blockIdx.x * STEP_MC_THREADS + threadIdx.x;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  double e_part = 0.0, i_part = 0.0;
+  int my_bad = 0;
+  if (i < n) {
+    double nl;
+    if (fuse) {
+      // K1 finalize: partials of every CTA whose chunk range covers test index i, in CTA order
+      const int64_t G = pl.grid, T = pl.T;
+      const int64_t g_lo = ((i * pl.cpi + 1) * G - 1) / T, g_hi = (((i + 1) * pl.cpi) * G - 1) / T;
+      double sum = 0.0;
+      for (int64_t g = g_lo; g <= g_hi; ++g) {
+        const int64_t first_i = (g * T / G) / pl.cpi;
+        const double* src = k1a.part + ((g * pl.maxseg + (i - first_i)) * (K1_CONSUMERS / 32)) * nbk + bl;
+#pragma unroll
+        for (int w = 0; w < K1_CONSUMERS / 32; ++w) sum += src[w * nbk];
+      }
+      h[(3 + l % 3) * n + i] = sum;
+      nl = sum;
+    } else {
+      nl = h[(3 + l % 3) * n + i];
+    }
+    const double mb = a.mass_diag ? a.mass_diag[i] : 1.0;
+    const double ld = a.lin_diag ? a.lin_diag[i] : 0.0;
+    const double f = a.forcing ? a.forcing[i] : 0.0;
+    const double inv_dt = 1.0 / a.dt;
+    double ext = 0.0, bdf = 0.0, u0 = 0.0;
+    for (int q = 0; q < k; ++q) {
+      const int64_t m = ((l - q) % 3 + 3) % 3;
+      const double uq = h[m * n + i];
+      const double nq = q == 0 ? nl : h[(3 + m) * n + i];
+      if (q == 0) u0 = uq;
+      ext += c_alpha[k - 1][q] * (nq + ld * uq + f);
+      bdf += c_beta[k - 1][q + 1] * inv_dt * uq;
+    }
+    const double un = (-ext - mb * bdf) * a.hdiag[k - 1][i];
+    i_part = u0 * nl;
+    e_part = mb * un * un;
+    my_bad = !isfinite(un);
+    h[((l + 1) % 3) * n + i] = un;
+  }
+  if (my_bad) bad = 1;
+  block_sum2(e_part, i_part, sh);
+  if (threadIdx.x == 0) {
+    if (bad) report_nonfinite(a, b);
+    double* r = a.red + ((int64_t)b * a.nblk + blockIdx.x) * 2;
+    r[0] = e_part;
+    r[1] = i_part;
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.cnt[b], 1u);
+    last = prev == (unsigned)(a.nblk - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double e = 0.0, inv = 0.0;
+    const double* r = a.red + (int64_t)b * a.nblk * 2;
+    for (int q = 0; q < a.nblk; ++q) {
+      e += __ldcg(r + 2 * q);
+      inv += __ldcg(r + 2 * q + 1);
+    }
+    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e;
+    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = inv;
+    a.taken[b] = l + 1;
+    a.cnt[b] = 0u;
+  }
+}
+
+cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
+                                int nbk, cudaStream_t s) {
+  dim3 grid((unsigned)a.nblk, (unsigned)nb);
+  K1Plan pl{};
+  K1Args ka{};
+  if (k1) pl = *k1;
+  if (k1a) ka = *k1a;
+  k_step_diag_mc<<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, pl, ka, k1 ? 1 : 0, b0, nbk);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ dense path
 // work layout per trajectory: [y | t | z | v] (n each)
 
@@ -222,6 +320,7 @@ __global__ void k_step_hdiag(const StepArgs a) {
 
 cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index, cudaStream_t s) {
   if (diagonal) {
+    if (a.red) return step_diag_mc_launch(a, step_index, nullptr, nullptr, 0, a.batch, 1, s);
     k_step_diag<<<a.batch, STEP_THREADS, 0, s>>>(a, step_index);
     return cudaGetLastError();
   }
