@@ -59,6 +59,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('none' to skip)")
+    p.add_argument("--serve-requests", type=int, default=10000, help="serving-mix requests (0 to skip)")
+    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--serve-slots", type=int, default=64)
     p.add_argument("--json-out", default="")
     return p.parse_args()
 
@@ -193,8 +196,118 @@ def time_variant(grom, torch, rom, u0, steps, warmup, flush=None):
     return ms, code, per
 
 
+def max_over_ranks(ms, device="cuda"):
+    """Largest per-step time over all ranks (every rank gets it)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ms, world):
+    """Steps per second of all replicas together, each stepping one trajectory."""
+    return world * 1e3 / ms
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ----------------------------------------------------------------- serving
+def serving_section(args, grom, synth, torch, a_of):
+    """Serving mix: four resident ROMs N = 128, 256, 512, 1024, each with skew
+    CP factor sets of rank N and N/2 (the leading N/2 columns) in BF16 and
+    FP64, served with continuous batching; compared with plain per-request
+    FP64 full G-ROM stepping (one trajectory at a time, measured step times,
+    FIFO queue)."""
+    seed = synth.seed_for(4)
+    ns = [128, 256, 512, 1024]
+    roms, keys, streams, fulls = [], [], [], {}
+    srv = grom.Server(150 * 2 ** 30, quantum=16)
+    for n in ns:
+        U, V, W, resid, _ = synth.cp_workload(n, n, 4)
+        a = a_of(n)
+        for R in (n // 2, n):
+            for storage in ("bf16", "f64"):
+                st = torch.cuda.Stream()
+                streams.append(st)
+                fac = tuple(np.ascontiguousarray(x[:, :R]) for x in (U, V, W))
+                rom = grom.Rom(n, "cp_skew", storage, factors=fac, stiffness=a, nu=NU, dt=DT,
+                               max_batch=args.serve_slots, stream=st)
+                roms.append(rom)
+                keys.append((n, R, storage))
+                srv.add_rom(rom, args.serve_slots)
+        fulls[n] = (U, V, W, resid)
+    times, horizons, draws = synth.arrivals(args.serve_requests, args.serve_rate, seed)
+    nidx = (draws % 4).astype(int)
+    vidx = ((draws // 4) % 4).astype(int)
+    models = nidx * 4 + vidx
+    u0s = [synth.initial_condition(ns[nidx[q]], seed, traj=q)[0] for q in range(len(models))]
+    out = srv.serve(models, horizons, times, u0s, want_final=True)
+    lat = out["t_done"] - times
+    stats = out["stats"]
+    res = {"requests": int(len(models)), "rate_per_s": args.serve_rate, "slots_per_rom": args.serve_slots,
+           "roms": len(roms), "quantum_steps": 16, "hbm_budget_gb": 150,
+           "status_ok": int(np.sum(out["status"] == 0)),
+           "trajectory_steps": int(stats["trajectory_steps"]), "seconds": stats["seconds"],
+           "steps_per_s": stats["trajectory_steps"] / stats["seconds"],
+           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+           "peak_active": int(stats["peak_active"]), "peak_gb": stats["peak_bytes"] / 1e9}
+    # plain per-request FP64 full G-ROM: single-trajectory step time per N
+    step_ms = {}
+    finals_full = {}
+    order = np.argsort(horizons)
+    sample = list(order[:8])
+    for n in ns:
+        U, V, W, resid = fulls[n]
+        Cn = synth.cp_tensor_device(U, V, W, seed, resid, "cuda")
+        full_rom = grom.Rom(n, "full", "f64", tensor=Cn, stiffness=a_of(n), nu=NU, dt=DT)
+        del Cn
+        tr = grom.Trajectories(full_rom, synth.initial_condition(n, seed, 0))
+        tr.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        tr.step(24)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        step_ms[n] = e0.elapsed_time(e1) / 24
+        tr.close()
+        for q in sample:
+            if ns[nidx[q]] == n:
+                t1 = grom.Trajectories(full_rom, u0s[q][None, :])
+                t1.step(int(horizons[q]))
+                finals_full[q] = t1.get_state()[0][:n]
+                t1.close()
+        full_rom.close()
+        torch.cuda.empty_cache()
+    # FIFO queue of one-at-a-time requests with the measured step times
+    end = 0.0
+    blat = np.empty(len(models))
+    for q in np.argsort(times, kind="stable"):
+        start = max(times[q], end)
+        end = start + horizons[q] * step_ms[ns[nidx[q]]] * 1e-3
+        blat[q] = end - times[q]
+    res["baseline_fp64_full_per_request"] = {
+        "steps_per_s": float(horizons.sum() / (end - times.min())),
+        "p50_latency_s": float(np.percentile(blat, 50)), "p99_latency_s": float(np.percentile(blat, 99)),
+        "step_ms_by_n": {str(k): v for k, v in step_ms.items()},
+        "how": "measured single-trajectory FP64 full step time per N; requests served one at a time in arrival order"}
+    errs = {}
+    for q, ref in finals_full.items():
+        n, R, storage = keys[models[q]]
+        errs.setdefault("%s_R%s" % (storage, "N" if R == n else "N/2"), []).append(rel(out["final"][q], ref))
+    res["final_state_rel_err_vs_fp64_full"] = {k: float(max(v)) for k, v in errs.items()}
+    res["final_state_error_sample"] = "%d shortest-horizon requests, final state vs the same request on the " \
+                                      "FP64 full G-ROM (model gap + precision)" % len(finals_full)
+    srv.close()
+    for rom in roms:
+        rom.close()
+    return res
 
 
 # --------------------------------------------------------------- reference
@@ -318,11 +431,8 @@ def main():
     rom.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
     code, bad = tr.status()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1e3 / ms  # all replicas' steps per second
+    ms = max_over_ranks(ms)
+    value = replica_throughput(ms, world)  # all replicas' steps per second
 
     # roofline of the dominant kernel (K1 streaming contraction)
     k1_avg_ms = k1_ms / max(1, k1_launches)
@@ -437,6 +547,24 @@ def main():
             batched["B%d" % B] = entry
             btr.close()
             brom.close()
+            # the CPD-ROM (skew CP factors, rank N) on the same batch
+            for storage in ("bf16", "f64"):
+                crom = grom.Rom(n, "cp_skew", storage, factors=factors, stiffness=a, nu=NU, dt=DT, max_batch=B)
+                ctr = grom.Trajectories(crom, U0)
+                ctr.step(2)
+                torch.cuda.synchronize()
+                e0b.record(stream)
+                ctr.step(bsteps)
+                e1b.record(stream)
+                torch.cuda.synchronize()
+                cms = e0b.elapsed_time(e1b) / bsteps
+                cflops = 2.0 * 5 * n * R * B  # p, q, s projections and two expansions
+                batched["B%d_cpd_%s" % (B, storage)] = {
+                    "ms_per_step": cms, "trajectory_steps_per_s": B * 1e3 / cms,
+                    "alg_tflops": cflops / (cms * 1e-3) / 1e12,
+                    "kernel": "k3g project/expand (register-tiled GEMMs)" if B >= 16 else "k3 project/expand"}
+                ctr.close()
+                crom.close()
 
     # ---------------------------------------------- CPU baseline (oracle)
     if rank_id == 0 and not args.no_cpu_baseline:
@@ -466,6 +594,13 @@ def main():
             vrom.close()
         errors["oracle_full_eval_seconds"] = t_ref
 
+    # ------------------------------------------------------ serving mix
+    serving = None
+    if args.serve_requests > 0 and rank_id == 0:
+        del C
+        torch.cuda.empty_cache()
+        serving = serving_section(args, grom, synth, torch, a_of=synth.diag_stiffness)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -479,6 +614,7 @@ def main():
         "status": grom.ERRORS.get(code, "OK") if code else "OK",
         "variants": variants,
         "batched": batched,
+        "serving": serving,
     }
     if errors:
         line["oracle"] = errors

@@ -175,6 +175,66 @@ int64_t grom_rom_bytes(const grom_rom* rom);
                                 (BF16 storage only)                                          */
 grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
 
+/* ------------------------------------------------------------ serving
+ * A server keeps several ROMs resident and steps trajectory requests as they
+ * arrive, with continuous batching: each ROM owns a pool of max_slots
+ * trajectory slots stepped together by the batched kernels (inactive slots
+ * are skipped); a request is admitted into a free slot of its ROM as soon as
+ * one is free and its state fits the HBM budget, is stepped in scheduling
+ * quanta alongside whatever else is resident, and leaves (its final state
+ * copied to the host, its slot and memory released) after its horizon.  The
+ * ROMs step concurrently when they were created on different streams. */
+typedef struct grom_server grom_server;
+
+typedef struct grom_request {
+  int32_t model;    /* id returned by grom_server_add_rom / _add_simulated       */
+  int32_t horizon;  /* steps to take, >= 1                                       */
+  double arrival;   /* seconds after the start of grom_serve                     */
+  const double* u0; /* n doubles, host: initial state                            */
+  double* u_final;  /* n doubles, host, or NULL: final state                     */
+} grom_request;
+
+typedef struct grom_result {
+  int32_t status;   /* GROM_OK, GROM_ERR_NONFINITE (final state not finite) or
+                       GROM_ERR_BUDGET (the request can never fit the budget)    */
+  int32_t steps;    /* steps taken                                                */
+  double t_admit;   /* seconds after start: slot and memory granted               */
+  double t_done;    /* seconds after start: final state on the host               */
+} grom_result;
+
+typedef struct grom_serve_stats {
+  int64_t trajectory_steps; /* steps taken by all requests                       */
+  int64_t quanta;           /* scheduling rounds                                 */
+  double seconds;           /* duration of grom_serve                            */
+  int64_t peak_bytes;       /* peak charged footprint (models + admitted states) */
+  int32_t peak_active;      /* peak number of concurrently stepped trajectories  */
+  int32_t reserved;
+} grom_serve_stats;
+
+/* hbm_budget_bytes caps the footprint charged for resident models and
+ * admitted trajectory states; quantum_steps (a multiple of 8 is best) is the
+ * number of steps each ROM advances between scheduling decisions.  With
+ * simulate = 1 nothing runs on a GPU: models are added with
+ * grom_server_add_simulated and a quantum costs quantum_steps * step_seconds
+ * of virtual time (for testing the scheduler). */
+grom_status grom_server_create(int64_t hbm_budget_bytes, int32_t quantum_steps, int32_t simulate,
+                               grom_server** out);
+/* Makes `rom` resident with a pool of max_slots slots (max_slots <= the ROM's
+ * max_batch).  Charged: the ROM's bytes plus the pool; GROM_ERR_BUDGET if it
+ * does not fit.  The ROM must outlive the server. */
+grom_status grom_server_add_rom(grom_server* s, grom_rom* rom, int32_t max_slots, int32_t* model);
+/* Simulation mode only: a model of n modes occupying rom_bytes whose batched
+ * step takes step_seconds. */
+grom_status grom_server_add_simulated(grom_server* s, int32_t n, int64_t rom_bytes, int32_t max_slots,
+                                      double step_seconds, int32_t* model);
+/* Runs the requests to completion in real time (arrival times are honoured;
+ * simulation mode uses virtual time) and fills results[count].  Each
+ * admitted request is charged 8 * (7 n + 4) bytes of trajectory state.
+ * stats is nullable. */
+grom_status grom_serve(grom_server* s, const grom_request* reqs, int32_t count, grom_result* results,
+                       grom_serve_stats* stats);
+grom_status grom_server_destroy(grom_server* s);
+
 /* Kernel timing: while enabled, the library records CUDA events on the ROM's
  * stream around every launch of its main contraction kernel (K1 streaming
  * kernel for the full form, the CP projection+expansion for CP forms).

@@ -22,6 +22,21 @@ STORAGE = {"f64": 0, "f32x2": 1, "f32": 2, "bf16": 3}
 STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("horizon", ctypes.c_int32), ("arrival", ctypes.c_double),
+                ("u0", ctypes.c_void_p), ("u_final", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("trajectory_steps", ctypes.c_int64), ("quanta", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("peak_bytes", ctypes.c_int64), ("peak_active", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class GromError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s: %s" % (ERRORS.get(code, code), msg))
@@ -65,6 +80,15 @@ EXPORTS = {
                           ctypes.c_int32),
     "grom_nonlinear_full_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+                           ctypes.c_int32),
+    "grom_server_add_rom": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+                            ctypes.c_int32),
+    "grom_server_add_simulated": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_int32)], ctypes.c_int32),
+    "grom_serve": ([ctypes.c_void_p, ctypes.POINTER(_Request), ctypes.c_int32, ctypes.POINTER(_Result),
+                    ctypes.POINTER(_Stats)], ctypes.c_int32),
+    "grom_server_destroy": ([ctypes.c_void_p], ctypes.c_int32),
     "grom_last_error": ([], ctypes.c_char_p),
 }
 
@@ -296,6 +320,73 @@ class Trajectories:
     def close(self):
         if getattr(self, "_h", None):
             _check(load().grom_traj_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over resident ROMs (grom_server_*, grom_serve).
+
+    simulate=True runs the scheduler without a GPU (models added with
+    add_simulated cost step_seconds of virtual time per batched step).
+    """
+
+    def __init__(self, budget_bytes, quantum=16, simulate=False):
+        h = ctypes.c_void_p()
+        _check(load().grom_server_create(int(budget_bytes), int(quantum), 1 if simulate else 0, ctypes.byref(h)))
+        self._h = h
+        self._roms = []
+        self.n = []
+
+    def add_rom(self, rom, max_slots):
+        mid = ctypes.c_int32()
+        _check(load().grom_server_add_rom(self._h, rom.handle, int(max_slots), ctypes.byref(mid)))
+        self._roms.append(rom)
+        self.n.append(rom.n)
+        return mid.value
+
+    def add_simulated(self, n, rom_bytes, max_slots, step_seconds):
+        mid = ctypes.c_int32()
+        _check(load().grom_server_add_simulated(self._h, int(n), int(rom_bytes), int(max_slots), float(step_seconds),
+                                                ctypes.byref(mid)))
+        self.n.append(int(n))
+        return mid.value
+
+    def serve(self, models, horizons, arrivals, u0s, want_final=False):
+        """Run requests (model id, horizon, arrival time, initial state) to completion.
+
+        Returns a dict of numpy arrays (status, steps, t_admit, t_done), the
+        final states when want_final, and the run statistics."""
+        count = len(models)
+        reqs = (_Request * max(count, 1))()
+        finals = []
+        keep = []
+        for q in range(count):
+            u0 = np.ascontiguousarray(u0s[q], dtype=np.float64)
+            keep.append(u0)
+            reqs[q].model, reqs[q].horizon, reqs[q].arrival = int(models[q]), int(horizons[q]), float(arrivals[q])
+            reqs[q].u0 = u0.ctypes.data
+            if want_final:
+                f = np.empty(self.n[int(models[q])])
+                finals.append(f)
+                reqs[q].u_final = f.ctypes.data
+        res = (_Result * max(count, 1))()
+        st = _Stats()
+        _check(load().grom_serve(self._h, reqs, count, res, ctypes.byref(st)))
+        out = {k: np.array([getattr(res[q], k) for q in range(count)]) for k in ("status", "steps", "t_admit", "t_done")}
+        out["final"] = finals
+        out["stats"] = {k: getattr(st, k) for k in ("trajectory_steps", "quanta", "seconds", "peak_bytes",
+                                                    "peak_active")}
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load().grom_server_destroy(self._h))
             self._h = None
 
     def __del__(self):

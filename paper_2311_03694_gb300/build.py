@@ -21,6 +21,7 @@ SOURCES = [
     "k_convert.cu",
     "k_step.cu",
     "k3_cp.cu",
+    "k3_gemm.cu",
     "k1_plan.cu",
     "k1_f64.cu",
     "k1_f32x2.cu",
@@ -28,6 +29,7 @@ SOURCES = [
     "k1_bf16.cu",
     "k1_static.cu",
     "k2_tc.cu",
+    "serve.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]

@@ -114,7 +114,7 @@ static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int
 static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
-                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch};
+                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -149,6 +149,10 @@ static bool use_k2(const grom_rom* r, int batch) {
   if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
   if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
   return batch > 8;
+}
+
+static bool use_k3g(const grom_rom* r, int batch) {
+  return r->form != GROM_FORM_FULL && batch >= K3G_MIN_BATCH && r->k3g_scratch;
 }
 
 static K1Args k1_args(grom_rom* r) {
@@ -282,6 +286,17 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
         return bail(st);
     r->part_bytes = k3_scratch_bytes(r->k3, r->storage);
     if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
+    if (r->max_batch >= K3G_MIN_BATCH &&
+        (st = dmalloc(&r->k3g_scratch, k3g_scratch_bytes(n, rp, r->max_batch, r->storage, r->sm_count),
+                      &r->total_bytes)))
+      return bail(st);
+    if (r->k3g_scratch && cudaMemsetAsync(r->k3g_scratch, 0,
+                                          k3g_scratch_bytes(n, rp, r->max_batch, r->storage, r->sm_count),
+                                          r->stream) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    // the per-tile arrival counters of the projection kernel start at zero
+    if (cudaMemsetAsync(r->part, 0, r->part_bytes, r->stream) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "grom_create"));
   }
 
   // ------------------------------------------------------ linear operators
@@ -413,7 +428,8 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     cudaEvent_t e0, e1;
     if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
     if (e0) cudaEventRecord(e0, r->stream);
-    e = k3_launch(r->k3, r->storage, a, batch, r->stream);
+    e = use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
+                          : k3_launch(r->k3, r->storage, a, batch, r->stream);
     if (e1) cudaEventRecord(e1, r->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear launch");
@@ -447,7 +463,7 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
   if ((st = dmalloc(&t->err, 2 * sizeof(int), nullptr))) return bail(st);
   if ((st = dmalloc(&t->io, (size_t)batch * n * sizeof(double), nullptr))) return bail(st);
   if (r->diagonal) {
-    const int nblk = step_mc_blocks(n);
+    const int nblk = std::max(step_mc_blocks(n), k3_expand_blocks(n));
     if ((st = dmalloc(&t->red, (size_t)batch * nblk * 2 * sizeof(double), nullptr))) return bail(st);
     if ((st = dmalloc(&t->cnt, (size_t)batch * sizeof(unsigned int), nullptr))) return bail(st);
     if (cudaMemsetAsync(t->cnt, 0, (size_t)batch * sizeof(unsigned int), r->stream) != cudaSuccess)
@@ -481,6 +497,8 @@ grom_status grom_traj_destroy(grom_traj* t) {
   if (t->gstream) cudaStreamDestroy(t->gstream);
   if (t->ev_in) cudaEventDestroy(t->ev_in);
   if (t->ev_out) cudaEventDestroy(t->ev_out);
+  if (t->active) cudaFree(t->active);
+  if (t->steps_left) cudaFree(t->steps_left);
   --t->rom->traj_count;
   delete t;
   return GROM_OK;
@@ -493,6 +511,7 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.hist = t->hist;
     a.taken = t->taken;
     a.hist_stride = 6 * (int64_t)r->n;
+    a.active = t->active;
     a.batch = t->batch;
     a.scratch = r->k2_scratch;
     a.err = r->err;
@@ -504,6 +523,7 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.hist = t->hist;
     a.taken = t->taken;
     a.hist_stride = 6 * (int64_t)r->n;
+    a.active = t->active;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
     return k1_launch(r->k1, r->storage, a, t->batch, strm);
   }
@@ -511,10 +531,12 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   a.hist = t->hist;
   a.taken = t->taken;
   a.hist_stride = 6 * (int64_t)r->n;
+  a.active = t->active;
   cudaEvent_t e0, e1;
   if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
   if (e0) cudaEventRecord(e0, strm);
-  cudaError_t e = k3_launch(r->k3, r->storage, a, t->batch, strm);
+  cudaError_t e = use_k3g(r, t->batch) ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
+                                       : k3_launch(r->k3, r->storage, a, t->batch, strm);
   if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, strm);
   return e;
 }
@@ -547,6 +569,9 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
   a.red = t->red;
   a.cnt = t->cnt;
   a.nblk = step_mc_blocks(r->n);
+  a.active = t->active;
+  a.active_rw = t->active;
+  a.steps_left = t->steps_left;
   return a;
 }
 
@@ -555,13 +580,28 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   grom_rom* r = t->rom;
   StepArgs a = step_args(t, energy, invariant);
   const bool fused_k1 = r->diagonal && r->form == GROM_FORM_FULL && !use_k2(r, t->batch);
+  const bool fused_k3 = r->diagonal && r->form != GROM_FORM_FULL && !use_k3g(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
-    if (fused_k1) {
+    if (fused_k3) {
+      K3Args k = k3_args(r);
+      k.hist = t->hist;
+      k.taken = t->taken;
+      k.hist_stride = 6 * (int64_t)r->n;
+      k.active = t->active;
+      StepArgs st3 = a;
+      st3.nblk = k3_expand_blocks(r->n);
+      cudaEvent_t e0, e1;
+      if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
+      if (e0) cudaEventRecord(e0, strm);
+      e = k3_launch_step(r->k3, r->storage, k, t->batch, &st3, s, strm);
+      if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, strm);
+    } else if (fused_k1) {
       K1Args k = k1_args(r);
       k.hist = t->hist;
       k.taken = t->taken;
       k.hist_stride = 6 * (int64_t)r->n;
+      k.active = t->active;
       if (!prof_pair(r, &k.ev0, &k.ev1)) return cudaErrorMemoryAllocation;
       e = k1_launch_fused_step(r->k1, r->storage, k, a, t->batch, s, strm);
     } else {

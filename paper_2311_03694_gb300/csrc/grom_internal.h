@@ -144,6 +144,16 @@ struct K3Args {
 };
 K3Plan k3_plan(int64_t n, int64_t r, int storage, int sm_count);
 cudaError_t k3_launch(const K3Plan& plan, int storage, const K3Args& a, int batch, cudaStream_t s);
+struct StepArgs;
+// CP evaluation with the diagonal step fused into the expansion kernel.
+cudaError_t k3_launch_step(const K3Plan& p, int storage, const K3Args& a0, int batch, const StepArgs* st,
+                           int step_index, cudaStream_t s);
+int k3_expand_blocks(int64_t n);
+// Batched CP form as register-tiled GEMMs (batches of 16 or more).
+size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int sm_count);
+cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
+                       int sm_count, cudaStream_t s);
+constexpr int K3G_MIN_BATCH = 16;
 
 // --------------------------------------------------------------- stepper
 struct StepArgs {
@@ -174,7 +184,21 @@ struct StepArgs {
   double* red;              // batch x nblk x 2
   unsigned int* cnt;        // batch (zero between launches)
   int nblk;                 // CTAs per trajectory
+  // serving: per-trajectory remaining steps; a trajectory whose count
+  // reaches zero is deactivated (active[b] = 0) by the step that ends it
+  int32_t* steps_left;      // nullable
+  int32_t* active_rw;       // writable view of `active` (same array)
 };
+// Ends the step of trajectory b: advance its count, retire it when its
+// serving budget runs out.
+__device__ __forceinline__ void step_done(const StepArgs& a, int b, int64_t l) {
+  a.taken[b] = l + 1;
+  if (a.steps_left) {
+    const int32_t left = a.steps_left[b] - 1;
+    a.steps_left[b] = left;
+    if (left <= 0) a.active_rw[b] = 0;
+  }
+}
 constexpr int STEP_MC_THREADS = 128;
 inline int step_mc_blocks(int64_t n) { return (int)((n + STEP_MC_THREADS - 1) / STEP_MC_THREADS); }
 // Diagonal step over several CTAs per trajectory.  With k1 != nullptr the
@@ -184,7 +208,9 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
                                 int nbk, cudaStream_t s);
 cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch,
                                  int step_index, cudaStream_t s);
-cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s);
+cudaError_t slot_admit_launch(double* hist, int64_t* taken, int32_t* steps_left, int32_t* active, int64_t n,
+                              int count, const int32_t* slots, const int32_t* horizons, const double* u0s,
+                              cudaStream_t s);
 // Copies u (batch x n, device) into / out of the newest-state slot of the ring.
 cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int batch, double* u, bool inject,
                             cudaStream_t s);
@@ -229,6 +255,7 @@ struct grom_rom {
   bool k2_ok = false;                // tensor map built (BF16 full form)
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
+  void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
   size_t k2_scratch_bytes = 0;
   bool prof = false;                 // kernel timing enabled
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
@@ -250,4 +277,6 @@ struct grom_traj {
   int graph_version = -1;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int32_t* active = nullptr;      // serving slots: 1 = occupied (nullable: all active)
+  int32_t* steps_left = nullptr;  // serving slots: remaining steps
 };

@@ -55,60 +55,6 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
   atomicMin(a.first_bad, b);
 }
 
-// Fused step for diagonal A, B (or identity) and L: one CTA per trajectory.
-__global__ void __launch_bounds__(STEP_THREADS) k_step_diag(const StepArgs a, const int step_index) {
-  __shared__ double sh[64];
-  __shared__ int bad;
-  const int b = blockIdx.x;
-  if (a.active && !a.active[b]) return;
-  const int64_t n = a.n;
-  const int64_t l = a.taken[b];
-  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
-  double* h = a.hist + b * a.hist_stride;
-  const double* u_old[3];
-  const double* n_old[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int64_t m = ((l - q) % 3 + 3) % 3;
-    u_old[q] = h + m * n;
-    n_old[q] = h + (3 + m) * n;
-  }
-  double* u_new = h + ((l + 1) % 3) * n;
-  const double* hd = a.hdiag[k - 1];
-  const double inv_dt = 1.0 / a.dt;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  double e_part = 0.0, i_part = 0.0;
-  int my_bad = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double mb = a.mass_diag ? a.mass_diag[i] : 1.0;
-    const double ld = a.lin_diag ? a.lin_diag[i] : 0.0;
-    const double f = a.forcing ? a.forcing[i] : 0.0;
-    double ext = 0.0, bdf = 0.0;
-    double uq[3];
-    for (int q = 0; q < k; ++q) {
-      uq[q] = u_old[q][i];
-      ext += c_alpha[k - 1][q] * (n_old[q][i] + ld * uq[q] + f);
-      bdf += c_beta[k - 1][q + 1] * inv_dt * uq[q];
-    }
-    const double rhs = -ext - mb * bdf;
-    const double un = rhs * hd[i];
-    i_part += uq[0] * n_old[0][i];
-    e_part += mb * un * un;
-    if (!isfinite(un)) my_bad = 1;
-    u_new[i] = un;
-  }
-  if (my_bad) bad = 1;
-  block_sum2(e_part, i_part, sh);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e_part;
-    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = i_part;
-    if (bad) report_nonfinite(a, b);
-    a.taken[b] = l + 1;
-  }
-}
-
 // Diagonal step spread over nblk CTAs per trajectory (STEP_MC_THREADS each).
 // Per-CTA energy/invariant partials are summed in CTA order by the last CTA
 // of the trajectory to arrive (arrival counter, no waiting), which also
@@ -191,7 +137,7 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
     }
     if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e;
     if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = inv;
-    a.taken[b] = l + 1;
+    step_done(a, b, l);
     a.cnt[b] = 0u;
   }
 }
@@ -301,7 +247,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_finish(const StepArgs a, 
     if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e_part;
     if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = i_part;
     if (bad) report_nonfinite(a, b);
-    a.taken[b] = l + 1;
+    step_done(a, b, l);
   }
 }
 
@@ -319,11 +265,7 @@ __global__ void k_step_hdiag(const StepArgs a) {
 }
 
 cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index, cudaStream_t s) {
-  if (diagonal) {
-    if (a.red) return step_diag_mc_launch(a, step_index, nullptr, nullptr, 0, a.batch, 1, s);
-    k_step_diag<<<a.batch, STEP_THREADS, 0, s>>>(a, step_index);
-    return cudaGetLastError();
-  }
+  if (diagonal) return step_diag_mc_launch(a, step_index, nullptr, nullptr, 0, a.batch, 1, s);
   const int64_t n = a.n;
   dim3 ge((unsigned)((n + 255) / 256), (unsigned)a.batch);
   dim3 gw((unsigned)((n + 7) / 8), (unsigned)a.batch);
@@ -338,6 +280,32 @@ cudaError_t step_launch_indexed(const StepArgs& a, bool diagonal, int step_index
   }
   if (a.mass) k_step_gemv<<<gw, 256, 0, s>>>(a, 3);
   k_step_finish<<<a.batch, STEP_THREADS, 0, s>>>(a, step_index, (hdense || a.mass) ? 0 : 1);
+  return cudaGetLastError();
+}
+
+// Serving admission: slot slots[q] gets the initial state u0s[q] (no steps
+// taken, empty history), a budget of horizons[q] steps and is activated.
+__global__ void k_slot_admit(double* hist, int64_t* taken, int32_t* steps_left, int32_t* active, int64_t n,
+                             int count, const int32_t* slots, const int32_t* horizons, const double* u0s) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * 6 * n) return;
+  const int q = (int)(t / (6 * n));
+  const int64_t e = t - (int64_t)q * 6 * n;
+  const int b = slots[q];
+  hist[(int64_t)b * 6 * n + e] = e < n ? u0s[(int64_t)q * n + e] : 0.0;
+  if (e == 0) {
+    taken[b] = 0;
+    steps_left[b] = horizons[q];
+    active[b] = 1;
+  }
+}
+
+cudaError_t slot_admit_launch(double* hist, int64_t* taken, int32_t* steps_left, int32_t* active, int64_t n,
+                              int count, const int32_t* slots, const int32_t* horizons, const double* u0s,
+                              cudaStream_t s) {
+  const int64_t total = (int64_t)count * 6 * n;
+  k_slot_admit<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(hist, taken, steps_left, active, n, count, slots,
+                                                               horizons, u0s);
   return cudaGetLastError();
 }
 
@@ -359,8 +327,5 @@ cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int b
   return cudaGetLastError();
 }
 
-cudaError_t step_launch(const StepArgs& a, bool diagonal, cudaStream_t s) {
-  return step_launch_indexed(a, diagonal, 0, s);
-}
 
 }  // namespace grom

@@ -327,3 +327,52 @@ def test_invalid_arguments_are_rejected():
     u = torch.zeros((3, n), dtype=torch.float64, device="cuda")
     with pytest.raises(grom.GromError):
         rom.nonlinear(u, torch.empty_like(u))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("form", ["cp", "cp_skew"])
+@pytest.mark.parametrize("batch", [16, 37, 70])
+def test_cp_batched_gemm_path(storage, form, batch, rng):
+    # batches of 16 or more run the register-tiled GEMM kernels
+    n, r = 75, 29
+    if form == "cp_skew":
+        U, V, W, _, seed = synth.cp_workload(n, r, 1)
+        factors = (U, V, W)
+        ref_fn = lambda u: oracle.nonlinear_cp_skew(U, V, W, u)
+    else:
+        factors = tuple(rng.standard_normal((n, r)) / np.sqrt(r) for _ in range(3))
+        ref_fn = lambda u: oracle.nonlinear_cp(*factors, u)
+    U0 = synth.initial_condition(n, 9, 0, batch)
+    rom = grom.Rom(n, form, storage, factors=factors, stiffness=synth.diag_stiffness(n), max_batch=batch)
+    c = _eval(rom, U0)
+    for b in range(batch):
+        assert _rel(c[b], ref_fn(U0[b])) <= TOL[storage], (storage, form, batch, b)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("bf16", 2e-2)])
+def test_cp_batched_stepping_matches_oracle(storage, tol):
+    n, r, batch, steps = 64, 24, 20, 30
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, seed, 0, batch)
+    rom = grom.Rom(n, "cp_skew", storage, factors=(U, V, W), stiffness=a, max_batch=batch)
+    tr = grom.Trajectories(rom, U0)
+    tr.step(steps)
+    H = tr.get_state()
+    for b in (0, 11, batch - 1):
+        ref = oracle.Rom("cp_skew", n, a, 1e-2, 1e-3, factors=(U, V, W))
+        h = ref.initial_history(U0[b])
+        ref.step(h, steps)
+        assert _rel(H[b][:n], h[:n]) <= tol
+
+
+def test_cp_batched_varying_batch_sizes_share_scratch():
+    # one ROM, batches of different sizes in turn (split counts differ)
+    n, r, mb = 96, 40, 70
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    rom = grom.Rom(n, "cp_skew", "f64", factors=(U, V, W), stiffness=synth.diag_stiffness(n), max_batch=mb)
+    for batch in (70, 20, 41, 16, 70):
+        U0 = synth.initial_condition(n, batch, 0, batch)
+        c = _eval(rom, U0)
+        for b in (0, batch // 2, batch - 1):
+            assert _rel(c[b], oracle.nonlinear_cp_skew(U, V, W, U0[b])) <= 1e-12, (batch, b)
