@@ -273,6 +273,13 @@ grom_status grom_profile_read(grom_rom* rom, double* total_ms, int64_t* launches
 grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, const void* tensor, const double* u,
                                         double* c, void* stream);
 
+/* Self-test of failure detection: enqueues on the ROM's stream a kernel that
+ * waits on a device barrier nothing ever signals, through the same bounded
+ * wait the library's kernels use, with a limit of limit_ns.  The wait gives
+ * up and raises the ROM's timeout flag, so the next grom_sync returns
+ * GROM_ERR_TIMEOUT (once); the ROM stays usable.  Faults nothing. */
+grom_status grom_selftest_timeout(grom_rom* rom, int64_t limit_ns);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* grom_last_error(void);
 

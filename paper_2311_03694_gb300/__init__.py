@@ -89,6 +89,7 @@ EXPORTS = {
     "grom_serve": ([ctypes.c_void_p, ctypes.POINTER(_Request), ctypes.c_int32, ctypes.POINTER(_Result),
                     ctypes.POINTER(_Stats)], ctypes.c_int32),
     "grom_server_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "grom_selftest_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "grom_last_error": ([], ctypes.c_char_p),
 }
 
@@ -253,6 +254,10 @@ class Rom:
 
     def sync(self):
         _check(load().grom_sync(self._h))
+
+    def selftest_timeout(self, limit_ns):
+        """Run a bounded device wait that nothing signals (see grom_selftest_timeout)."""
+        _check(load().grom_selftest_timeout(self._h, int(limit_ns)))
 
     def set_kernel(self, kernel):
         """Override the dense-contraction kernel: "auto", "stream" (K1) or "tensor" (K2)."""

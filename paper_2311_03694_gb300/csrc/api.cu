@@ -389,7 +389,17 @@ grom_status grom_sync(grom_rom* r) {
   GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
   int flags[2] = {0, 0};
   GROM_CUDA_TRY(cudaMemcpy(flags, r->err, sizeof(flags), cudaMemcpyDeviceToHost));
-  if (flags[0] & DEV_ERR_TIMEOUT) return fail(GROM_ERR_TIMEOUT, "a device-side wait timed out");
+  if (flags[0] & DEV_ERR_TIMEOUT) {
+    // reported once; the ROM stays usable
+    GROM_CUDA_TRY(cudaMemset(r->err, 0, sizeof(int)));
+    return fail(GROM_ERR_TIMEOUT, "a device-side wait timed out");
+  }
+  return GROM_OK;
+}
+
+grom_status grom_selftest_timeout(grom_rom* r, int64_t limit_ns) {
+  if (!r || limit_ns < 0) return fail(GROM_ERR_INVALID_ARG, "grom_selftest_timeout: bad argument");
+  GROM_CUDA_TRY(selftest_wait_launch(r->err, (uint64_t)limit_ns, r->stream));
   return GROM_OK;
 }
 

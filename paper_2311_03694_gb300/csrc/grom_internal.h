@@ -208,6 +208,7 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
                                 int nbk, cudaStream_t s);
 cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch,
                                  int step_index, cudaStream_t s);
+cudaError_t selftest_wait_launch(int* err, uint64_t limit_ns, cudaStream_t s);
 cudaError_t slot_admit_launch(double* hist, int64_t* taken, int32_t* steps_left, int32_t* active, int64_t n,
                               int count, const int32_t* slots, const int32_t* horizons, const double* u0s,
                               cudaStream_t s);

@@ -9,6 +9,7 @@
 // energy 1/2 u^T B u of the new state, the invariant u^T n of the old state
 // and flags non-finite states.
 #include "grom_internal.h"
+#include "ptx.cuh"
 
 namespace grom {
 
@@ -327,5 +328,27 @@ cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int b
   return cudaGetLastError();
 }
 
+
+}  // namespace grom
+
+namespace grom {
+
+// Self-test of the bounded device waits: waits on an mbarrier that nothing
+// ever arrives on, gives up after limit_ns and raises the timeout flag, as
+// the production kernels do.
+__global__ void k_selftest_wait(int* err, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(&bar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !ptx::mbar_wait_limit(&bar, 0, nullptr, limit_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+cudaError_t selftest_wait_launch(int* err, uint64_t limit_ns, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(err, limit_ns);
+  return cudaGetLastError();
+}
 
 }  // namespace grom

@@ -376,3 +376,19 @@ def test_cp_batched_varying_batch_sizes_share_scratch():
         c = _eval(rom, U0)
         for b in (0, batch // 2, batch - 1):
             assert _rel(c[b], oracle.nonlinear_cp_skew(U, V, W, U0[b])) <= 1e-12, (batch, b)
+
+
+def test_device_wait_timeout_is_reported_and_recoverable():
+    # failure detection without a fault: a bounded wait on a barrier nothing
+    # signals gives up after 20 ms, the status reports TIMEOUT once, and the
+    # ROM keeps working
+    n = 32
+    C = synth.skew_normal_tensor(n, 2)
+    u = synth.initial_condition(n, 2)[0]
+    rom = _full_rom(C, "f64")
+    rom.selftest_timeout(20_000_000)
+    with pytest.raises(grom.GromError) as ei:
+        rom.sync()
+    assert ei.value.name == "TIMEOUT"
+    rom.sync()  # reported once
+    assert _rel(_eval(rom, u[None, :])[0], oracle.nonlinear_full(C, u)) <= 1e-12
