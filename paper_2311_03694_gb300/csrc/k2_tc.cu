@@ -14,10 +14,12 @@
 // cancellation-heavy states pushes the result past the BF16 tolerance; with
 // the split the Khatri-Rao operand is exact to ~2^-17.
 //
-// CTA (10 warps): warp 0 issues TMA loads of 128 x 64 BF16 tiles of C; warp
-// 1 owns the tensor memory and issues tcgen05.mma (M=128, N=btile, K=16) into
-// an FP32 accumulator in TMEM; warps 2-9 generate the KR tiles (one row b
-// each) and afterwards read the accumulator back (tcgen05.ld) and store FP32
+// CTA (10 warps): warp 0 issues TMA loads of 256 x 64 BF16 tiles of C (two
+// 128-row halves); warp 1 owns the tensor memory and issues tcgen05.mma
+// (M=128, N=btile, K=16) into two FP32 accumulators in TMEM, one per half,
+// both fed by the same KR tile, which halves KR generation per flop; warps 2-9
+// generate the KR tiles (one row b each, u_bj prefetched eight tiles ahead)
+// and afterwards read the accumulators back (tcgen05.ld) and store FP32
 // partial sums.  Stages are recycled through mbarriers signalled by
 // tcgen05.commit.  The K range is split across CTAs by ranges of j; a reduce
 // kernel sums the splits in a fixed order (deterministic) into FP64.
@@ -32,7 +34,10 @@ namespace grom {
 
 constexpr int K2_THREADS = 320;
 constexpr int K2_GEN_WARPS = 8;
-constexpr int K2_A_BYTES = 128 * 128;  // 128 rows x 64 bf16
+constexpr int K2_MT = 2;                         // 128-row accumulators per CTA
+constexpr int K2_A_TILE = 128 * 128;             // 128 rows x 64 bf16
+constexpr int K2_A_BYTES = K2_MT * K2_A_TILE;    // one TMA box of 256 rows
+constexpr int K2_PF = 8;                         // u_bj prefetch distance (tiles)
 
 struct K2Dev {
   int64_t n, np;
@@ -48,13 +53,16 @@ __device__ __forceinline__ void k2_abort(volatile int* abort_flag, int* err) {
   atomicOr(err, DEV_ERR_TIMEOUT);
 }
 
+// K-tile t of a CTA: advected block kb = t / nj (outer), advecting index j0 + t % nj (inner).
+__device__ __forceinline__ int64_t k2_j(int64_t t, int64_t nj, int64_t j0) { return j0 + t % nj; }
+
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_constant__ CUtensorMap tmap, const K2Dev p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int SA = p.stages_a, SB = p.stages_b;
   const int half_bytes = p.btile * 128;   // one BF16 KR tile (hi or lo)
   const int b_bytes = 2 * half_bytes;      // hi tile, then lo tile
-  uint8_t* sa = smem;                                  // SA x 16 KB
+  uint8_t* sa = smem;                                  // SA x (2 x 128 rows x 128 B)
   uint8_t* sb = smem + (size_t)SA * K2_A_BYTES;        // SB x (hi | lo)
   uint64_t* full_a = reinterpret_cast<uint64_t*>(sb + (size_t)SB * b_bytes);
   uint64_t* empty_a = full_a + SA;
@@ -65,11 +73,11 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // tile coordinates
+  // tile coordinates: a pair of 128-row tiles of the test index, a column tile, a K split
   const int split = blockIdx.x % p.splits;
   const int rest = blockIdx.x / p.splits;
   const int col_tile = rest % p.col_tiles;
-  const int i_tile = rest / p.col_tiles;
+  const int i_pair = rest / p.col_tiles;
   const int64_t j0 = (int64_t)split * p.n / p.splits, j1 = ((int64_t)split + 1) * p.n / p.splits;
   const int64_t nj = j1 - j0;
   const int64_t kblocks = p.np / 64;
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
         }
         const int64_t kb = t / nj, j = j0 + (t - kb * nj);
         ptx::mbar_arrive_expect_tx(&full_a[s], K2_A_BYTES);
-        tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, (int32_t)(j * p.np + kb * 64), i_tile * 128, &full_a[s]);
+        tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, (int32_t)(j * p.np + kb * 64), i_pair * 256, &full_a[s]);
       }
       for (int64_t q = t > SA ? t - SA : 0; q < t; ++q)
         if (!ptx::mbar_wait(&full_a[q % SA], (uint32_t)((q / SA) & 1), nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
@@ -120,6 +128,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(128, p.btile);
+      const uint32_t acc1 = tmem + (uint32_t)p.btile;  // second accumulator: columns btile..2 btile-1
       for (int64_t t = 0; t < T; ++t) {
         const int s = (int)(t % SA), r = (int)(t % SB);
         if (!ptx::mbar_wait(&full_a[s], (uint32_t)((t / SA) & 1), abort_flag) ||
@@ -128,13 +137,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
           break;
         }
         tc::fence_after_sync();
-        const uint64_t ad = tc::sw128_kmajor_desc(sa + (size_t)s * K2_A_BYTES);
+        const uint64_t a0 = tc::sw128_kmajor_desc(sa + (size_t)s * K2_A_BYTES);
+        const uint64_t a1 = tc::sw128_kmajor_desc(sa + (size_t)s * K2_A_BYTES + K2_A_TILE);
         const uint64_t bh = tc::sw128_kmajor_desc(sb + (size_t)r * b_bytes);
         const uint64_t bl = tc::sw128_kmajor_desc(sb + (size_t)r * b_bytes + half_bytes);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {  // 4 x K=16 inside the 128-byte swizzle span
-          tc::mma_bf16(tmem, ad + 2 * k, bh + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
-          tc::mma_bf16(tmem, ad + 2 * k, bl + 2 * k, idesc, 1u);
+          const uint32_t first = (t > 0 || k > 0) ? 1u : 0u;
+          tc::mma_bf16(tmem, a0 + 2 * k, bh + 2 * k, idesc, first);
+          tc::mma_bf16(tmem, a0 + 2 * k, bl + 2 * k, idesc, 1u);
+          tc::mma_bf16(acc1, a1 + 2 * k, bh + 2 * k, idesc, first);
+          tc::mma_bf16(acc1, a1 + 2 * k, bl + 2 * k, idesc, 1u);
         }
         tc::commit(&empty_a[s]);
         tc::commit(&empty_b[r]);
@@ -149,53 +162,59 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     const float* urow = p.ub + bglob * p.np;
     float uk[64];
     int64_t cur_kb = -1;
-    // u_bj of the next K-tile is fetched one tile ahead to hide its latency
-    float uj_next = row_on ? urow[j0] : 0.f;
-    for (int64_t t = 0; t < T; ++t) {
-      const int r = (int)(t % SB);
-      const uint32_t ph = (uint32_t)((t / SB) & 1);
-      const int64_t kb = t / nj;
-      const float uj = uj_next;
-      if (row_on && t + 1 < T) {
-        const int64_t t1 = t + 1, kb1 = t1 / nj;
-        uj_next = urow[j0 + (t1 - kb1 * nj)];
-      }
-      if (row_on && kb != cur_kb) {
-        const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
+    // u_bj of the next K2_PF K-tiles, in a ring indexed by t mod K2_PF
+    float ring[K2_PF];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float4 v = src[q];
-          uk[4 * q] = v.x; uk[4 * q + 1] = v.y; uk[4 * q + 2] = v.z; uk[4 * q + 3] = v.w;
-        }
-        cur_kb = kb;
-      }
-      if (t >= SB && !ptx::mbar_wait(&empty_b[r], ph ^ 1u, abort_flag)) {
-        k2_abort(abort_flag, p.err);
-        break;
-      }
-      if (row_on) {
-        uint8_t* row_hi = sb + (size_t)r * b_bytes + (size_t)g * 128;
-        uint8_t* row_lo = row_hi + half_bytes;
+    for (int q = 0; q < K2_PF; ++q) ring[q] = (row_on && q < T) ? urow[k2_j(q, nj, j0)] : 0.f;
+    bool stop = false;
+    for (int64_t t0 = 0; t0 < T && !stop; t0 += K2_PF) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint32_t wh[4], wl[4];
+      for (int q = 0; q < K2_PF; ++q) {
+        const int64_t t = t0 + q;
+        if (t >= T) break;
+        const int r = (int)(t % SB);
+        const uint32_t ph = (uint32_t)((t / SB) & 1);
+        const int64_t kb = t / nj;
+        const float uj = ring[q];
+        if (row_on && t + K2_PF < T) ring[q] = urow[k2_j(t + K2_PF, nj, j0)];
+        if (row_on && kb != cur_kb) {
+          const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const float p0 = uk[8 * c + 2 * h] * uj, p1 = uk[8 * c + 2 * h + 1] * uj;
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
-            const float2 hf = __bfloat1622float2(hi);
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - hf.x, p1 - hf.y);
-            wh[h] = *reinterpret_cast<const uint32_t*>(&hi);
-            wl[h] = *reinterpret_cast<const uint32_t*>(&lo);
+          for (int v = 0; v < 16; ++v) {
+            const float4 x = src[v];
+            uk[4 * v] = x.x; uk[4 * v + 1] = x.y; uk[4 * v + 2] = x.z; uk[4 * v + 3] = x.w;
           }
-          const int off = (c ^ (g & 7)) << 4;
-          *reinterpret_cast<uint4*>(row_hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-          *reinterpret_cast<uint4*>(row_lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+          cur_kb = kb;
         }
+        if (t >= SB && !ptx::mbar_wait(&empty_b[r], ph ^ 1u, abort_flag)) {
+          k2_abort(abort_flag, p.err);
+          stop = true;
+          break;
+        }
+        if (row_on) {
+          uint8_t* row_hi = sb + (size_t)r * b_bytes + (size_t)g * 128;
+          uint8_t* row_lo = row_hi + half_bytes;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float p0 = uk[8 * c + 2 * h] * uj, p1 = uk[8 * c + 2 * h + 1] * uj;
+              const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
+              const float2 hf = __bfloat1622float2(hi);
+              const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - hf.x, p1 - hf.y);
+              wh[h] = *reinterpret_cast<const uint32_t*>(&hi);
+              wl[h] = *reinterpret_cast<const uint32_t*>(&lo);
+            }
+            const int off = (c ^ (g & 7)) << 4;
+            *reinterpret_cast<uint4*>(row_hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4*>(row_lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+          }
+        }
+        ptx::fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&full_b[r]);
       }
-      ptx::fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&full_b[r]);
     }
     // -------------------------------------------------------------- epilogue
     if (warp >= 2 && warp < 6) {
@@ -203,25 +222,27 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
       if (!ok) atomicOr(p.err, DEV_ERR_TIMEOUT);
       tc::fence_after_sync();
       const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are readable by this warp
-      const int64_t i = (int64_t)i_tile * 128 + 32 * q + lane;
       if (ok && !*abort_flag) {
-        for (int c0 = 0; c0 < p.btile; c0 += 32) {
-          uint32_t rr[32];
-          tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, rr);
-          tc::tmem_ld_wait();
-          if (i < p.n) {
-            float* dst = p.part + ((int64_t)split * p.n + i) * p.bp + (int64_t)col_tile * p.btile + c0;
-            const int m = p.btile - c0 < 32 ? p.btile - c0 : 32;
-            if (m == 32) {
+        for (int m = 0; m < K2_MT; ++m) {
+          const int64_t i = (int64_t)i_pair * 256 + m * 128 + 32 * q + lane;
+          for (int c0 = 0; c0 < p.btile; c0 += 32) {
+            uint32_t rr[32];
+            tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * p.btile + c0), rr);
+            tc::tmem_ld_wait();
+            if (i < p.n) {
+              float* dst = p.part + ((int64_t)split * p.n + i) * p.bp + (int64_t)col_tile * p.btile + c0;
+              const int mm = p.btile - c0 < 32 ? p.btile - c0 : 32;
+              if (mm == 32) {
 #pragma unroll
-              for (int v = 0; v < 8; ++v)
-                reinterpret_cast<float4*>(dst)[v] =
-                    make_float4(__uint_as_float(rr[4 * v]), __uint_as_float(rr[4 * v + 1]),
-                                __uint_as_float(rr[4 * v + 2]), __uint_as_float(rr[4 * v + 3]));
-            } else {
+                for (int v = 0; v < 8; ++v)
+                  reinterpret_cast<float4*>(dst)[v] =
+                      make_float4(__uint_as_float(rr[4 * v]), __uint_as_float(rr[4 * v + 1]),
+                                  __uint_as_float(rr[4 * v + 2]), __uint_as_float(rr[4 * v + 3]));
+              } else {
 #pragma unroll
-              for (int v = 0; v < 32; ++v)
-                if (v < m) dst[v] = __uint_as_float(rr[v]);
+                for (int v = 0; v < 32; ++v)
+                  if (v < mm) dst[v] = __uint_as_float(rr[v]);
+              }
             }
           }
         }
@@ -281,7 +302,7 @@ bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np) {
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)(n * np), (cuuint64_t)n};
   cuuint64_t strides[1] = {(cuuint64_t)(n * np * 2)};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {64, 256};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(tensor), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -297,7 +318,7 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
   if (btile > 256) btile = 256;
   p.btile = btile;
   p.col_tiles = (batch + btile - 1) / btile;
-  p.i_tiles = (int)((n + 127) / 128);
+  p.i_tiles = (int)((n + 255) / 256);  // pairs of 128-row tiles
   const int tiles = p.col_tiles * p.i_tiles;
   int splits = sm_count / tiles;
   if (splits < 1) splits = 1;
@@ -306,11 +327,11 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
   const int b_bytes = 2 * btile * 128;  // hi and lo KR tiles
   p.stages_b = btile >= 128 ? 2 : 4;
   int sa = (int)((200 * 1024 - p.stages_b * b_bytes) / K2_A_BYTES);
-  if (sa > 8) sa = 8;
+  if (sa > 6) sa = 6;
   if (sa < 2) sa = 2;
   p.stages_a = sa;
   int cols = 32;
-  while (cols < btile) cols <<= 1;
+  while (cols < 2 * btile) cols <<= 1;  // two accumulators
   p.tmem_cols = cols;
   p.smem = 1024 + (size_t)sa * K2_A_BYTES + (size_t)p.stages_b * b_bytes + (size_t)(2 * sa + 2 * p.stages_b + 1) * 8 + 16;
   p.bp = (int64_t)p.col_tiles * btile;
