@@ -22,6 +22,7 @@ SOURCES = [
     "k_step.cu",
     "k3_cp.cu",
     "k3_gemm.cu",
+    "k3_persistent.cu",
     "k1_plan.cu",
     "k1_f64.cu",
     "k1_f32x2.cu",

@@ -114,7 +114,7 @@ static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int
 static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
-                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch};
+                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -293,6 +293,11 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     if (r->k3g_scratch && cudaMemsetAsync(r->k3g_scratch, 0,
                                           k3g_scratch_bytes(n, rp, r->max_batch, r->storage, r->sm_count),
                                           r->stream) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    // persistent stepper (its grid-barrier word starts at zero)
+    const size_t kp = k3p_scratch_bytes(n, rp, r->storage, r->sm_count);
+    if ((st = dmalloc(&r->k3p_scratch, kp, &r->total_bytes))) return bail(st);
+    if (cudaMemsetAsync(r->k3p_scratch, 0, kp, r->stream) != cudaSuccess)
       return bail(cuda_fail(cudaGetLastError(), "grom_create"));
     // the per-tile arrival counters of the projection kernel start at zero
     if (cudaMemsetAsync(r->part, 0, r->part_bytes, r->stream) != cudaSuccess)
@@ -628,6 +633,16 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step: nsteps < 0");
   grom_rom* r = t->rom;
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
+  // CP forms with a few trajectories: all steps in one persistent launch
+  if (r->diagonal && r->form != GROM_FORM_FULL && r->k3p_scratch && !t->active && !r->prof &&
+      t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 &&
+      k3p_fits(r->n, r->k3.rb, r->storage, t->batch, r->sm_count)) {
+    StepArgs a = step_args(t, energy, invariant);
+    cudaError_t e = k3p_launch(r->op, r->op + r->panel_bytes, r->op + 2 * r->panel_bytes, r->form, r->n, r->k3.rb,
+                               r->storage, t->batch, nsteps, a, r->k3p_scratch, r->sm_count, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grom_step persistent launch");
+    return GROM_OK;
+  }
   constexpr int G = 8;  // steps per captured graph
   int done = 0;
   if (!energy && !invariant && !r->prof && nsteps >= G) {

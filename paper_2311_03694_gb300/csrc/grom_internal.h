@@ -154,6 +154,13 @@ size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int 
 cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
                        int sm_count, cudaStream_t s);
 constexpr int K3G_MIN_BATCH = 16;
+// Persistent cooperative CPD-ROM stepper for a few trajectories.
+size_t k3p_scratch_bytes(int64_t n, int64_t rp, int storage, int sm_count);
+int k3p_max_batch(int storage);
+bool k3p_fits(int64_t n, int64_t rp, int storage, int batch, int sm_count);
+cudaError_t k3p_launch(const uint8_t* fa, const uint8_t* fb, const uint8_t* fc, int form, int64_t n, int64_t rp,
+                       int storage, int batch, int nsteps, const StepArgs& st, void* scratch, int sm_count,
+                       cudaStream_t s);
 
 // --------------------------------------------------------------- stepper
 struct StepArgs {
@@ -257,6 +264,7 @@ struct grom_rom {
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
+  void* k3p_scratch = nullptr;       // persistent CP stepper: partials, h, barrier
   size_t k2_scratch_bytes = 0;
   bool prof = false;                 // kernel timing enabled
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs

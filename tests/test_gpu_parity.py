@@ -392,3 +392,46 @@ def test_device_wait_timeout_is_reported_and_recoverable():
     assert ei.value.name == "TIMEOUT"
     rom.sync()  # reported once
     assert _rel(_eval(rom, u[None, :])[0], oracle.nonlinear_full(C, u)) <= 1e-12
+
+
+@pytest.mark.parametrize("storage,batch,tol", [("f64", 2, 1e-11), ("f32", 3, 1e-5), ("bf16", 4, 2e-2), ("f64", 1, 1e-11)])
+def test_cp_persistent_stepper_with_outputs(storage, batch, tol):
+    # CP forms with a few trajectories step in one persistent cooperative launch
+    n, r, dt, nu, steps = 80, 33, 1e-3, 1e-2, 37
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, seed, 0, batch)
+    rom = grom.Rom(n, "cp_skew", storage, factors=(U, V, W), stiffness=a, nu=nu, dt=dt, max_batch=batch)
+    tr = grom.Trajectories(rom, U0)
+    energy = torch.empty((steps, batch), dtype=torch.float64, device="cuda")
+    inv = torch.empty((steps, batch), dtype=torch.float64, device="cuda")
+    tr.step(steps, energy, inv)
+    code, _ = tr.status()
+    assert code == 0
+    H = tr.get_state()
+    for b in range(batch):
+        ref = oracle.Rom("cp_skew", n, a, nu, dt, factors=(U, V, W))
+        h = ref.initial_history(U0[b])
+        e_ref, i_ref = ref.step(h, steps, want_energy=True, want_invariant=True)
+        assert _rel(H[b][:n], h[:n]) <= tol
+        assert H[b][6 * n] == steps
+        np.testing.assert_allclose(energy.cpu().numpy()[:, b], e_ref, rtol=max(tol, 1e-12))
+        # the skew CP structure conserves u^T c(u) = 0
+        assert np.max(np.abs(inv.cpu().numpy()[:, b])) <= 1e-3 * np.max(e_ref) * (1e-6 if storage == "f64" else 1)
+
+
+def test_cp_persistent_resume_is_bit_identical():
+    n, r = 64, 20
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    a = synth.diag_stiffness(n)
+    u0 = synth.initial_condition(n, seed)[0]
+    rom = grom.Rom(n, "cp_skew", "bf16", factors=(U, V, W), stiffness=a)
+    t1 = grom.Trajectories(rom, u0[None, :])
+    t1.step(40)
+    whole = t1.get_state()
+    t2 = grom.Trajectories(rom, u0[None, :])
+    t2.step(15)
+    t3 = grom.Trajectories(rom, u0[None, :])
+    t3.set_state(t2.get_state())
+    t3.step(25)
+    np.testing.assert_array_equal(t3.get_state(), whole)
