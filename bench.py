@@ -9,11 +9,12 @@ dt = 1e-3, initial state u_i ~ N(0,1)/i.
 
 One bench step is one BDF3/EXT3 step (advection term, extrapolation, cached
 reduced solve, energy/invariant, history rotation) of one trajectory of the
-headline model: the full G-ROM with the tensor stored in BF16, FP32
-accumulation and FP64 state update.  The same step is also timed for the
-other storage types and for the CPD-ROM (skew CP factors, rank N) and
-reported under "variants"; each result carries its error against the FP64
-oracle.
+headline model: the full G-ROM with the tensor stored in BF16 in the
+skew-packed layout (one entry of each pair C_ijk = -C_kji; the same model
+as the dense tensor), FP32 accumulation and FP64 state update.  The same step
+is also timed for the other storage types, for the dense layout and for the
+CPD-ROM (skew CP factors, rank N) and reported under "variants"; each result
+carries its error against the FP64 oracle.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -39,9 +40,11 @@ sys.path.insert(0, ROOT)
 METRIC = "ROM steps/s at N=1024 (full vs CPD, FP64 vs BF16), HBM/TC roofline %, p99 latency"
 UNIT = "steps/s"
 NU, DT = 1e-2, 1e-3
-HEADLINE = ("full", "bf16")
-VARIANTS = [("full", "bf16"), ("full", "f32"), ("full", "f32x2"), ("full", "f64"), ("cp_skew", "bf16"),
-            ("cp_skew", "f32"), ("cp_skew", "f64")]
+HEADLINE = ("full", "bf16", "skew_packed")
+VARIANTS = [("full", "bf16", "skew_packed"), ("full", "f32", "skew_packed"), ("full", "f32x2", "skew_packed"),
+            ("full", "f64", "skew_packed"), ("full", "bf16", "dense"), ("full", "f32", "dense"),
+            ("full", "f32x2", "dense"), ("full", "f64", "dense"), ("cp_skew", "bf16", "dense"),
+            ("cp_skew", "f32", "dense"), ("cp_skew", "f64", "dense")]
 TOL = {"f64": 1e-12, "f32x2": 1e-12, "f32": 1e-5, "bf16": 2e-2}
 STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
 L2_BYTES = 129 * 2 ** 20
@@ -55,7 +58,7 @@ def parse_args():
     p.add_argument("--impl", default="grom", choices=["grom", "reference"])
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--rank", type=int, default=0, help="CP rank (default N)")
-    p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64,cp_skew:bf16")
+    p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64:skew_packed,cp_skew:bf16 (layout defaults to dense)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('none' to skip)")
@@ -365,11 +368,17 @@ def _cuda_ok():
         return False
 
 
+def _packed_len(n):
+    """Stored elements per row of the skew-packed layout: round_up(max(n//2, 1), 64)."""
+    return (max(n // 2, 1) + 63) // 64 * 64
+
+
 def _config(n, rank):
-    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage, FP32 accumulation, FP64 state; "
+    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage in the skew-packed layout "
+                        "(one entry of each pair C_ijk = -C_kji), FP32 accumulation, FP64 state; "
                         "CP-structured skew tensor (R=%d) + 1e-3 skew residual; one trajectory per GPU" % (n, rank),
-            "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT,
-            "l2": "inputs larger than L2 (full tensor %.2f GB per step)" % (n ** 3 * 2 / 1e9)}
+            "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT, "layout": "skew_packed",
+            "l2": "inputs larger than L2 (stored tensor %.2f GB per step)" % (n * n * _packed_len(n) * 2 / 1e9)}
 
 
 # -------------------------------------------------------------------- main
@@ -400,9 +409,9 @@ def main():
     u0 = synth.initial_condition(n, seed, traj=rank_id)  # one trajectory per replica
     hbm_peak, tc_peak, tc_sustained, peak_kind = peaks()
 
-    def make_rom(form, storage):
+    def make_rom(form, storage, layout="dense"):
         if form == "full":
-            return grom.Rom(n, "full", storage, tensor=C, stiffness=a, nu=NU, dt=DT)
+            return grom.Rom(n, "full", storage, tensor=C, stiffness=a, nu=NU, dt=DT, layout=layout)
         return grom.Rom(n, form, storage, factors=factors, stiffness=a, nu=NU, dt=DT)
 
     # ---------------------------------------------------- headline, timed
@@ -415,7 +424,6 @@ def main():
         torch.distributed.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    rom.profile(True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
@@ -427,22 +435,37 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    k1_ms, k1_launches = rom.profile_read()
-    rom.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
     code, bad = tr.status()
     ms = max_over_ranks(ms)
     value = replica_throughput(ms, world)  # all replicas' steps per second
 
-    # roofline of the dominant kernel (K1 streaming contraction)
+    # The same K steps again with a CUDA event pair around every streaming
+    # launch (event nodes inside the replayed graphs): the kernel's live
+    # duration for the roofline.  The event nodes lengthen each step, so the
+    # headline value above comes from the run without them.
+    rom.profile(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    tr.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    profiled_ms = e0.elapsed_time(e1) / args.steps
+    k1_ms, k1_launches = rom.profile_read()
+    rom.profile(False)
+
+    # roofline of the dominant kernel (packed K1 streaming contraction): the
+    # stored skew-packed tensor, N * N rows of round_up(N/2, 64) BF16 values
     k1_avg_ms = k1_ms / max(1, k1_launches)
-    alg_bytes = float(n) ** 3 * STORAGE_BYTES[HEADLINE[1]]
+    alg_bytes = float(n) * n * _packed_len(n) * STORAGE_BYTES[HEADLINE[1]]
     achieved = alg_bytes / (k1_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": kernel_traffic("k1_stream_bf16_n%d" % n),
-                "kernel": "k1_stream_kernel<BF16> (+finalize excluded)", "peak_kind": peak_kind,
+                "frac": achieved / hbm_peak, "traffic": kernel_traffic("k1_packed_bf16_n%d" % n),
+                "kernel": "k1_packed_kernel<BF16> (finalize excluded)", "peak_kind": peak_kind,
                 "kernel_ms": k1_avg_ms, "kernel_launches": k1_launches,
-                "algorithmic_bytes_per_launch": alg_bytes}
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "timing": "CUDA events around each launch in a second timed run of the same %d steps "
+                          "(%.4f ms per step with the event nodes)" % (args.steps, profiled_ms)}
 
     # ------------------------------------------------------------- e2e
     pin_in = torch.empty((1, n), dtype=torch.float64).pin_memory()
@@ -460,7 +483,7 @@ def main():
     e2e = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
            "api": "grom_step_host(traj, 1, u_in=pinned host, u_out=pinned host)"}
     tr.close()
-    launches_per_step = 3  # K1 streaming kernel, K1 finalize, fused BDF3/EXT3 step
+    launches_per_step = 2  # packed K1 streaming kernel; its finalize fused with the BDF3/EXT3 step
 
     # -------------------------------------------- errors vs the FP64 oracle
     cores = os.cpu_count() or 1
@@ -477,16 +500,16 @@ def main():
 
     # ------------------------------------------------------------ variants
     wanted = VARIANTS if args.variants == "all" else (
-        [] if args.variants == "none" else [tuple(v.split(":")) for v in args.variants.split(",")])
+        [] if args.variants == "none" else [tuple((v + ":dense").split(":")[:3]) for v in args.variants.split(",")])
     flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device="cuda")
     variants = {}
-    for form, storage in wanted:
-        vrom = make_rom(form, storage)
-        key = "%s_%s" % ("full" if form == "full" else "cpd", storage)
+    for form, storage, layout in wanted:
+        vrom = make_rom(form, storage, layout)
+        key = "%s_%s%s" % ("full" if form == "full" else "cpd", storage, "_packed" if layout == "skew_packed" else "")
         vsteps = max(10, min(args.steps, 200))
         if form == "full":
             vms, vcode, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
-            entry = {"ms_per_step": vms, "steps_per_s": 1e3 / vms, "l2": "tensor > L2"}
+            entry = {"ms_per_step": vms, "steps_per_s": 1e3 / vms, "l2": "tensor > L2", "layout": layout}
         else:
             vms, vcode, per = time_variant(grom, torch, vrom, u0, vsteps, 3, flush=flush)
             wms, _, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
@@ -580,12 +603,10 @@ def main():
         cpu_baseline = {"value": k / tk, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                         "sample": "%d BDF3/EXT3 steps (after 1 untimed) of the N=%d FP64 full G-ROM on the "
                                   "host cores, OpenMP over the test index" % (k, n)}
-        # trajectory error of each full-form storage type after 1 + k steps
-        for storage in ("bf16", "f32", "f32x2", "f64"):
-            key = "full_%s" % storage
-            if key not in variants:
-                continue
-            vrom = make_rom("full", storage)
+        # trajectory error of each full-form storage type and layout after 1 + k steps
+        for key in [k for k in variants if k.startswith("full_")]:
+            storage = key.split("_")[1]
+            vrom = make_rom("full", storage, variants[key]["layout"])
             vt = grom.Trajectories(vrom, u0)
             vt.step(1 + k)
             hv = vt.get_state()[0]
@@ -609,7 +630,7 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * args.steps,  # in the headline timed region
         "clocks": clocks,
         "status": grom.ERRORS.get(code, "OK") if code else "OK",
         "variants": variants,

@@ -65,6 +65,28 @@ typedef int32_t grom_status;
 #define GROM_F32 2   /* rn(x) to float; FP32 accumulation                          */
 #define GROM_BF16 3  /* rn(x) to bfloat16; FP32 accumulation                       */
 
+/* Stored layout of the FULL tensor.
+ *
+ * GROM_LAYOUT_DENSE: all n^3 entries (rows (i, j), advected index k inner).
+ *
+ * GROM_LAYOUT_SKEW_PACKED: for the skew-symmetric tensors of the energy-
+ * conserving G-ROM (Sec. 3.2: C_ijk = -C_kji, test and advected index
+ * swapped; hence C_iji = 0), each unordered pair {i, k} is stored once.  Row
+ * (i, j) keeps the entries k = (i + d) mod n for d = 1 .. floor(n/2); for even
+ * n the entry at d = n/2 is kept only in rows with i < n/2 (row i >= n/2
+ * stores zero there).  The other entries follow from C_ijk = -C_kji, so
+ *   c_i = sum_j u_j [ sum_d C_{i,j,i+d} u_{i+d} - sum_d C_{i-d,j,i} u_{i-d} ]
+ * (indices mod n) is the same contraction as the dense one.  This halves the
+ * bytes and the multiply-adds of the streaming contraction.
+ * The caller's tensor must be skew to rounding.  While uploading, the library
+ * forms the probe sum_ijk x_i y_j x_k C_ijk for two seeded +-1 vector pairs
+ * (zero for a skew tensor, about ||sym(C)||_F otherwise) and rejects the
+ * tensor with GROM_ERR_INVALID_ARG if a probe exceeds 1e-9 ||C||_F.  The
+ * tensor-core batched kernel needs the dense layout; packed ROMs evaluate
+ * every batch with the streaming kernel. */
+#define GROM_LAYOUT_DENSE 0
+#define GROM_LAYOUT_SKEW_PACKED 1
+
 typedef struct grom_rom grom_rom;
 typedef struct grom_traj grom_traj;
 
@@ -100,7 +122,8 @@ typedef struct grom_desc {
   int32_t defer_tensor; /* FULL only: 1 = rows come from grom_upload_tensor_slab  */
   int32_t max_batch;    /* largest batch passed to grom_nonlinear/grom_traj_create
                            (sizes the library's scratch); 0 means 1              */
-  int32_t reserved[4];  /* must be zero                                           */
+  int32_t layout;       /* FULL only: GROM_LAYOUT_DENSE (0) or GROM_LAYOUT_SKEW_PACKED */
+  int32_t reserved[3];  /* must be zero                                           */
 } grom_desc;
 
 /* Creates a ROM on the current CUDA device.  Every input is copied; the caller

@@ -20,6 +20,7 @@ ERRORS = {
 FORMS = {"full": 0, "cp": 1, "cp_skew": 2}
 STORAGE = {"f64": 0, "f32x2": 1, "f32": 2, "bf16": 3}
 STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
+LAYOUTS = {"dense": 0, "skew_packed": 1}
 
 
 class _Request(ctypes.Structure):
@@ -52,7 +53,8 @@ class _Desc(ctypes.Structure):
         ("mass", ctypes.c_void_p), ("mass_diag", ctypes.c_void_p),
         ("linear", ctypes.c_void_p), ("linear_diag", ctypes.c_void_p), ("forcing", ctypes.c_void_p),
         ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("order", ctypes.c_int32),
-        ("defer_tensor", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("defer_tensor", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("layout", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -188,11 +190,13 @@ class Rom:
     form: "full" (tensor n^3), "cp" (factors A, B, C) or "cp_skew" (U, V, W).
     storage: "f64", "f32x2", "f32" or "bf16".  stiffness may be a length-n
     diagonal or an n x n matrix; mass None means identity.
+    layout (full form): "dense" or "skew_packed" (one entry of each pair
+    C_ijk = -C_kji stored; the tensor must be skew in i and k).
     """
 
     def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,
                  linear=None, forcing=None, nu=1e-2, dt=1e-3, order=3, max_batch=1, defer_tensor=False,
-                 stream=None):
+                 stream=None, layout="dense"):
         lib = load()
         keep = []
 
@@ -208,6 +212,7 @@ class Rom:
         d.n, d.form, d.storage = int(n), FORMS[form], STORAGE[storage]
         d.nu, d.dt, d.order, d.max_batch = float(nu), float(dt), int(order), int(max_batch)
         d.defer_tensor = 1 if defer_tensor else 0
+        d.layout = LAYOUTS[layout]
         if form == "full":
             d.tensor = arr(tensor)
         else:
@@ -236,6 +241,7 @@ class Rom:
         _check(lib.grom_create(ctypes.byref(d), ctypes.c_void_p(self._stream), ctypes.byref(h)))
         self._h = h
         self.n, self.form, self.storage, self.max_batch = int(n), form, storage, int(max_batch)
+        self.layout = layout
         self.rank = int(d.rank)
         self.order = int(order)
 

@@ -29,6 +29,10 @@ SOURCES = [
     "k1_f32.cu",
     "k1_bf16.cu",
     "k1_static.cu",
+    "k1p_f64.cu",
+    "k1p_f32x2.cu",
+    "k1p_f32.cu",
+    "k1p_bf16.cu",
     "k2_tc.cu",
     "serve.cu",
 ]

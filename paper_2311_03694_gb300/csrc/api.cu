@@ -111,10 +111,48 @@ static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int
   return GROM_OK;
 }
 
+// Streams dense FP64 tensor rows (i, j) for test indices [i0, i1) through a
+// staging buffer into the skew-packed layout, adding their skew probes.
+static grom_status upload_rows_packed(grom_rom* r, const double* src, int64_t i0, int64_t i1) {
+  const int64_t n = r->n;
+  const int64_t per_i = n * n;  // doubles per test index
+  const int64_t si = std::max<int64_t>(1, (int64_t)(256ll << 20) / (per_i * 8));
+  double* stage = nullptr;
+  grom_status st = dmalloc(&stage, (size_t)(std::min(si, i1 - i0) * per_i * 8), nullptr);
+  if (st) return st;
+  for (int64_t a = i0; a < i1; a += si) {
+    const int64_t cnt = std::min(si, i1 - a);
+    cudaError_t e = cudaMemcpyAsync(stage, src + (a - i0) * per_i, (size_t)(cnt * per_i * 8), cudaMemcpyDefault, r->stream);
+    if (e == cudaSuccess) e = skew_probe_launch(stage, cnt * n, n, a, r->probe, r->stream);
+    if (e == cudaSuccess)
+      e = convert_rows_packed_launch(stage, cnt * n, n, a, r->k1.lp, r->storage, r->op + a * n * r->k1.row_bytes,
+                                     r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) {
+      cudaFree(stage);
+      return cuda_fail(e, "tensor upload");
+    }
+  }
+  cudaFree(stage);
+  return GROM_OK;
+}
+
+// After the last row: the probes of a skew tensor vanish up to rounding.
+static grom_status check_skew_probe(grom_rom* r) {
+  double acc[3];
+  GROM_CUDA_TRY(cudaMemcpy(acc, r->probe, sizeof(acc), cudaMemcpyDeviceToHost));
+  const double fro = std::sqrt(acc[2]);
+  if (!(std::fabs(acc[0]) <= 1e-9 * fro) || !(std::fabs(acc[1]) <= 1e-9 * fro))
+    return fail(GROM_ERR_INVALID_ARG,
+                "skew-packed layout: the tensor is not skew in its test and advected index (C_ijk = -C_kji)");
+  return GROM_OK;
+}
+
 static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
-                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch};
+                  r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
+                  r->k1p_dg, r->k1p_tg, r->probe};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -145,7 +183,7 @@ static bool prof_pair(grom_rom* r, cudaEvent_t* e0, cudaEvent_t* e1) {
 }
 
 static bool use_k2(const grom_rom* r, int batch) {
-  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok) return false;
+  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE) return false;
   if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
   if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
   return batch > 8;
@@ -160,6 +198,8 @@ static K1Args k1_args(grom_rom* r) {
   a.tensor = r->op;
   a.part = r->part;
   a.err = r->err;
+  a.dg = r->k1p_dg;
+  a.tg = r->k1p_tg;
   return a;
 }
 
@@ -194,8 +234,12 @@ int32_t grom_max_n(int32_t form, int32_t storage) {
 grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   if (!d || !out) return fail(GROM_ERR_INVALID_ARG, "grom_create: null argument");
   *out = nullptr;
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 3; ++q)
     if (d->reserved[q]) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
+  if (d->layout != GROM_LAYOUT_DENSE && d->layout != GROM_LAYOUT_SKEW_PACKED)
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: unknown layout");
+  if (d->layout != GROM_LAYOUT_DENSE && d->form != GROM_FORM_FULL)
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: the skew-packed layout is for the full form");
   if (d->n < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: n must be >= 1");
   if (d->form < GROM_FORM_FULL || d->form > GROM_FORM_CP_SKEW) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad form");
   if (storage_elem_bytes(d->storage) == 0) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad storage type");
@@ -229,6 +273,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   r->nu = d->nu;
   r->dt = d->dt;
   r->max_batch = d->max_batch > 0 ? d->max_batch : 1;
+  r->layout = d->layout;
   r->stream = static_cast<cudaStream_t>(stream);
   const int64_t n = r->n;
   grom_status st = GROM_OK;
@@ -246,13 +291,21 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   // ---------------------------------------------------- advection operator
   if (r->form == GROM_FORM_FULL) {
     r->np = padded_n(n);
-    r->k1 = k1_plan(n, r->storage, r->sm_count);
+    const bool packed = r->layout == GROM_LAYOUT_SKEW_PACKED;
+    r->k1 = k1_plan(n, r->storage, r->sm_count, packed ? 1 : 0);
     const size_t row_bytes = (size_t)r->k1.row_bytes;
     r->op_bytes = (size_t)n * (size_t)n * row_bytes;
     if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
     r->part_bytes = (size_t)r->k1.grid * r->k1.maxseg * (K1_CONSUMERS / 32) * r->k1.nb_max * sizeof(double);
     if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
-    if (r->storage == GROM_BF16) {
+    if (packed) {
+      if ((st = dmalloc(&r->k1p_dg, k1p_dg_bytes(r->k1, r->storage), &r->total_bytes))) return bail(st);
+      if ((st = dmalloc(&r->k1p_tg, k1p_tg_bytes(r->k1), &r->total_bytes))) return bail(st);
+      if ((st = dmalloc(&r->probe, 3 * sizeof(double), &r->total_bytes))) return bail(st);
+      if (cudaMemsetAsync(r->probe, 0, 3 * sizeof(double), r->stream) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    }
+    if (r->storage == GROM_BF16 && !packed) {
       r->k2_ok = k2_make_tmap(&r->k2_tmap, r->op, n, r->np);
       if (r->k2_ok) {
         // scratch for the largest plan over the batch sizes this ROM accepts
@@ -267,7 +320,12 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       }
     }
     if (d->tensor) {
-      if ((st = upload_rows(r, d->tensor, n * n, n, r->np, r->op, (int64_t)row_bytes))) return bail(st);
+      if (packed) {
+        if ((st = upload_rows_packed(r, d->tensor, 0, n))) return bail(st);
+        if ((st = check_skew_probe(r))) return bail(st);
+      } else if ((st = upload_rows(r, d->tensor, n * n, n, r->np, r->op, (int64_t)row_bytes))) {
+        return bail(st);
+      }
       r->rows_uploaded = n;
     } else {
       r->row_seen = new (std::nothrow) uint8_t[(size_t)n]();
@@ -370,14 +428,25 @@ grom_status grom_upload_tensor_slab(grom_rom* r, int32_t i0, int32_t i1, const d
     return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: ROM was not created with defer_tensor");
   if (i0 < 0 || i1 > r->n || i0 >= i1) return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: bad row range");
   const int64_t n = r->n;
-  grom_status st = upload_rows(r, rows, (int64_t)(i1 - i0) * n, n, r->np,
-                               r->op + (size_t)i0 * n * (size_t)r->k1.row_bytes, r->k1.row_bytes);
+  const bool packed = r->layout == GROM_LAYOUT_SKEW_PACKED;
+  if (packed) {
+    // the probe adds every row once
+    for (int64_t i = i0; i < i1; ++i)
+      if (r->row_seen[i]) return fail(GROM_ERR_INVALID_ARG, "grom_upload_tensor_slab: rows already uploaded (packed layout)");
+  }
+  grom_status st = packed ? upload_rows_packed(r, rows, i0, i1)
+                          : upload_rows(r, rows, (int64_t)(i1 - i0) * n, n, r->np,
+                                        r->op + (size_t)i0 * n * (size_t)r->k1.row_bytes, r->k1.row_bytes);
   if (st) return st;
   for (int64_t i = i0; i < i1; ++i)
     if (!r->row_seen[i]) {
       r->row_seen[i] = 1;
       ++r->rows_uploaded;
     }
+  if (packed && r->rows_uploaded == n && (st = check_skew_probe(r))) {
+    r->rows_uploaded = n - 1;  // the ROM stays unusable
+    return st;
+  }
   return GROM_OK;
 }
 
@@ -442,10 +511,10 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.c_stride = r->n;
     cudaEvent_t e0, e1;
     if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
-    if (e0) cudaEventRecord(e0, r->stream);
+    if (e0) prof_record(e0, r->stream);
     e = use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
                           : k3_launch(r->k3, r->storage, a, batch, r->stream);
-    if (e1) cudaEventRecord(e1, r->stream);
+    if (e1) prof_record(e1, r->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear launch");
   return GROM_OK;
@@ -478,7 +547,7 @@ grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_
   if ((st = dmalloc(&t->err, 2 * sizeof(int), nullptr))) return bail(st);
   if ((st = dmalloc(&t->io, (size_t)batch * n * sizeof(double), nullptr))) return bail(st);
   if (r->diagonal) {
-    const int nblk = std::max(step_mc_blocks(n), k3_expand_blocks(n));
+    const int nblk = std::max(std::max(step_mc_blocks(n), k3_expand_blocks(n)), step_pk_blocks(n));
     if ((st = dmalloc(&t->red, (size_t)batch * nblk * 2 * sizeof(double), nullptr))) return bail(st);
     if ((st = dmalloc(&t->cnt, (size_t)batch * sizeof(unsigned int), nullptr))) return bail(st);
     if (cudaMemsetAsync(t->cnt, 0, (size_t)batch * sizeof(unsigned int), r->stream) != cudaSuccess)
@@ -509,6 +578,7 @@ grom_status grom_traj_destroy(grom_traj* t) {
   if (t->red) cudaFree(t->red);
   if (t->cnt) cudaFree(t->cnt);
   if (t->graph) cudaGraphExecDestroy(t->graph);
+  if (t->graph_tmpl) cudaGraphDestroy(t->graph_tmpl);
   if (t->gstream) cudaStreamDestroy(t->gstream);
   if (t->ev_in) cudaEventDestroy(t->ev_in);
   if (t->ev_out) cudaEventDestroy(t->ev_out);
@@ -549,10 +619,10 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   a.active = t->active;
   cudaEvent_t e0, e1;
   if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
-  if (e0) cudaEventRecord(e0, strm);
+  if (e0) prof_record(e0, strm);
   cudaError_t e = use_k3g(r, t->batch) ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
                                        : k3_launch(r->k3, r->storage, a, t->batch, strm);
-  if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, strm);
+  if (e1 && e == cudaSuccess) e = prof_record(e1, strm);
   return e;
 }
 
@@ -608,9 +678,9 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
       st3.nblk = k3_expand_blocks(r->n);
       cudaEvent_t e0, e1;
       if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
-      if (e0) cudaEventRecord(e0, strm);
+      if (e0) prof_record(e0, strm);
       e = k3_launch_step(r->k3, r->storage, k, t->batch, &st3, s, strm);
-      if (e1 && e == cudaSuccess) e = cudaEventRecord(e1, strm);
+      if (e1 && e == cudaSuccess) e = prof_record(e1, strm);
     } else if (fused_k1) {
       K1Args k = k1_args(r);
       k.hist = t->hist;
@@ -645,13 +715,18 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   }
   constexpr int G = 8;  // steps per captured graph
   int done = 0;
-  if (!energy && !invariant && !r->prof && nsteps >= G) {
+  if (!energy && !invariant && nsteps >= G) {
     // Replay a captured graph of G steps on a private stream joined to the
     // ROM's stream by events (the ROM's stream may be the legacy default
     // stream, which cannot be captured).
     if (t->graph && t->graph_version != r->version) {
       cudaGraphExecDestroy(t->graph);
+      cudaGraphDestroy(t->graph_tmpl);
       t->graph = nullptr;
+      t->graph_tmpl = nullptr;
+      t->prof_nodes.clear();
+      t->prof_index.clear();
+      t->prof_pairs = 0;
     }
     if (!t->graph) {
       if (!t->gstream) {
@@ -660,23 +735,65 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
         GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
       }
       cudaGraph_t g = nullptr;
+      const size_t used0 = r->prof_used;
       GROM_CUDA_TRY(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = launch_steps(t, G, nullptr, nullptr, t->gstream);
       cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
+      // the timing pairs taken during capture are placeholders: each replay
+      // points the event nodes at fresh pairs
+      const size_t used1 = r->prof_used;
+      r->prof_used = used0;
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         return cuda_fail(e != cudaSuccess ? e : e2, "grom_step graph capture");
       }
+      if (r->prof) {
+        size_t count = 0;
+        e = cudaGraphGetNodes(g, nullptr, &count);
+        std::vector<cudaGraphNode_t> nodes(count);
+        if (e == cudaSuccess && count) e = cudaGraphGetNodes(g, nodes.data(), &count);
+        for (size_t q = 0; e == cudaSuccess && q < count; ++q) {
+          cudaGraphNodeType ty;
+          if ((e = cudaGraphNodeGetType(nodes[q], &ty)) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+          cudaEvent_t ev;
+          if ((e = cudaGraphEventRecordNodeGetEvent(nodes[q], &ev)) != cudaSuccess) break;
+          for (size_t p = 2 * used0; p < 2 * used1; ++p)
+            if (r->prof_ev[p] == ev) {
+              t->prof_nodes.push_back(nodes[q]);
+              t->prof_index.push_back((int)(p - 2 * used0));
+            }
+        }
+        t->prof_pairs = (int)(used1 - used0);
+        if (e != cudaSuccess) {
+          cudaGraphDestroy(g);
+          return cuda_fail(e, "grom_step graph timing nodes");
+        }
+      }
       e = cudaGraphInstantiate(&t->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(e, "grom_step graph instantiate");
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        t->prof_nodes.clear();
+        t->prof_index.clear();
+        return cuda_fail(e, "grom_step graph instantiate");
+      }
+      t->graph_tmpl = g;
       t->graph_steps = G;
       t->graph_version = r->version;
     }
     GROM_CUDA_TRY(cudaEventRecord(t->ev_in, r->stream));
     GROM_CUDA_TRY(cudaStreamWaitEvent(t->gstream, t->ev_in, 0));
-    for (; done + G <= nsteps; done += G) GROM_CUDA_TRY(cudaGraphLaunch(t->graph, t->gstream));
+    for (; done + G <= nsteps; done += G) {
+      if (r->prof) {
+        // fresh timing pairs for this replay, in the graph's event order
+        std::vector<cudaEvent_t> evs((size_t)2 * t->prof_pairs);
+        for (int k = 0; k < t->prof_pairs; ++k)
+          if (!prof_pair(r, &evs[2 * k], &evs[2 * k + 1])) return fail(GROM_ERR_CUDA, "event creation failed");
+        for (size_t q = 0; q < t->prof_nodes.size(); ++q)
+          GROM_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(t->graph, t->prof_nodes[q], evs[t->prof_index[q]]));
+      }
+      GROM_CUDA_TRY(cudaGraphLaunch(t->graph, t->gstream));
+    }
     GROM_CUDA_TRY(cudaEventRecord(t->ev_out, t->gstream));
     GROM_CUDA_TRY(cudaStreamWaitEvent(r->stream, t->ev_out, 0));
   }
@@ -713,7 +830,7 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   if (kernel < GROM_KERNEL_AUTO || kernel > GROM_KERNEL_TENSOR)
     return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
   if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
-    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form");
+    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form, dense layout");
   r->kernel_choice = kernel;
   ++r->version;
   return GROM_OK;
@@ -722,6 +839,7 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
 grom_status grom_profile_enable(grom_rom* r, int32_t enable) {
   if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_profile_enable: null rom");
   GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  if (r->prof != (enable != 0)) ++r->version;  // captured graphs carry (or lack) timing nodes
   r->prof = enable != 0;
   r->prof_used = 0;
   return GROM_OK;

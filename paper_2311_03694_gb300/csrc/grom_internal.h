@@ -24,6 +24,16 @@ grom_status cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::grom::cuda_fail(_e, #expr);   \
   } while (0)
 
+// Records a kernel-timing event.  Under stream capture the record becomes an
+// event node of the graph (cudaEventRecordExternal), so graph replays time
+// their kernels too.
+inline cudaError_t prof_record(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cudaGetLastError();
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
 // Device-side error flags (bit mask in a device int).
 constexpr int DEV_ERR_TIMEOUT = 1;
 constexpr int DEV_ERR_NONFINITE = 2;
@@ -53,7 +63,7 @@ constexpr int K1_MAX_ROW_BYTES = K1_STAGE_BYTES;
 
 struct K1Plan {
   int64_t n, np;
-  int64_t row_bytes;   // np * element bytes
+  int64_t row_bytes;   // stored elements per row (np, or lp when packed) * element bytes
   int64_t rpc;         // rows per chunk (all in one test index i)
   int64_t cpi;         // chunks per test index
   int64_t T;           // total chunks = n * cpi
@@ -62,7 +72,17 @@ struct K1Plan {
   int qm;              // vector positions per consumer thread per row (1,2,4,8)
   int nb_max;          // trajectories per pass
   size_t smem;         // dynamic shared memory
+  // skew-packed layout (GROM_LAYOUT_SKEW_PACKED); zero for the dense layout
+  int packed;
+  int rg;              // row groups per chunk that share a position (1, 2 or 4)
+  int64_t h;           // stored distances d = 1..h, h = n / 2
+  int64_t lp;          // stored elements per row: round_up(max(h, 1), 64)
+  int64_t lw;          // transposed-term window per CTA: maxseg - 1 + lp
 };
+// Scratch of the packed kernel: D u_i per (CTA, test-index segment, trajectory,
+// position) and the per-CTA transposed-term windows.
+size_t k1p_dg_bytes(const K1Plan& p, int storage);
+size_t k1p_tg_bytes(const K1Plan& p);
 
 struct K1Args {
   const uint8_t* tensor;  // stored tensor (storage layout)
@@ -82,9 +102,11 @@ struct K1Args {
   const int32_t* active;  // nullable: trajectories with active[b]==0 are skipped
   cudaEvent_t ev0, ev1;   // nullable: recorded around the streaming kernel
   int skip_finalize;      // 1: the caller runs a fused finalize (see k_step.cu)
+  void* dg;               // packed layout: k1p_dg_bytes of scratch
+  double* tg;             // packed layout: k1p_tg_bytes of scratch
 };
 
-K1Plan k1_plan(int64_t n, int storage, int sm_count);
+K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed = 0);
 cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a, int batch, cudaStream_t s);
 
 // ------------------------------------------------- K2 (tensor cores, BF16)
@@ -208,11 +230,17 @@ __device__ __forceinline__ void step_done(const StepArgs& a, int b, int64_t l) {
 }
 constexpr int STEP_MC_THREADS = 128;
 inline int step_mc_blocks(int64_t n) { return (int)((n + STEP_MC_THREADS - 1) / STEP_MC_THREADS); }
+// fused finalize + step of the skew-packed streaming kernel: 32 test indices per block
+constexpr int STEP_PK_THREADS = 1024;
+constexpr int STEP_PK_MAX_GRID = 1024;  // streaming CTAs whose window starts fit the block's table
+inline int step_pk_blocks(int64_t n) { return (int)((n + 31) / 32); }
 // Diagonal step over several CTAs per trajectory.  With k1 != nullptr the
 // K1 partial sums of trajectories b0 .. b0+nb-1 are finalised in the same
 // kernel (the advection term is written to the history ring first).
 cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
                                 int nbk, cudaStream_t s);
+cudaError_t step_diag_packed_launch(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a, int b0,
+                                    int nb, int nbk, cudaStream_t s);
 cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch,
                                  int step_index, cudaStream_t s);
 cudaError_t selftest_wait_launch(int* err, uint64_t limit_ns, cudaStream_t s);
@@ -226,6 +254,12 @@ cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int b
 // ------------------------------------------------------------ conversion
 cudaError_t convert_rows_launch(const double* src, int64_t rows, int64_t n, int64_t np,
                                 int storage, uint8_t* dst, cudaStream_t s);
+// Dense FP64 rows (i, j) for i in [i0, i0 + rows/n) -> skew-packed stored rows.
+cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t n, int64_t i0, int64_t lp,
+                                       int storage, uint8_t* dst, cudaStream_t s);
+// Adds the skew probes of FP64 rows (i, j), i from i0, into acc[0..2]
+// (probe 1, probe 2, sum of squares).
+cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t i0, double* acc, cudaStream_t s);
 cudaError_t convert_panels_launch(const double* src, int64_t n, int64_t r, int64_t rb,
                                   int storage, uint8_t* dst, cudaStream_t s);
 
@@ -233,7 +267,7 @@ cudaError_t convert_panels_launch(const double* src, int64_t n, int64_t r, int64
 
 // ------------------------------------------------------------ ROM objects
 struct grom_rom {
-  int n = 0, form = 0, rank = 0, storage = 0, order = 3, max_batch = 1;
+  int n = 0, form = 0, rank = 0, storage = 0, order = 3, max_batch = 1, layout = 0;
   int64_t np = 0;
   double nu = 0, dt = 0;
   cudaStream_t stream = nullptr;
@@ -254,6 +288,9 @@ struct grom_rom {
   double* part = nullptr;       // streaming / CP partials
   size_t part_bytes = 0;
   int* err = nullptr;           // device flags [0] = mask, [1] = first bad
+  void* k1p_dg = nullptr;       // packed layout: segment values D u_i
+  double* k1p_tg = nullptr;     // packed layout: transposed-term windows
+  double* probe = nullptr;      // packed layout: skew probe accumulators (3)
   grom::K1Plan k1{};
   grom::K3Plan k3{};
   size_t total_bytes = 0;
@@ -282,8 +319,14 @@ struct grom_traj {
   double* red = nullptr;    // multi-CTA step partials
   unsigned int* cnt = nullptr;
   cudaGraphExec_t graph = nullptr;  // captured block of steps (no per-step outputs)
+  cudaGraph_t graph_tmpl = nullptr; // its template (kept for event-node updates)
   int graph_steps = 0;
   int graph_version = -1;
+  // kernel-timing event nodes of a graph captured with profiling on: node and
+  // its index in the graph's event sequence (pair k: 2k start, 2k + 1 stop)
+  std::vector<cudaGraphNode_t> prof_nodes;
+  std::vector<int> prof_index;
+  int prof_pairs = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int32_t* active = nullptr;      // serving slots: 1 = occupied (nullable: all active)

@@ -7,6 +7,10 @@ cudaError_t k1_dispatch_f64(int qm, int nb, const K1Plan&, const K1Args&, int, c
 cudaError_t k1_dispatch_f32x2(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
 cudaError_t k1_dispatch_f32(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
 cudaError_t k1_dispatch_bf16(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1p_dispatch_f64(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1p_dispatch_f32x2(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1p_dispatch_f32(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1p_dispatch_bf16(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
 
 static int pow2_ceil(int64_t x) {
   int p = 1;
@@ -34,15 +38,31 @@ static int epv(int storage) {
   return 1;
 }
 
-K1Plan k1_plan(int64_t n, int storage, int sm_count) {
+K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed) {
   K1Plan p{};
   p.n = n;
   p.np = padded_n(n);
-  p.row_bytes = p.np * storage_elem_bytes(storage);
-  // vector positions per row and the consumer mapping (see k1_stream.cuh)
-  const int64_t P = p.np / epv(storage);
-  p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
-  const int64_t rpr = P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
+  p.packed = packed;
+  p.h = n / 2;
+  p.lp = packed ? padded_n(p.h > 0 ? p.h : 1) : p.np;
+  p.row_bytes = p.lp * storage_elem_bytes(storage);
+  // vector positions per row and the consumer mapping (see k1_stream.cuh and
+  // k1_packed.cuh)
+  const int64_t P = p.lp / epv(storage);
+  int64_t rpr;
+  if (packed) {
+    // up to four row groups per position, kept inside one warp
+    int64_t R = 1;
+    while (R < 4 && 2 * R * P <= K1_CONSUMERS) R *= 2;
+    p.rg = (int)R;
+    const int64_t W = K1_CONSUMERS / R;
+    p.qm = pow2_ceil((P + W - 1) / W);
+    rpr = R;
+  } else {
+    p.rg = 1;
+    p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
+    rpr = P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
+  }
   const int64_t rmax = 8 / p.qm;  // rows a consumer thread holds in registers per chunk
   p.rpc = K1_STAGE_BYTES / p.row_bytes;
   if (p.rpc > rmax * rpr) p.rpc = rmax * rpr;
@@ -63,7 +83,34 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count) {
   while (nb > 1 && (acc_regs(storage) * p.qm * nb > 64 || nb * u_bytes_per_traj > budget)) nb >>= 1;
   p.nb_max = nb;
   p.smem = (size_t)base + (size_t)nb * u_bytes_per_traj;
+  p.lw = p.maxseg - 1 + p.lp;
   return p;
+}
+
+size_t k1p_dg_bytes(const K1Plan& p, int storage) {
+  const size_t rs = (storage == GROM_F64 || storage == GROM_F32X2) ? 8 : 4;
+  return (size_t)p.grid * p.maxseg * p.nb_max * p.lp * rs;
+}
+
+size_t k1p_tg_bytes(const K1Plan& p) { return (size_t)p.grid * p.nb_max * p.lw * sizeof(double); }
+
+static cudaError_t k1_dispatch(const K1Plan& pl, int storage, int nb, const K1Args& a, int b0, cudaStream_t s) {
+  if (pl.packed) {
+    switch (storage) {
+      case GROM_F64: return k1p_dispatch_f64(pl.qm, nb, pl, a, b0, s);
+      case GROM_F32X2: return k1p_dispatch_f32x2(pl.qm, nb, pl, a, b0, s);
+      case GROM_F32: return k1p_dispatch_f32(pl.qm, nb, pl, a, b0, s);
+      case GROM_BF16: return k1p_dispatch_bf16(pl.qm, nb, pl, a, b0, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  switch (storage) {
+    case GROM_F64: return k1_dispatch_f64(pl.qm, nb, pl, a, b0, s);
+    case GROM_F32X2: return k1_dispatch_f32x2(pl.qm, nb, pl, a, b0, s);
+    case GROM_F32: return k1_dispatch_f32(pl.qm, nb, pl, a, b0, s);
+    case GROM_BF16: return k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a0, int batch, cudaStream_t s) {
@@ -76,14 +123,7 @@ cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a0, int bat
     // shared memory for the template width actually launched
     const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
     pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
-    cudaError_t e;
-    switch (storage) {
-      case GROM_F64: e = k1_dispatch_f64(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_F32X2: e = k1_dispatch_f32x2(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_F32: e = k1_dispatch_f32(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_BF16: e = k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s); break;
-      default: e = cudaErrorInvalidValue;
-    }
+    cudaError_t e = k1_dispatch(pl, storage, nb, a, b0, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -99,21 +139,16 @@ cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& 
     K1Args a = a0;
     const int rem = batch - b0;
     a.nb = rem < plan.nb_max ? rem : plan.nb_max;
+    // the finalize (dense or packed) is fused into the step kernel
     a.skip_finalize = 1;
     const int nb = pow2_ceil(a.nb);
     K1Plan pl = plan;
     const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
     pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
-    cudaError_t e;
-    switch (storage) {
-      case GROM_F64: e = k1_dispatch_f64(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_F32X2: e = k1_dispatch_f32x2(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_F32: e = k1_dispatch_f32(pl.qm, nb, pl, a, b0, s); break;
-      case GROM_BF16: e = k1_dispatch_bf16(pl.qm, nb, pl, a, b0, s); break;
-      default: e = cudaErrorInvalidValue;
-    }
+    cudaError_t e = k1_dispatch(pl, storage, nb, a, b0, s);
     if (e != cudaSuccess) return e;
-    e = step_diag_mc_launch(st, step_index, &pl, &a, b0, a.nb, nb, s);
+    e = plan.packed ? step_diag_packed_launch(st, step_index, pl, a, b0, a.nb, nb, s)
+                    : step_diag_mc_launch(st, step_index, &pl, &a, b0, a.nb, nb, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -416,10 +416,10 @@ cudaError_t k1_launch_one(const K1Plan& pl, const K1Args& a, int b0, cudaStream_
   auto kern = k1_stream_kernel<ST, QM, NB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
-  if (a.ev0) cudaEventRecord(a.ev0, s);
+  if (a.ev0) prof_record(a.ev0, s);
   kern<<<pl.grid, K1_THREADS, pl.smem, s>>>(pl, a, b0);
   e = cudaGetLastError();
-  if (e == cudaSuccess && a.ev1) e = cudaEventRecord(a.ev1, s);
+  if (e == cudaSuccess && a.ev1) e = prof_record(a.ev1, s);
   if (e != cudaSuccess) return e;
   if (a.skip_finalize) return cudaSuccess;
   const int64_t total = pl.n * a.nb;

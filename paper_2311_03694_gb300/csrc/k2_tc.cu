@@ -362,11 +362,11 @@ cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a,
                                                                 a.active, a.batch);
   cudaError_t e = cudaFuncSetAttribute(k2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
-  if (a.ev0) cudaEventRecord(a.ev0, s);
+  if (a.ev0) prof_record(a.ev0, s);
   k2_tc_kernel<<<(unsigned)(p.i_tiles * p.col_tiles * p.splits), K2_THREADS, p.smem, s>>>(*tmap, d);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.ev1) cudaEventRecord(a.ev1, s);
+  if (a.ev1) prof_record(a.ev1, s);
   const int64_t red = (int64_t)a.batch * p.n;
   k2_reduce_kernel<<<(unsigned)((red + 255) / 256), 256, 0, s>>>(d, a.c, a.c_stride, a.hist, a.taken, a.hist_stride,
                                                                  a.active, a.batch);

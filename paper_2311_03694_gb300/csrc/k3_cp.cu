@@ -279,36 +279,50 @@ __global__ void __launch_bounds__(256) k3_expand_kernel(const K3Shape sh, const 
     si[warp][lane] = i_part;
   }
   __syncthreads();
-  if (threadIdx.x < NB && threadIdx.x < a.nb) {
-    const int b = threadIdx.x, bgl = b0 + b;
+  // warp b closes trajectory b (NB <= K3_WARPS): lane 0 publishes the block's
+  // partials; in the last block to arrive the warp sums all blocks' partials
+  // (lane q adds blocks q, q+32, ... in order, then a fixed shuffle tree)
+  static_assert(NB <= K3_WARPS, "one warp per trajectory");
+  if (warp < NB && warp < a.nb) {
+    const int b = warp, bgl = b0 + b;
     if (a.active == nullptr || a.active[bgl]) {
-      double e = 0.0, inv = 0.0;
+      if (lane == 0) {
+        double e = 0.0, inv = 0.0;
 #pragma unroll
-      for (int w = 0; w < K3_WARPS; ++w) {
-        e += se[w][b];
-        inv += si[w][b];
+        for (int w = 0; w < K3_WARPS; ++w) {
+          e += se[w][b];
+          inv += si[w][b];
+        }
+        if (sbad[b]) {
+          atomicOr(st.err, DEV_ERR_NONFINITE);
+          atomicMin(st.first_bad, bgl);
+        }
+        double* r = st.red + ((int64_t)bgl * st.nblk + blockIdx.x) * 2;
+        r[0] = e;
+        r[1] = inv;
+        __threadfence();
+        last[b] = atomicAdd(&st.cnt[bgl], 1u) == (unsigned)(st.nblk - 1);
       }
-      if (sbad[b]) {
-        atomicOr(st.err, DEV_ERR_NONFINITE);
-        atomicMin(st.first_bad, bgl);
-      }
-      double* r = st.red + ((int64_t)bgl * st.nblk + blockIdx.x) * 2;
-      r[0] = e;
-      r[1] = inv;
-      __threadfence();
-      last[b] = atomicAdd(&st.cnt[bgl], 1u) == (unsigned)(st.nblk - 1);
+      __syncwarp();
       if (last[b]) {
         __threadfence();
         double es = 0.0, is = 0.0;
         const double* rr = st.red + (int64_t)bgl * st.nblk * 2;
-        for (int q = 0; q < st.nblk; ++q) {
+        for (int q = lane; q < st.nblk; q += 32) {
           es += __ldcg(rr + 2 * q);
           is += __ldcg(rr + 2 * q + 1);
         }
-        if (st.energy) st.energy[(int64_t)step_index * st.batch + bgl] = 0.5 * es;
-        if (st.invariant) st.invariant[(int64_t)step_index * st.batch + bgl] = is;
-        step_done(st, bgl, st.taken[bgl]);
-        st.cnt[bgl] = 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          es += __shfl_xor_sync(0xffffffffu, es, off);
+          is += __shfl_xor_sync(0xffffffffu, is, off);
+        }
+        if (lane == 0) {
+          if (st.energy) st.energy[(int64_t)step_index * st.batch + bgl] = 0.5 * es;
+          if (st.invariant) st.invariant[(int64_t)step_index * st.batch + bgl] = is;
+          step_done(st, bgl, st.taken[bgl]);
+          st.cnt[bgl] = 0u;
+        }
       }
     }
   }

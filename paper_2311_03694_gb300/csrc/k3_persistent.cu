@@ -373,15 +373,25 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k3p_kernel(const KPArgs p) {
     }
     if (!grid_barrier(p.bar, st.err)) return;
     // ---- 4: energy / invariant of this step
-    if (g == 0 && threadIdx.x < NB && threadIdx.x < p.batch && (st.energy || st.invariant)) {
-      const int b = threadIdx.x;
+    // warp b of CTA 0 sums trajectory b's CTA partials (lane q adds CTAs q,
+    // q+32, ... in order, then a fixed shuffle tree)
+    static_assert(NB <= KP_WARPS, "one warp per trajectory");
+    if (g == 0 && warp < NB && warp < p.batch && (st.energy || st.invariant)) {
+      const int b = warp;
       double ev = 0.0, iv = 0.0;
-      for (int q = 0; q < G; ++q) {
+      for (int q = lane; q < G; q += 32) {
         ev += __ldcg(p.red + ((int64_t)q * NB + b) * 2);
         iv += __ldcg(p.red + ((int64_t)q * NB + b) * 2 + 1);
       }
-      if (st.energy) st.energy[(int64_t)step * st.batch + b] = 0.5 * ev;
-      if (st.invariant) st.invariant[(int64_t)step * st.batch + b] = iv;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, off);
+        iv += __shfl_xor_sync(0xffffffffu, iv, off);
+      }
+      if (lane == 0) {
+        if (st.energy) st.energy[(int64_t)step * st.batch + b] = 0.5 * ev;
+        if (st.invariant) st.invariant[(int64_t)step * st.batch + b] = iv;
+      }
     }
   }
   // write the owned rows' history back into the ring (n^l of the newest

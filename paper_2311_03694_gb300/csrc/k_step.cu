@@ -51,6 +51,55 @@ __device__ __forceinline__ void block_sum2(double& x, double& y, double* sh) {
   }
 }
 
+// One element of the diagonal step: u^{l+1}_i from the history and n^l_i = nl.
+__device__ __forceinline__ void step_elem(const StepArgs& a, double* h, int64_t n, int64_t l, int k, int64_t i,
+                                          double nl, double& e_part, double& i_part, int& bad) {
+  const double mb = a.mass_diag ? a.mass_diag[i] : 1.0;
+  const double ld = a.lin_diag ? a.lin_diag[i] : 0.0;
+  const double f = a.forcing ? a.forcing[i] : 0.0;
+  const double inv_dt = 1.0 / a.dt;
+  double ext = 0.0, bdf = 0.0, u0 = 0.0;
+  for (int q = 0; q < k; ++q) {
+    const int64_t m = ((l - q) % 3 + 3) % 3;
+    const double uq = h[m * n + i];
+    const double nq = q == 0 ? nl : h[(3 + m) * n + i];
+    if (q == 0) u0 = uq;
+    ext += c_alpha[k - 1][q] * (nq + ld * uq + f);
+    bdf += c_beta[k - 1][q + 1] * inv_dt * uq;
+  }
+  const double un = (-ext - mb * bdf) * a.hdiag[k - 1][i];
+  i_part = u0 * nl;
+  e_part = mb * un * un;
+  bad = !isfinite(un);
+  h[((l + 1) % 3) * n + i] = un;
+}
+
+// Called by all lanes of one warp of the last block of trajectory b to
+// arrive: sums the nblk per-block (energy, invariant) partials (lane q adds
+// blocks q, q+32, ... in order, then a fixed shuffle tree), writes the outputs
+// and advances the step count.
+__device__ __forceinline__ void step_finish_last(const StepArgs& a, int b, int64_t l, int step_index) {
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  double e = 0.0, inv = 0.0;
+  const double* rr = a.red + (int64_t)b * a.nblk * 2;
+  for (int q = lane; q < a.nblk; q += 32) {
+    e += __ldcg(rr + 2 * q);
+    inv += __ldcg(rr + 2 * q + 1);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, off);
+    inv += __shfl_xor_sync(0xffffffffu, inv, off);
+  }
+  if (lane == 0) {
+    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e;
+    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = inv;
+    step_done(a, b, l);
+    a.cnt[b] = 0u;
+  }
+}
+
 __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
   atomicOr(a.err, DEV_ERR_NONFINITE);
   atomicMin(a.first_bad, b);
@@ -97,24 +146,7 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
     } else {
       nl = h[(3 + l % 3) * n + i];
     }
-    const double mb = a.mass_diag ? a.mass_diag[i] : 1.0;
-    const double ld = a.lin_diag ? a.lin_diag[i] : 0.0;
-    const double f = a.forcing ? a.forcing[i] : 0.0;
-    const double inv_dt = 1.0 / a.dt;
-    double ext = 0.0, bdf = 0.0, u0 = 0.0;
-    for (int q = 0; q < k; ++q) {
-      const int64_t m = ((l - q) % 3 + 3) % 3;
-      const double uq = h[m * n + i];
-      const double nq = q == 0 ? nl : h[(3 + m) * n + i];
-      if (q == 0) u0 = uq;
-      ext += c_alpha[k - 1][q] * (nq + ld * uq + f);
-      bdf += c_beta[k - 1][q + 1] * inv_dt * uq;
-    }
-    const double un = (-ext - mb * bdf) * a.hdiag[k - 1][i];
-    i_part = u0 * nl;
-    e_part = mb * un * un;
-    my_bad = !isfinite(un);
-    h[((l + 1) % 3) * n + i] = un;
+    step_elem(a, h, n, l, k, i, nl, e_part, i_part, my_bad);
   }
   if (my_bad) bad = 1;
   block_sum2(e_part, i_part, sh);
@@ -128,19 +160,7 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
     last = prev == (unsigned)(a.nblk - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double e = 0.0, inv = 0.0;
-    const double* r = a.red + (int64_t)b * a.nblk * 2;
-    for (int q = 0; q < a.nblk; ++q) {
-      e += __ldcg(r + 2 * q);
-      inv += __ldcg(r + 2 * q + 1);
-    }
-    if (a.energy) a.energy[(int64_t)step_index * a.batch + b] = 0.5 * e;
-    if (a.invariant) a.invariant[(int64_t)step_index * a.batch + b] = inv;
-    step_done(a, b, l);
-    a.cnt[b] = 0u;
-  }
+  if (last && threadIdx.x < 32) step_finish_last(a, b, l, step_index);
 }
 
 cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
@@ -151,6 +171,113 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
   if (k1) pl = *k1;
   if (k1a) ka = *k1a;
   k_step_diag_mc<<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, pl, ka, k1 ? 1 : 0, b0, nbk);
+  return cudaGetLastError();
+}
+
+// Diagonal step fused with the finalize of the skew-packed streaming kernel
+// (k1_packed.cuh): n^l_i = (row sums of test index i) - (transposed-term
+// windows of every CTA at k = i), then the step of element i.  A block covers
+// 32 test indices of one trajectory; warp w sums the windows of CTAs
+// [w G/32, (w+1) G/32) and warp 0 adds the row sums and steps the elements.
+// Energy/invariant partials of the blocks are summed in block order by the
+// last block to arrive, which also advances the step count.
+__global__ void __launch_bounds__(STEP_PK_THREADS) k_step_diag_packed(const StepArgs a, const int step_index,
+                                                                      const K1Plan pl, const K1Args k1a,
+                                                                      const int b0, const int nbk) {
+  __shared__ double sh[32][33];
+  __shared__ int fi_tab[STEP_PK_MAX_GRID];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bl = blockIdx.y;
+  const int b = b0 + bl;
+  if (a.active && !a.active[b]) return;  // uniform over the block
+  const int64_t n = a.n;
+  const int G = pl.grid;
+  const int64_t T = pl.T;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) fi_tab[g] = (int)(((int64_t)g * T / G) / pl.cpi);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (i < n) {
+    const int g0 = warp * G / 32, g1 = (warp + 1) * G / 32;
+    if (pl.lw <= n && g1 - g0 <= 8) {
+      // at most one window entry per CTA: independent loads, summed in CTA order
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int g = g0 + q;
+        v[q] = 0.0;
+        if (g < g1) {
+          int64_t w = i - fi_tab[g] - 1;
+          if (w < 0) w += n;
+          if (w < pl.lw) v[q] = k1a.tg[((int64_t)g * nbk + bl) * pl.lw + w];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += v[q];
+    } else {
+      for (int g = g0; g < g1; ++g) {
+        int64_t w = i - fi_tab[g] - 1;
+        if (w < 0) w += n;
+        const double* win = k1a.tg + ((int64_t)g * nbk + bl) * pl.lw;
+        for (; w < pl.lw; w += n) s += win[w];
+      }
+    }
+  }
+  sh[warp][lane] = s;
+  double rs = 0.0;
+  if (warp == 0 && i < n) {
+    const int64_t g_lo = ((i * pl.cpi + 1) * G - 1) / T, g_hi = (((i + 1) * pl.cpi) * G - 1) / T;
+    for (int64_t g = g_lo; g <= g_hi; ++g) {
+      const double* src = k1a.part + ((g * pl.maxseg + (i - fi_tab[g])) * (K1_CONSUMERS / 32)) * nbk + bl;
+      double v[K1_CONSUMERS / 32];
+#pragma unroll
+      for (int w = 0; w < K1_CONSUMERS / 32; ++w) v[w] = src[w * nbk];
+#pragma unroll
+      for (int w = 0; w < K1_CONSUMERS / 32; ++w) rs += v[w];
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  const int64_t l = a.taken[b];
+  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
+  double* h = a.hist + b * a.hist_stride;
+  double e_part = 0.0, i_part = 0.0;
+  int bad = 0;
+  if (i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 32; ++w) t += sh[w][lane];
+    const double nl = rs - t;
+    h[(3 + l % 3) * n + i] = nl;
+    step_elem(a, h, n, l, k, i, nl, e_part, i_part, bad);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e_part += __shfl_down_sync(0xffffffffu, e_part, off);
+    i_part += __shfl_down_sync(0xffffffffu, i_part, off);
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (bad) report_nonfinite(a, b);
+    double* r = a.red + ((int64_t)b * a.nblk + blockIdx.x) * 2;
+    r[0] = e_part;
+    r[1] = i_part;
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.cnt[b], 1u);
+    last = prev == (unsigned)(a.nblk - 1);
+  }
+  __syncwarp();
+  if (last) step_finish_last(a, b, l, step_index);
+}
+
+cudaError_t step_diag_packed_launch(const StepArgs& a0, int step_index, const K1Plan& pl, const K1Args& k1a, int b0,
+                                    int nb, int nbk, cudaStream_t s) {
+  if (pl.grid > STEP_PK_MAX_GRID) return cudaErrorInvalidValue;
+  StepArgs a = a0;
+  a.nblk = step_pk_blocks(a.n);
+  dim3 grid((unsigned)a.nblk, (unsigned)nb);
+  k_step_diag_packed<<<grid, STEP_PK_THREADS, 0, s>>>(a, step_index, pl, k1a, b0, nbk);
   return cudaGetLastError();
 }
 

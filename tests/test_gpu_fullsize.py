@@ -45,10 +45,11 @@ def _oracle_rows(u):
     return np.concatenate(out)
 
 
+@pytest.mark.parametrize("layout", ["dense", "skew_packed"])
 @pytest.mark.parametrize("storage", ["bf16", "f64", "f32x2", "f32"])
-def test_full_size_single_trajectory(tensor, storage):
+def test_full_size_single_trajectory(tensor, storage, layout):
     u = synth.initial_condition(N, SEED)[0]
-    rom = grom.Rom(N, "full", storage, tensor=tensor, stiffness=synth.diag_stiffness(N))
+    rom = grom.Rom(N, "full", storage, tensor=tensor, stiffness=synth.diag_stiffness(N), layout=layout)
     ud = torch.from_numpy(u[None, :].copy()).cuda()
     cd = torch.empty_like(ud)
     rom.nonlinear(ud, cd)
@@ -66,12 +67,13 @@ def test_full_size_single_trajectory(tensor, storage):
     rom.close()
 
 
-def test_full_size_stepping_headline_configuration(tensor):
+@pytest.mark.parametrize("layout", ["dense", "skew_packed"])
+def test_full_size_stepping_headline_configuration(tensor, layout):
     # the bench's headline: BF16 storage, one trajectory, BDF3/EXT3 with graphs
     steps = 24
     a = synth.diag_stiffness(N)
     u0 = synth.initial_condition(N, SEED)[0]
-    rom = grom.Rom(N, "full", "bf16", tensor=tensor, stiffness=a, nu=1e-2, dt=1e-3)
+    rom = grom.Rom(N, "full", "bf16", tensor=tensor, stiffness=a, nu=1e-2, dt=1e-3, layout=layout)
     tr = grom.Trajectories(rom, u0[None, :])
     tr.step(steps)
     code, _ = tr.status()
