@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ROM steps/s at N=1024 (full vs CPD, FP64 vs BF16), HBM/TC roofline %, p99 latency"
 UNIT = "steps/s"
 NU, DT = 1e-2, 1e-3
-HEADLINE = ("full", "bf16", "skew_packed")
+HEADLINE = ("full", "bf16")  # + the layout chosen by --layout (skew-packed by default)
 VARIANTS = [("full", "bf16", "skew_packed"), ("full", "f32", "skew_packed"), ("full", "f32x2", "skew_packed"),
             ("full", "f64", "skew_packed"), ("full", "bf16", "dense"), ("full", "f32", "dense"),
             ("full", "f32x2", "dense"), ("full", "f64", "dense"), ("cp_skew", "bf16", "dense"),
@@ -66,6 +66,8 @@ def parse_args():
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-slots", type=int, default=64)
     p.add_argument("--json-out", default="")
+    p.add_argument("--layout", default="skew_packed", choices=["skew_packed", "dense"],
+                   help="stored layout of the headline tensor")
     return p.parse_args()
 
 
@@ -352,7 +354,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(n, rank),
+        "config": _config(n, rank, args.layout),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -373,12 +375,17 @@ def _packed_len(n):
     return (max(n // 2, 1) + 63) // 64 * 64
 
 
-def _config(n, rank):
-    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage in the skew-packed layout "
-                        "(one entry of each pair C_ijk = -C_kji), FP32 accumulation, FP64 state; "
-                        "CP-structured skew tensor (R=%d) + 1e-3 skew residual; one trajectory per GPU" % (n, rank),
-            "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT, "layout": "skew_packed",
-            "l2": "inputs larger than L2 (stored tensor %.2f GB per step)" % (n * n * _packed_len(n) * 2 / 1e9)}
+def _row_len(n, layout):
+    return _packed_len(n) if layout == "skew_packed" else (n + 63) // 64 * 64
+
+
+def _config(n, rank, layout):
+    how = ("in the skew-packed layout (one entry of each pair C_ijk = -C_kji)" if layout == "skew_packed"
+           else "in the dense layout")
+    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage %s, FP32 accumulation, FP64 state; "
+                        "CP-structured skew tensor (R=%d) + 1e-3 skew residual; one trajectory per GPU" % (n, how, rank),
+            "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT, "layout": layout,
+            "l2": "inputs larger than L2 (stored tensor %.2f GB per step)" % (n * n * _row_len(n, layout) * 2 / 1e9)}
 
 
 # -------------------------------------------------------------------- main
@@ -415,7 +422,7 @@ def main():
         return grom.Rom(n, form, storage, factors=factors, stiffness=a, nu=NU, dt=DT)
 
     # ---------------------------------------------------- headline, timed
-    rom = make_rom(*HEADLINE)
+    rom = make_rom(*HEADLINE, args.layout)
     tr = grom.Trajectories(rom, u0)
     stream = torch.cuda.current_stream()
     tr.step(args.warmup)
@@ -454,14 +461,16 @@ def main():
     k1_ms, k1_launches = rom.profile_read()
     rom.profile(False)
 
-    # roofline of the dominant kernel (packed K1 streaming contraction): the
-    # stored skew-packed tensor, N * N rows of round_up(N/2, 64) BF16 values
+    # roofline of the dominant kernel (K1 streaming contraction): the stored
+    # tensor, N * N rows of round_up(N/2, 64) (skew-packed) or round_up(N, 64)
+    # (dense) BF16 values
     k1_avg_ms = k1_ms / max(1, k1_launches)
-    alg_bytes = float(n) * n * _packed_len(n) * STORAGE_BYTES[HEADLINE[1]]
+    alg_bytes = float(n) * n * _row_len(n, args.layout) * STORAGE_BYTES[HEADLINE[1]]
     achieved = alg_bytes / (k1_avg_ms * 1e-3) / 1e9
+    kname = "k1_packed" if args.layout == "skew_packed" else "k1_stream"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": kernel_traffic("k1_packed_bf16_n%d" % n),
-                "kernel": "k1_packed_kernel<BF16> (finalize excluded)", "peak_kind": peak_kind,
+                "frac": achieved / hbm_peak, "traffic": kernel_traffic("%s_bf16_n%d" % (kname, n)),
+                "kernel": "%s_kernel<BF16> (finalize excluded)" % kname, "peak_kind": peak_kind,
                 "kernel_ms": k1_avg_ms, "kernel_launches": k1_launches,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "timing": "CUDA events around each launch in a second timed run of the same %d steps "
@@ -483,7 +492,7 @@ def main():
     e2e = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
            "api": "grom_step_host(traj, 1, u_in=pinned host, u_out=pinned host)"}
     tr.close()
-    launches_per_step = 2  # packed K1 streaming kernel; its finalize fused with the BDF3/EXT3 step
+    launches_per_step = 2  # K1 streaming kernel; its finalize fused with the BDF3/EXT3 step
 
     # -------------------------------------------- errors vs the FP64 oracle
     cores = os.cpu_count() or 1
@@ -626,7 +635,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": _config(n, R),
+        "config": _config(n, R, args.layout),
         "roofline": roofline,
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
