@@ -66,6 +66,7 @@ def parse_args():
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-slots", type=int, default=64)
     p.add_argument("--json-out", default="")
+    p.add_argument("--svd-ranks", default="64,256", help="SVD-ROM variant ranks ('none' to skip)")
     p.add_argument("--layout", default="skew_packed", choices=["skew_packed", "dense"],
                    help="stored layout of the headline tensor")
     return p.parse_args()
@@ -137,6 +138,27 @@ def workload(n, rank, seed, device):
     C = synth.cp_tensor_device(U, V, W, seed, s, device)
     a = synth.diag_stiffness(n)
     return C, (U, V, W), a
+
+
+def svd_of_workload(C, ranks, torch):
+    """Truncated SVD of the tensor's matricization over the advecting index
+    (the SVD-ROM's offline step, Sec. 4.4.2), on the device in FP64: the
+    eigenpairs of M M^T give U and sigma, and V = M^T U / sigma.  Returns
+    {rank: (U, sigma, V)} with V laid out n x rank x n (V[i][r][k])."""
+    n = C.shape[0]
+    M = C.permute(1, 0, 2).reshape(n, n * n)
+    lam, vec = torch.linalg.eigh(M @ M.T)
+    order = torch.argsort(lam, descending=True)
+    out = {}
+    for r in ranks:
+        idx = order[:r]
+        sigma = torch.sqrt(torch.clamp(lam[idx], min=0.0))
+        U = vec[:, idx].contiguous()
+        V = (M.T @ U) / sigma[None, :]
+        out[r] = (U, sigma.contiguous(), V.reshape(n, n, r).permute(0, 2, 1).contiguous())
+        del V
+    del M
+    return out
 
 
 def peaks():
@@ -538,6 +560,35 @@ def main():
         entry["status"] = grom.ERRORS.get(vcode, "OK") if vcode else "OK"
         variants[key] = entry
         vrom.close()
+    # SVD-ROM (Sec. 4.4.2) at the requested ranks: skew-packed BF16 slices
+    if args.svd_ranks and args.svd_ranks != "none" and args.variants != "none":
+        ranks = [int(x) for x in args.svd_ranks.split(",")]
+        for r, (Us, ss, Vs) in svd_of_workload(C, ranks, torch).items():
+            for storage in ("bf16", "f64"):
+                vrom = grom.Rom(n, "svd", storage, factors=(Us, ss, Vs), stiffness=a, nu=NU, dt=DT,
+                                layout="skew_packed")
+                vsteps = max(10, min(args.steps, 200))
+                vms, vcode, per = time_variant(grom, torch, vrom, u0, vsteps, 3, flush=flush)
+                wms, _, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
+                entry = {"rank": r, "cr_svd": n / r, "layout": "skew_packed", "ms_per_step": vms,
+                         "steps_per_s": 1e3 / vms, "l2": "flushed before every step",
+                         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+                         "warm_l2_ms_per_step": wms, "warm_l2_steps_per_s": 1e3 / wms,
+                         "stored_bytes": n * r * _packed_len(n) * STORAGE_BYTES[storage]}
+                if rank_id == 0:
+                    ud = torch.from_numpy(u0.copy()).cuda()
+                    cd = torch.empty_like(ud)
+                    vrom.nonlinear(ud, cd)
+                    torch.cuda.synchronize()
+                    ref = oracle.nonlinear_svd(Us.cpu().numpy(), ss.cpu().numpy(), Vs.cpu().numpy(), u0[0])
+                    entry["eval_rel_err_vs_fp64_oracle"] = rel(cd.cpu().numpy()[0], ref)
+                    entry["tolerance"] = TOL[storage]
+                    entry["svd_vs_full_model_gap"] = rel(ref, c_full)
+                entry["status"] = grom.ERRORS.get(vcode, "OK") if vcode else "OK"
+                variants["svd_%s_packed_R%d" % (storage, r)] = entry
+                vrom.close()
+            del Us, ss, Vs
+        torch.cuda.empty_cache()
     del flush
 
     # ------------------------------------------- batched trajectories (K2)

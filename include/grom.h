@@ -54,6 +54,15 @@ typedef int32_t grom_status;
 #define GROM_FORM_CP_SKEW 2 /* skew CP blocks fa=U, fb=V, fc=W (eq. skew_abc_struct):
                                evaluated as c = U(p o q) - W(p o s) with p = V^T u,
                                q = W^T u, s = U^T u; paper rank 2*rank            */
+#define GROM_FORM_SVD 3     /* SVD-ROM (Sec. 4.4.2): truncated SVD of the tensor's
+                               matricization over the advecting index,
+                               C_ijk ~ sum_r U_jr sigma_r V[i][r][k], with
+                               fa = U (n x rank), fb = sigma (rank values) and
+                               fc = V (n x rank x n, V[i][r][k], each slice
+                               V[.][r][.] an n x n matrix over (test, advected));
+                               evaluated as c_i = sum_r beta_r sum_k V[i][r][k] u_k,
+                               beta = sigma o (U^T u); storage and layout apply to V
+                               (the skew-packed layout needs each slice skew) */
 
 /* Storage (and arithmetic) type of the advection operator on the device.
  * The state update, the reduced solve and the energy/invariant sums are FP64
@@ -93,12 +102,13 @@ typedef struct grom_traj grom_traj;
 typedef struct grom_desc {
   int32_t n;       /* number of modes N >= 1                                       */
   int32_t form;    /* GROM_FORM_*                                                  */
-  int32_t rank;    /* CP rank (columns of each factor); ignored for FULL          */
+  int32_t rank;    /* CP or SVD rank (columns of each factor); ignored for FULL   */
   int32_t storage; /* GROM_F64, GROM_F32X2, GROM_F32, GROM_BF16                     */
   /* FULL: n*n*n doubles, host or device; NULL together with defer_tensor = 1
    * to upload the rows later with grom_upload_tensor_slab. */
   const double* tensor;
-  /* CP forms: three n x rank factor matrices, host or device. */
+  /* CP forms: three n x rank factor matrices, host or device.  SVD form: see
+   * GROM_FORM_SVD (U: n x rank, sigma: rank, V: n x rank x n). */
   const double* fa;
   const double* fb;
   const double* fc;
@@ -122,7 +132,7 @@ typedef struct grom_desc {
   int32_t defer_tensor; /* FULL only: 1 = rows come from grom_upload_tensor_slab  */
   int32_t max_batch;    /* largest batch passed to grom_nonlinear/grom_traj_create
                            (sizes the library's scratch); 0 means 1              */
-  int32_t layout;       /* FULL only: GROM_LAYOUT_DENSE (0) or GROM_LAYOUT_SKEW_PACKED */
+  int32_t layout;       /* FULL and SVD: GROM_LAYOUT_DENSE (0) or GROM_LAYOUT_SKEW_PACKED */
   int32_t reserved[3];  /* must be zero                                           */
 } grom_desc;
 

@@ -63,6 +63,7 @@ def _load():
             "oracle_nonlinear_cp_skew": [i64, i64, vp, vp, vp, vp, vp],
             "oracle_cp_skew_expand": [i64, i64, vp, vp, vp, vp, vp, vp],
             "oracle_cp_reconstruct": [i64, i64, vp, vp, vp, vp],
+            "oracle_nonlinear_svd": [i64, i64, vp, vp, vp, vp, vp],
             "oracle_bdf_ext_coefficients": [ctypes.c_int, vp, vp],
             "oracle_cholesky_solve": [i64, vp, vp, vp],
             "oracle_set_threads": [ctypes.c_int],
@@ -76,7 +77,7 @@ def _load():
         lib.oracle_get_threads.restype = ctypes.c_int
         lib.oracle_rom_step.argtypes = [ctypes.POINTER(_Rom), vp, i64, vp, vp]
         lib.oracle_rom_step.restype = ctypes.c_int
-        for name in ("oracle_cr_als", "oracle_cr_als_skew", "oracle_cost_reduction"):
+        for name in ("oracle_cr_als", "oracle_cr_als_skew", "oracle_cost_reduction", "oracle_cr_svd"):
             fn = getattr(lib, name)
             fn.argtypes = [i64, i64]
             fn.restype = dbl
@@ -151,6 +152,45 @@ def cp_reconstruct(A, B, Cf):
     return X
 
 
+def nonlinear_svd(U, sigma, V, u):
+    """SVD-ROM advection term (Sec. 4.4.2): c_i = sum_r sigma_r (U^T u)_r sum_k V[i][r][k] u_k.
+
+    U is n x r, sigma has r entries, V is n x r x n (V[i][r][k])."""
+    U, sigma, V, u = _f64(U), _f64(sigma), _f64(V), _f64(u)
+    n, r = U.shape
+    assert sigma.shape == (r,) and V.shape == (n, r, n)
+    c = np.empty(n)
+    _load().oracle_nonlinear_svd(n, r, _p(U), _p(sigma), _p(V), _p(u), _p(c))
+    return c
+
+
+def advecting_matricization(C):
+    """The tensor unfolded over its advecting index: row j holds the n x n
+    matrix (i, k) -> C_ijk, flattened row-major (Sec. 4.4.1)."""
+    n = C.shape[0]
+    return np.ascontiguousarray(np.transpose(_f64(C), (1, 0, 2)).reshape(n, n * n))
+
+
+def svd_factors(C, r):
+    """Rank-r truncated SVD of the advecting-index matricization (numpy's SVD
+    as the library step), returned as (U, sigma, V) with V[i][m][k] the
+    right singular vector m read as an n x n matrix over (i, k)."""
+    n = C.shape[0]
+    Um, s, Vt = np.linalg.svd(advecting_matricization(C), full_matrices=False)
+    V = np.ascontiguousarray(Vt[:r].reshape(r, n, n).transpose(1, 0, 2))
+    return np.ascontiguousarray(Um[:, :r]), np.ascontiguousarray(s[:r]), V
+
+
+def svd_reconstruct(U, sigma, V):
+    """C_ijk = sum_m U_jm sigma_m V[i][m][k] (plain loops over the rank)."""
+    U, sigma, V = _f64(U), _f64(sigma), _f64(V)
+    n, r = U.shape
+    X = np.zeros((n, n, n))
+    for m in range(r):
+        X += sigma[m] * U[None, :, m, None] * V[:, None, m, :]
+    return X
+
+
 def bdf_ext_coefficients(k):
     beta, alpha = np.empty(4), np.empty(3)
     _load().oracle_bdf_ext_coefficients(int(k), _p(beta), _p(alpha))
@@ -176,13 +216,14 @@ def cholesky_solve(L, b):
 class Rom:
     """A reduced model for the oracle stepper.
 
-    form: "full" (C is n x n x n), "cp" (factors A, B, Cf, each n x r) or
-    "cp_skew" (blocks U, V, W, each n x r).  A is the stiffness matrix (n x n,
+    form: "full" (C is n x n x n), "cp" (factors A, B, Cf, each n x r),
+    "cp_skew" (blocks U, V, W, each n x r) or "svd" (factors U (n x r),
+    sigma (r), V (n x r x n)).  A is the stiffness matrix (n x n,
     or a length-n diagonal), B the mass matrix (None = identity), L an
     optional explicit linear operator and f an optional constant forcing.
     """
 
-    FORMS = {"full": 0, "cp": 1, "cp_skew": 2}
+    FORMS = {"full": 0, "cp": 1, "cp_skew": 2, "svd": 3}
 
     def __init__(self, form, n, A, nu, dt, order=3, C=None, factors=None, B=None, L=None, f=None):
         self.n = int(n)
@@ -232,6 +273,10 @@ def cr_als(n, r):
 
 def cr_als_skew(n, r):
     return _load().oracle_cr_als_skew(n, r)
+
+
+def cr_svd(n, r):
+    return _load().oracle_cr_svd(n, r)
 
 
 def cost_reduction(n, r):

@@ -10,6 +10,7 @@
  *   - CP contraction    c_i = sum_r a_ir (sum_j b_jr u_j)(sum_k c_kr u_k)   (Sec. 3.1, eq. tc_ap)
  *   - skew CP structure A1=[U W], A2=[V V], A3=[W -U]              (Sec. 3.3, eq. skew_abc_struct)
  *   - CP reconstruction X_ijk = sum_r a_ir b_jr c_kr                (Sec. 2.3, eq. cpd)
+ *   - SVD-ROM contraction c_i = sum_r sigma_r (sum_j U_jr u_j)(sum_k V[i][r][k] u_k)   (Sec. 4.4.2)
  *   - BDFk/EXTk step (beta0/dt B + nu A) u^{l+1} = -sum_i alpha_i (n^{l+1-i} + L u^{l+1-i} + f)
  *                                                  - B sum_i beta_i/dt u^{l+1-i}   (Sec. 2.2, eq. nse_d1)
  *     solved with a dense Cholesky factorisation written here.
@@ -131,6 +132,34 @@ void oracle_cp_reconstruct(int64_t n, int64_t r, const double* A, const double* 
       }
 }
 
+/* SVD-ROM (Sec. 4.4.2).  The tensor's matricization over the advecting index
+ * j (rows j, columns the pairs (i, k)) is approximated by its truncated SVD
+ * U_R Sigma_R V_R^T; with V_R's column r read as the n x n matrix V[i][r][k],
+ *   C_ijk ~ sum_r U_jr sigma_r V[i][r][k],
+ * and the advection term of that tensor is
+ *   c_i = sum_r sigma_r (sum_j U_jr u_j) (sum_k V[i][r][k] u_k).
+ * U is n x r row-major, sigma has r entries, V is n x r x n row-major. */
+void oracle_nonlinear_svd(int64_t n, int64_t r, const double* U, const double* sigma, const double* V,
+                          const double* u, double* c) {
+  double* a = (double*)malloc((size_t)r * sizeof(double));
+  for (int64_t m = 0; m < r; ++m) {
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += U[j * r + m] * u[j];
+    a[m] = sigma[m] * s;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double ci = 0.0;
+    for (int64_t m = 0; m < r; ++m) {
+      double s = 0.0;
+      for (int64_t k = 0; k < n; ++k) s += V[(i * r + m) * n + k] * u[k];
+      ci += a[m] * s;
+    }
+    c[i] = ci;
+  }
+  free(a);
+}
+
 /* ---------------------------------------------------------------- stepper */
 
 /* BDFk/EXTk coefficients for k = 1, 2, 3 (standard values; the paper states
@@ -186,7 +215,8 @@ void oracle_cholesky_solve(int64_t n, const double* L, const double* b, double* 
 
 /* The reduced model stepped by the oracle.  form: 0 = dense tensor C,
  * 1 = general CP factors (fa, fb, fc; n x rank), 2 = skew CP blocks
- * (fa = U, fb = V, fc = W; n x rank).  A is n x n (dense), B is n x n or
+ * (fa = U, fb = V, fc = W; n x rank), 3 = SVD factors (fa = U, n x rank;
+ * fb = sigma, rank; fc = V, n x rank x n).  A is n x n (dense), B is n x n or
  * NULL for the identity, L is n x n or NULL, f has n entries or is NULL. */
 typedef struct {
   int64_t n;
@@ -210,8 +240,10 @@ static void rom_nonlinear(const oracle_rom* m, const double* u, double* c) {
     oracle_nonlinear_full(m->n, m->C, u, c);
   else if (m->form == 1)
     oracle_nonlinear_cp(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
-  else
+  else if (m->form == 2)
     oracle_nonlinear_cp_skew(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
+  else
+    oracle_nonlinear_svd(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
 }
 
 static void matvec(int64_t n, const double* M, const double* x, double* y) {
@@ -329,3 +361,5 @@ int oracle_rom_step(const oracle_rom* m, double* hist, int64_t nsteps, double* e
 double oracle_cr_als(int64_t n, int64_t r) { return (double)n * (double)n / (3.0 * (double)r); }
 double oracle_cr_als_skew(int64_t n, int64_t r) { return 2.0 * (double)n * (double)n / (3.0 * (double)r); }
 double oracle_cost_reduction(int64_t n, int64_t r) { return (double)n * (double)n / (3.0 * (double)r); }
+/* Compression ratio of the SVD-ROM: N^3 / (N^2 R) (Sec. 4.4.2). */
+double oracle_cr_svd(int64_t n, int64_t r) { return (double)n / (double)r; }

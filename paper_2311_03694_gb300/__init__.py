@@ -17,7 +17,7 @@ GROM_OK = 0
 ERRORS = {
     1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "TIMEOUT", 6: "BUDGET", 7: "UNSUPPORTED",
 }
-FORMS = {"full": 0, "cp": 1, "cp_skew": 2}
+FORMS = {"full": 0, "cp": 1, "cp_skew": 2, "svd": 3}
 STORAGE = {"f64": 0, "f32x2": 1, "f32": 2, "bf16": 3}
 STORAGE_BYTES = {"f64": 8, "f32x2": 8, "f32": 4, "bf16": 2}
 LAYOUTS = {"dense": 0, "skew_packed": 1}
@@ -187,11 +187,12 @@ def stored_layout(C, storage):
 class Rom:
     """A reduced-order model on the GPU (wraps grom_create / grom_destroy).
 
-    form: "full" (tensor n^3), "cp" (factors A, B, C) or "cp_skew" (U, V, W).
+    form: "full" (tensor n^3), "cp" (factors A, B, C), "cp_skew" (U, V, W) or
+    "svd" (factors (U, sigma, V): U n x rank, sigma rank, V n x rank x n).
     storage: "f64", "f32x2", "f32" or "bf16".  stiffness may be a length-n
     diagonal or an n x n matrix; mass None means identity.
-    layout (full form): "dense" or "skew_packed" (one entry of each pair
-    C_ijk = -C_kji stored; the tensor must be skew in i and k).
+    layout (full and svd forms): "dense" or "skew_packed" (one entry of each
+    pair C_ijk = -C_kji stored; the tensor, or each V slice, must be skew).
     """
 
     def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,

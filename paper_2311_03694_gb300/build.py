@@ -20,6 +20,7 @@ SOURCES = [
     "api.cu",
     "k_convert.cu",
     "k_step.cu",
+    "k_svd.cu",
     "k3_cp.cu",
     "k3_gemm.cu",
     "k3_persistent.cu",

@@ -114,8 +114,8 @@ static grom_status upload_rows(grom_rom* r, const double* src, int64_t rows, int
 // Streams dense FP64 tensor rows (i, j) for test indices [i0, i1) through a
 // staging buffer into the skew-packed layout, adding their skew probes.
 static grom_status upload_rows_packed(grom_rom* r, const double* src, int64_t i0, int64_t i1) {
-  const int64_t n = r->n;
-  const int64_t per_i = n * n;  // doubles per test index
+  const int64_t n = r->n, m = r->k1.m;
+  const int64_t per_i = m * n;  // doubles per test index
   const int64_t si = std::max<int64_t>(1, (int64_t)(256ll << 20) / (per_i * 8));
   double* stage = nullptr;
   grom_status st = dmalloc(&stage, (size_t)(std::min(si, i1 - i0) * per_i * 8), nullptr);
@@ -123,9 +123,9 @@ static grom_status upload_rows_packed(grom_rom* r, const double* src, int64_t i0
   for (int64_t a = i0; a < i1; a += si) {
     const int64_t cnt = std::min(si, i1 - a);
     cudaError_t e = cudaMemcpyAsync(stage, src + (a - i0) * per_i, (size_t)(cnt * per_i * 8), cudaMemcpyDefault, r->stream);
-    if (e == cudaSuccess) e = skew_probe_launch(stage, cnt * n, n, a, r->probe, r->stream);
+    if (e == cudaSuccess) e = skew_probe_launch(stage, cnt * m, n, m, a, r->probe, r->stream);
     if (e == cudaSuccess)
-      e = convert_rows_packed_launch(stage, cnt * n, n, a, r->k1.lp, r->storage, r->op + a * n * r->k1.row_bytes,
+      e = convert_rows_packed_launch(stage, cnt * m, n, m, a, r->k1.lp, r->storage, r->op + a * m * r->k1.row_bytes,
                                      r->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) {
@@ -152,7 +152,7 @@ static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
-                  r->k1p_dg, r->k1p_tg, r->probe};
+                  r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -189,8 +189,10 @@ static bool use_k2(const grom_rom* r, int batch) {
   return batch > 8;
 }
 
+static bool is_cp(const grom_rom* r) { return r->form == GROM_FORM_CP || r->form == GROM_FORM_CP_SKEW; }
+
 static bool use_k3g(const grom_rom* r, int batch) {
-  return r->form != GROM_FORM_FULL && batch >= K3G_MIN_BATCH && r->k3g_scratch;
+  return is_cp(r) && batch >= K3G_MIN_BATCH && r->k3g_scratch;
 }
 
 static K1Args k1_args(grom_rom* r) {
@@ -200,7 +202,19 @@ static K1Args k1_args(grom_rom* r) {
   a.err = r->err;
   a.dg = r->k1p_dg;
   a.tg = r->k1p_tg;
+  if (r->form == GROM_FORM_SVD) {
+    a.mid = r->svd_beta;
+    a.mid_stride = r->rank;
+  }
   return a;
+}
+
+// SVD form: the middle weights beta = sigma o (U^T u) of every trajectory,
+// from u (stride u_stride) or from the newest history slot.
+static cudaError_t svd_beta(grom_rom* r, int batch, const double* u, int64_t u_stride, const double* hist,
+                            const int64_t* taken, const int32_t* active, cudaStream_t s) {
+  return svd_project_launch(r->svd_ut, r->svd_sigma, r->n, r->rank, batch, u, u_stride, hist, taken, 6 * (int64_t)r->n,
+                            active, r->svd_beta, s);
 }
 
 static K3Args k3_args(grom_rom* r) {
@@ -223,7 +237,7 @@ const char* grom_last_error(void) { return g_last_error.c_str(); }
 
 int32_t grom_max_n(int32_t form, int32_t storage) {
   if (storage_elem_bytes(storage) == 0) return 0;
-  if (form == GROM_FORM_FULL) {
+  if (form == GROM_FORM_FULL || form == GROM_FORM_SVD) {
     // a stored row (np elements) must fit one streaming stage
     int64_t n = K1_MAX_ROW_BYTES / storage_elem_bytes(storage);
     return (int32_t)std::min<int64_t>(n, 8192);
@@ -238,10 +252,10 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     if (d->reserved[q]) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
   if (d->layout != GROM_LAYOUT_DENSE && d->layout != GROM_LAYOUT_SKEW_PACKED)
     return fail(GROM_ERR_INVALID_ARG, "grom_create: unknown layout");
-  if (d->layout != GROM_LAYOUT_DENSE && d->form != GROM_FORM_FULL)
-    return fail(GROM_ERR_INVALID_ARG, "grom_create: the skew-packed layout is for the full form");
+  if (d->layout != GROM_LAYOUT_DENSE && d->form != GROM_FORM_FULL && d->form != GROM_FORM_SVD)
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: the skew-packed layout is for the full and SVD forms");
   if (d->n < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: n must be >= 1");
-  if (d->form < GROM_FORM_FULL || d->form > GROM_FORM_CP_SKEW) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad form");
+  if (d->form < GROM_FORM_FULL || d->form > GROM_FORM_SVD) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad form");
   if (storage_elem_bytes(d->storage) == 0) return fail(GROM_ERR_INVALID_ARG, "grom_create: bad storage type");
   if (d->order < 1 || d->order > 3) return fail(GROM_ERR_INVALID_ARG, "grom_create: order must be 1, 2 or 3");
   if (!(d->dt > 0.0) || !(d->nu >= 0.0) || !std::isfinite(d->dt) || !std::isfinite(d->nu))
@@ -256,6 +270,10 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   if (d->form == GROM_FORM_FULL) {
     if (!d->tensor && !d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: tensor is NULL");
     if (d->tensor && d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: tensor given with defer_tensor");
+  } else if (d->form == GROM_FORM_SVD) {
+    if (d->rank < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: SVD rank must be >= 1");
+    if (!d->fa || !d->fb || !d->fc) return fail(GROM_ERR_INVALID_ARG, "grom_create: SVD factors are NULL");
+    if (d->defer_tensor) return fail(GROM_ERR_INVALID_ARG, "grom_create: defer_tensor is for the full form");
   } else {
     if (d->rank < 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: CP rank must be >= 1");
     if (!d->fa || !d->fb || !d->fc) return fail(GROM_ERR_INVALID_ARG, "grom_create: CP factors are NULL");
@@ -331,6 +349,38 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       r->row_seen = new (std::nothrow) uint8_t[(size_t)n]();
       if (!r->row_seen) return bail(fail(GROM_ERR_OOM, "grom_create: host allocation"));
     }
+  } else if (r->form == GROM_FORM_SVD) {
+    // V slices V[i][r][k] as n * rank streamed rows; U^T and sigma in FP64
+    const bool packed = r->layout == GROM_LAYOUT_SKEW_PACKED;
+    const int64_t R = r->rank;
+    r->np = padded_n(n);
+    r->k1 = k1_plan(n, r->storage, r->sm_count, packed ? 1 : 0, R);
+    const size_t row_bytes = (size_t)r->k1.row_bytes;
+    r->op_bytes = (size_t)n * (size_t)R * row_bytes;
+    if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
+    r->part_bytes = (size_t)r->k1.grid * r->k1.maxseg * (K1_CONSUMERS / 32) * r->k1.nb_max * sizeof(double);
+    if ((st = dmalloc(&r->part, r->part_bytes, &r->total_bytes))) return bail(st);
+    if (packed) {
+      if ((st = dmalloc(&r->k1p_dg, k1p_dg_bytes(r->k1, r->storage), &r->total_bytes))) return bail(st);
+      if ((st = dmalloc(&r->k1p_tg, k1p_tg_bytes(r->k1), &r->total_bytes))) return bail(st);
+      if ((st = dmalloc(&r->probe, 3 * sizeof(double), &r->total_bytes))) return bail(st);
+      if (cudaMemsetAsync(r->probe, 0, 3 * sizeof(double), r->stream) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+      if ((st = upload_rows_packed(r, d->fc, 0, n))) return bail(st);
+      if ((st = check_skew_probe(r))) return bail(st);
+    } else if ((st = upload_rows(r, d->fc, n * R, n, r->np, r->op, (int64_t)row_bytes))) {
+      return bail(st);
+    }
+    std::vector<double> U, sig, ut((size_t)(R * n));
+    if ((st = fetch(U, d->fa, (size_t)(n * R)))) return bail(st);
+    if ((st = fetch(sig, d->fb, (size_t)R))) return bail(st);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t q = 0; q < R; ++q) ut[q * n + j] = U[j * R + q];
+    if ((st = upload(&r->svd_ut, ut.data(), ut.size(), &r->total_bytes, r->stream))) return bail(st);
+    if ((st = upload(&r->svd_sigma, sig.data(), sig.size(), &r->total_bytes, r->stream))) return bail(st);
+    if ((st = dmalloc(&r->svd_beta, (size_t)r->max_batch * R * sizeof(double), &r->total_bytes))) return bail(st);
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    r->rows_uploaded = n;
   } else {
     r->k3 = k3_plan(n, r->rank, r->storage, r->sm_count);
     const int64_t rp = r->k3.rb;
@@ -495,14 +545,15 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
     e = k2_launch(k2_plan(r->n, batch, r->sm_count), &r->k2_tmap, a, r->stream);
-  } else if (r->form == GROM_FORM_FULL) {
+  } else if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.u = u;
     a.u_stride = r->n;
     a.c = c;
     a.c_stride = r->n;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
-    e = k1_launch(r->k1, r->storage, a, batch, r->stream);
+    e = r->form == GROM_FORM_SVD ? svd_beta(r, batch, u, r->n, nullptr, nullptr, nullptr, r->stream) : cudaSuccess;
+    if (e == cudaSuccess) e = k1_launch(r->k1, r->storage, a, batch, r->stream);
   } else {
     K3Args a = k3_args(r);
     a.u = u;
@@ -579,6 +630,7 @@ grom_status grom_traj_destroy(grom_traj* t) {
   if (t->cnt) cudaFree(t->cnt);
   if (t->graph) cudaGraphExecDestroy(t->graph);
   if (t->graph_tmpl) cudaGraphDestroy(t->graph_tmpl);
+  if (t->io_graph) cudaGraphExecDestroy(t->io_graph);
   if (t->gstream) cudaStreamDestroy(t->gstream);
   if (t->ev_in) cudaEventDestroy(t->ev_in);
   if (t->ev_out) cudaEventDestroy(t->ev_out);
@@ -603,13 +655,17 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
     return k2_launch(k2_plan(r->n, t->batch, r->sm_count), &r->k2_tmap, a, strm);
   }
-  if (r->form == GROM_FORM_FULL) {
+  if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.hist = t->hist;
     a.taken = t->taken;
     a.hist_stride = 6 * (int64_t)r->n;
     a.active = t->active;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
+    if (r->form == GROM_FORM_SVD) {
+      const cudaError_t e = svd_beta(r, t->batch, nullptr, 0, t->hist, t->taken, t->active, strm);
+      if (e != cudaSuccess) return e;
+    }
     return k1_launch(r->k1, r->storage, a, t->batch, strm);
   }
   K3Args a = k3_args(r);
@@ -664,8 +720,8 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
 static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double* invariant, cudaStream_t strm) {
   grom_rom* r = t->rom;
   StepArgs a = step_args(t, energy, invariant);
-  const bool fused_k1 = r->diagonal && r->form == GROM_FORM_FULL && !use_k2(r, t->batch);
-  const bool fused_k3 = r->diagonal && r->form != GROM_FORM_FULL && !use_k3g(r, t->batch);
+  const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch);
+  const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
     if (fused_k3) {
@@ -688,7 +744,8 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
       k.hist_stride = 6 * (int64_t)r->n;
       k.active = t->active;
       if (!prof_pair(r, &k.ev0, &k.ev1)) return cudaErrorMemoryAllocation;
-      e = k1_launch_fused_step(r->k1, r->storage, k, a, t->batch, s, strm);
+      e = r->form == GROM_FORM_SVD ? svd_beta(r, t->batch, nullptr, 0, t->hist, t->taken, t->active, strm) : cudaSuccess;
+      if (e == cudaSuccess) e = k1_launch_fused_step(r->k1, r->storage, k, a, t->batch, s, strm);
     } else {
       e = traj_nonlinear(t, strm);
       if (e == cudaSuccess) e = step_launch_indexed(a, r->diagonal, s, strm);
@@ -704,7 +761,7 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   grom_rom* r = t->rom;
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
   // CP forms with a few trajectories: all steps in one persistent launch
-  if (r->diagonal && r->form != GROM_FORM_FULL && r->k3p_scratch && !t->active && !r->prof &&
+  if (r->diagonal && is_cp(r) && r->k3p_scratch && !t->active && !r->prof &&
       t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 &&
       k3p_fits(r->n, r->k3.rb, r->storage, t->batch, r->sm_count)) {
     StepArgs a = step_args(t, energy, invariant);
@@ -716,9 +773,9 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   constexpr int G = 8;  // steps per captured graph
   int done = 0;
   if (!energy && !invariant && nsteps >= G) {
-    // Replay a captured graph of G steps on a private stream joined to the
-    // ROM's stream by events (the ROM's stream may be the legacy default
-    // stream, which cannot be captured).
+    // A graph of G steps, captured on a private stream (the ROM's stream may
+    // be the legacy default stream, which cannot be captured) and replayed on
+    // the ROM's stream.
     if (t->graph && t->graph_version != r->version) {
       cudaGraphExecDestroy(t->graph);
       cudaGraphDestroy(t->graph_tmpl);
@@ -781,8 +838,6 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
       t->graph_steps = G;
       t->graph_version = r->version;
     }
-    GROM_CUDA_TRY(cudaEventRecord(t->ev_in, r->stream));
-    GROM_CUDA_TRY(cudaStreamWaitEvent(t->gstream, t->ev_in, 0));
     for (; done + G <= nsteps; done += G) {
       if (r->prof) {
         // fresh timing pairs for this replay, in the graph's event order
@@ -792,14 +847,22 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
         for (size_t q = 0; q < t->prof_nodes.size(); ++q)
           GROM_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(t->graph, t->prof_nodes[q], evs[t->prof_index[q]]));
       }
-      GROM_CUDA_TRY(cudaGraphLaunch(t->graph, t->gstream));
+      GROM_CUDA_TRY(cudaGraphLaunch(t->graph, r->stream));
     }
-    GROM_CUDA_TRY(cudaEventRecord(t->ev_out, t->gstream));
-    GROM_CUDA_TRY(cudaStreamWaitEvent(r->stream, t->ev_out, 0));
   }
   cudaError_t e = launch_steps(t, nsteps - done, energy, invariant, r->stream);
   if (e != cudaSuccess) return cuda_fail(e, "grom_step launch");
   return GROM_OK;
+}
+
+static bool pinned_or_device(const void* p, bool* host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *host = at.type == cudaMemoryTypeHost;
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice;
 }
 
 grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, double* u_out) {
@@ -807,6 +870,49 @@ grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, dou
   grom_rom* r = t->rom;
   const int64_t n = r->n;
   const size_t bytes = (size_t)t->batch * n * sizeof(double);
+  if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step_host: nsteps must be >= 0");
+  if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step_host: tensor rows missing");
+  bool in_host = false, out_host = false;
+  // Short calls with pinned (or device) buffers: the copy in, the steps and
+  // the copy out replay as one captured graph, one launch per call.  (Longer
+  // CP calls keep the persistent stepper of grom_step.)
+  if (u_in && u_out && nsteps >= 1 && nsteps <= 8 && !r->prof && !t->active &&
+      (!is_cp(r) || nsteps < 4) && pinned_or_device(u_in, &in_host) &&
+      pinned_or_device(u_out, &out_host)) {
+    if (t->io_graph && (t->io_in != u_in || t->io_out != u_out || t->io_steps != nsteps || t->io_version != r->version)) {
+      cudaGraphExecDestroy(t->io_graph);
+      t->io_graph = nullptr;
+    }
+    if (!t->io_graph) {
+      if (!t->gstream) {
+        GROM_CUDA_TRY(cudaStreamCreateWithFlags(&t->gstream, cudaStreamNonBlocking));
+        GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
+        GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
+      }
+      cudaGraph_t g = nullptr;
+      GROM_CUDA_TRY(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaMemcpyAsync(t->io, u_in, bytes, cudaMemcpyDefault, t->gstream);
+      if (e == cudaSuccess) e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, true, t->gstream);
+      if (e == cudaSuccess) e = launch_steps(t, nsteps, nullptr, nullptr, t->gstream);
+      if (e == cudaSuccess) e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, false, t->gstream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(u_out, t->io, bytes, cudaMemcpyDefault, t->gstream);
+      cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&t->io_graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        t->io_graph = nullptr;
+        return cuda_fail(e != cudaSuccess ? e : e2, "grom_step_host graph");
+      }
+      t->io_in = u_in;
+      t->io_out = u_out;
+      t->io_steps = nsteps;
+      t->io_version = r->version;
+    }
+    GROM_CUDA_TRY(cudaGraphLaunch(t->io_graph, r->stream));
+    if (out_host) GROM_CUDA_TRY(cudaStreamSynchronize(r->stream));
+    return GROM_OK;
+  }
   if (u_in) {
     GROM_CUDA_TRY(cudaMemcpyAsync(t->io, u_in, bytes, cudaMemcpyDefault, r->stream));
     GROM_CUDA_TRY(state_io_launch(t->hist, t->taken, n, t->batch, t->io, true, r->stream));

@@ -54,59 +54,15 @@ inline int storage_elem_bytes(int storage) {
   return 0;
 }
 
-// ----------------------------------------------------------- K1 streaming
-constexpr int K1_CONSUMERS = 256;                 // consumer threads (8 warps)
-constexpr int K1_THREADS = K1_CONSUMERS + 32;     // + one producer warp
-constexpr int K1_STAGES = 6;
-constexpr int K1_STAGE_BYTES = 32768;
-constexpr int K1_MAX_ROW_BYTES = K1_STAGE_BYTES;
+}  // namespace grom
 
-struct K1Plan {
-  int64_t n, np;
-  int64_t row_bytes;   // stored elements per row (np, or lp when packed) * element bytes
-  int64_t rpc;         // rows per chunk (all in one test index i)
-  int64_t cpi;         // chunks per test index
-  int64_t T;           // total chunks = n * cpi
-  int grid;            // persistent CTAs
-  int maxseg;          // max test-index segments per CTA
-  int qm;              // vector positions per consumer thread per row (1,2,4,8)
-  int nb_max;          // trajectories per pass
-  size_t smem;         // dynamic shared memory
-  // skew-packed layout (GROM_LAYOUT_SKEW_PACKED); zero for the dense layout
-  int packed;
-  int rg;              // row groups per chunk that share a position (1, 2 or 4)
-  int64_t h;           // stored distances d = 1..h, h = n / 2
-  int64_t lp;          // stored elements per row: round_up(max(h, 1), 64)
-  int64_t lw;          // transposed-term window per CTA: maxseg - 1 + lp
-};
-// Scratch of the packed kernel: D u_i per (CTA, test-index segment, trajectory,
-// position) and the per-CTA transposed-term windows.
-size_t k1p_dg_bytes(const K1Plan& p, int storage);
-size_t k1p_tg_bytes(const K1Plan& p);
+#include "k1_types.h"
 
-struct K1Args {
-  const uint8_t* tensor;  // stored tensor (storage layout)
-  const double* u;        // batch x n (FP64), first trajectory of this pass
-  int64_t u_stride;       // doubles between trajectories
-  double* part;           // scratch: grid x maxseg x NB partials
-  double* c;              // batch x n output
-  int64_t c_stride;
-  int nb;                 // active trajectories in this pass (<= NB)
-  int* err;               // device error flags
-  // Optional per-trajectory ring addressing for the stepper: when `taken` is
-  // non-null, the u of trajectory b is hist + b*hist_stride + (taken[b]%3)*n
-  // and c is written to hist + b*hist_stride + (3 + taken[b]%3)*n.
-  double* hist;
-  const int64_t* taken;
-  int64_t hist_stride;
-  const int32_t* active;  // nullable: trajectories with active[b]==0 are skipped
-  cudaEvent_t ev0, ev1;   // nullable: recorded around the streaming kernel
-  int skip_finalize;      // 1: the caller runs a fused finalize (see k_step.cu)
-  void* dg;               // packed layout: k1p_dg_bytes of scratch
-  double* tg;             // packed layout: k1p_tg_bytes of scratch
-};
+namespace grom {
 
-K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed = 0);
+// m = 0: the G-ROM (middle extent n, weights u); m > 0: middle extent m with
+// separate weights (the SVD-ROM)
+K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed = 0, int64_t m = 0);
 cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a, int batch, cudaStream_t s);
 
 // ------------------------------------------------- K2 (tensor cores, BF16)
@@ -254,12 +210,18 @@ cudaError_t state_io_launch(double* hist, const int64_t* taken, int64_t n, int b
 // ------------------------------------------------------------ conversion
 cudaError_t convert_rows_launch(const double* src, int64_t rows, int64_t n, int64_t np,
                                 int storage, uint8_t* dst, cudaStream_t s);
-// Dense FP64 rows (i, j) for i in [i0, i0 + rows/n) -> skew-packed stored rows.
-cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t n, int64_t i0, int64_t lp,
+// Dense FP64 rows (i, j) of n values, m rows per test index, for i from i0
+// -> skew-packed stored rows (position p holds the value at k = (i + 1 + p) mod n).
+cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t n, int64_t m, int64_t i0, int64_t lp,
                                        int storage, uint8_t* dst, cudaStream_t s);
-// Adds the skew probes of FP64 rows (i, j), i from i0, into acc[0..2]
-// (probe 1, probe 2, sum of squares).
-cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t i0, double* acc, cudaStream_t s);
+// Adds the skew probes of FP64 rows (i, j) (m rows per test index, i from
+// i0) into acc[0..2] (probe 1, probe 2, sum of squares).
+cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t m, int64_t i0, double* acc,
+                              cudaStream_t s);
+// SVD-ROM middle weights beta[b][r] = sigma_r sum_j U_jr u_bj (k_svd.cu).
+cudaError_t svd_project_launch(const double* ut, const double* sigma, int64_t n, int64_t rank, int batch,
+                               const double* u, int64_t u_stride, const double* hist, const int64_t* taken,
+                               int64_t hist_stride, const int32_t* active, double* beta, cudaStream_t s);
 cudaError_t convert_panels_launch(const double* src, int64_t n, int64_t r, int64_t rb,
                                   int storage, uint8_t* dst, cudaStream_t s);
 
@@ -291,6 +253,9 @@ struct grom_rom {
   void* k1p_dg = nullptr;       // packed layout: segment values D u_i
   double* k1p_tg = nullptr;     // packed layout: transposed-term windows
   double* probe = nullptr;      // packed layout: skew probe accumulators (3)
+  double* svd_ut = nullptr;     // SVD form: U^T (rank x n)
+  double* svd_sigma = nullptr;  // SVD form: singular values (rank)
+  double* svd_beta = nullptr;   // SVD form: middle weights (max_batch x rank)
   grom::K1Plan k1{};
   grom::K3Plan k3{};
   size_t total_bytes = 0;
@@ -327,6 +292,13 @@ struct grom_traj {
   std::vector<cudaGraphNode_t> prof_nodes;
   std::vector<int> prof_index;
   int prof_pairs = 0;
+  // grom_step_host as one captured graph (state in, steps, state out) for a
+  // given pair of buffers and step count
+  cudaGraphExec_t io_graph = nullptr;
+  const void* io_in = nullptr;
+  void* io_out = nullptr;
+  int io_steps = 0;
+  int io_version = -1;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int32_t* active = nullptr;      // serving slots: 1 = occupied (nullable: all active)

@@ -77,27 +77,12 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
     ptx::fence_mbar_init();
   }
 
-  // u of the NB trajectories of this pass (zero-padded to np), in the
-  // arithmetic type of the storage; F32X2 keeps a hi and a lo plane.
-  for (int64_t idx = tid; idx < (int64_t)NB * np; idx += K1_THREADS) {
-    const int b = (int)(idx / np);
-    const int64_t k = idx - (int64_t)b * np;
-    double v = 0.0;
-    const int bg = b0 + b;
-    if (b < a.nb && k < n && (a.active == nullptr || a.active[bg])) {
-      const double* ub = a.taken ? a.hist + bg * a.hist_stride + (a.taken[bg] % 3) * n : a.u + bg * a.u_stride;
-      v = ub[k];
-    }
-    if constexpr (ST == GROM_F64) {
-      reinterpret_cast<double*>(ureg)[idx] = v;
-    } else if constexpr (ST == GROM_F32X2) {
-      const float hv = __double2float_rn(v);
-      reinterpret_cast<float*>(ureg)[idx] = hv;
-      reinterpret_cast<float*>(ureg)[(int64_t)NB * np + idx] = __double2float_rn(v - (double)hv);
-    } else {
-      reinterpret_cast<float*>(ureg)[idx] = __double2float_rn(v);
-    }
-  }
+  // u of the NB trajectories of this pass (zero-padded to np) and the middle
+  // weights (u itself for the G-ROM), in the arithmetic type of the storage;
+  // F32X2 keeps a hi and a lo plane.
+  const uint8_t* mreg;
+  int64_t mp;
+  k1_load_state<ST, NB>(pl, a, b0, ureg, mreg, mp);
   __syncthreads();
 
   if (warp == K1_CONSUMERS / 32) {
@@ -114,10 +99,10 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
           break;
         }
         const int64_t j0 = jc * pl.rpc;
-        const int64_t rows = n - j0 < pl.rpc ? n - j0 : pl.rpc;
+        const int64_t rows = pl.m - j0 < pl.rpc ? pl.m - j0 : pl.rpc;
         const uint32_t bytes = (uint32_t)(rows * row_bytes);
         ptx::mbar_arrive_expect_tx(&full[s], bytes);
-        ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * n + j0) * row_bytes, bytes, &full[s]);
+        ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * pl.m + j0) * row_bytes, bytes, &full[s]);
         if (++jc == pl.cpi) { jc = 0; ++i; }
         if (++s == K1_STAGES) { s = 0; ph ^= 1u; }
       }
@@ -227,7 +212,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
     for (int64_t c = c0; c < c1; ++c) {
       const int64_t i = ci;
       const int j0 = (int)(cj * pl.rpc);
-      const int rows = (int)(n - j0 < pl.rpc ? n - j0 : pl.rpc);
+      const int rows = (int)(pl.m - j0 < pl.rpc ? pl.m - j0 : pl.rpc);
       if (++cj == pl.cpi) { cj = 0; ++ci; }
       if (i != cur_i) {
         if (cur_i >= 0) flush(cur_i);
@@ -274,7 +259,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
         if constexpr (ST == GROM_F64) {
           double uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const double x0 = __hiloint2double((int)vec[t][q][0].y, (int)vec[t][q][0].x);
@@ -289,8 +274,8 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
           float uh[NB], ul[NB];
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
-            uh[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
-            ul[b] = reinterpret_cast<const float*>(ureg)[(NB + b) * (int)np + j];
+            uh[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
+            ul[b] = reinterpret_cast<const float*>(mreg)[(NB + b) * (int)mp + j];
           }
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
@@ -307,7 +292,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
         } else if constexpr (ST == GROM_F32) {
           float uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const uint4 x = vec[t][q][0];
@@ -322,7 +307,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_packed_kernel(const K1Plan p
         } else {  // BF16
           float uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const uint32_t ws[4] = {vec[t][q][0].x, vec[t][q][0].y, vec[t][q][0].z, vec[t][q][0].w};

@@ -38,10 +38,23 @@ static int epv(int storage) {
   return 1;
 }
 
-K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed) {
+// Shared-memory bytes per trajectory of a pass: u (np values) and, with
+// separate middle weights, those (mp values), in the storage's arithmetic
+// type (F32X2: hi and lo floats).
+static int64_t k1_traj_smem(const K1Plan& p, int storage) {
+  const int64_t ub = (storage == GROM_F64 || storage == GROM_F32X2) ? 8 : 4;
+  return (p.np + (p.has_mid ? p.mp : 0)) * ub;
+}
+
+static constexpr int64_t K1_SMEM_BASE = 1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16;
+
+K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed, int64_t m) {
   K1Plan p{};
   p.n = n;
   p.np = padded_n(n);
+  p.has_mid = m > 0 ? 1 : 0;
+  p.m = m > 0 ? m : n;
+  p.mp = padded_n(p.m);
   p.packed = packed;
   p.h = n / 2;
   p.lp = packed ? padded_n(p.h > 0 ? p.h : 1) : p.np;
@@ -67,8 +80,8 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed) {
   p.rpc = K1_STAGE_BYTES / p.row_bytes;
   if (p.rpc > rmax * rpr) p.rpc = rmax * rpr;
   if (p.rpc < 1) p.rpc = 1;
-  if (p.rpc > n) p.rpc = n;
-  p.cpi = (n + p.rpc - 1) / p.rpc;
+  if (p.rpc > p.m) p.rpc = p.m;
+  p.cpi = (p.m + p.rpc - 1) / p.rpc;
   p.T = n * p.cpi;
   int64_t grid = sm_count;  // one persistent CTA per SM (the stage ring fills most of shared memory)
   if (grid > p.T) grid = p.T;
@@ -76,13 +89,12 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed) {
   p.grid = (int)grid;
   const int64_t per = (p.T + grid - 1) / grid;
   p.maxseg = (int)((per + p.cpi - 1) / p.cpi + 1);
-  const int u_bytes_per_traj = (int)(p.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
-  const int base = 1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16;
-  const int budget = 227 * 1024 - base;
+  const int64_t per_traj = k1_traj_smem(p, storage);
+  const int64_t budget = 227 * 1024 - K1_SMEM_BASE;
   int nb = 8;
-  while (nb > 1 && (acc_regs(storage) * p.qm * nb > 64 || nb * u_bytes_per_traj > budget)) nb >>= 1;
+  while (nb > 1 && (acc_regs(storage) * p.qm * nb > 64 || nb * per_traj > budget)) nb >>= 1;
   p.nb_max = nb;
-  p.smem = (size_t)base + (size_t)nb * u_bytes_per_traj;
+  p.smem = (size_t)(K1_SMEM_BASE + nb * per_traj);
   p.lw = p.maxseg - 1 + p.lp;
   return p;
 }
@@ -121,8 +133,7 @@ cudaError_t k1_launch(const K1Plan& plan, int storage, const K1Args& a0, int bat
     const int nb = pow2_ceil(a.nb);
     K1Plan pl = plan;
     // shared memory for the template width actually launched
-    const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
-    pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
+    pl.smem = (size_t)(K1_SMEM_BASE + nb * k1_traj_smem(pl, storage));
     cudaError_t e = k1_dispatch(pl, storage, nb, a, b0, s);
     if (e != cudaSuccess) return e;
   }
@@ -143,8 +154,7 @@ cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& 
     a.skip_finalize = 1;
     const int nb = pow2_ceil(a.nb);
     K1Plan pl = plan;
-    const int u_bytes_per_traj = (int)(pl.np * (storage == GROM_F64 || storage == GROM_F32X2 ? 8 : 4));
-    pl.smem = (size_t)(1024 + K1_STAGES * K1_STAGE_BYTES + 2 * K1_STAGES * 8 + 16) + (size_t)nb * u_bytes_per_traj;
+    pl.smem = (size_t)(K1_SMEM_BASE + nb * k1_traj_smem(pl, storage));
     cudaError_t e = k1_dispatch(pl, storage, nb, a, b0, s);
     if (e != cudaSuccess) return e;
     e = plan.packed ? step_diag_packed_launch(st, step_index, pl, a, b0, a.nb, nb, s)

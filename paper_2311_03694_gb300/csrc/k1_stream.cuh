@@ -2,8 +2,10 @@
 //
 //   c_i = sum_j u_j sum_k C_ijk u_k            (Sec. 2.2, eq. Cu; 2N^3 flops, N^3 words)
 //
-// The stored tensor is a sequence of N^2 rows (i, j) of np elements (k padded
-// with zeros).  A persistent grid splits the rows into chunks of whole rows
+// The stored tensor is a sequence of N*m rows (i, j) of np elements (k padded
+// with zeros); m = N for the G-ROM.  For the SVD-ROM (Sec. 4.4.2) the same
+// kernel streams the slices V[i][r][k] (m = rank) with the middle index
+// weighted by beta = sigma o (U^T u) instead of u.  A persistent grid splits the rows into chunks of whole rows
 // that never straddle a test index i, and each CTA streams a contiguous range
 // of chunks through a ring of shared-memory stages filled by bulk TMA copies
 // (cp.async.bulk, completion on an mbarrier).  One producer warp issues the
@@ -58,13 +60,6 @@ __host__ __device__ inline int64_t k1_positions(int64_t np) {
   return np / K1Traits<ST>::EPV;
 }
 
-__device__ __forceinline__ void chunk_decode(int64_t c, int64_t cpi, int64_t rpc, int64_t n, int64_t& i,
-                                             int64_t& j0, int64_t& rows) {
-  i = c / cpi;
-  j0 = (c - i * cpi) * rpc;
-  rows = n - j0 < rpc ? n - j0 : rpc;
-}
-
 // Accumulator types.
 template <int ST>
 struct Acc;
@@ -105,6 +100,54 @@ __device__ __forceinline__ void ds_fma(float hi, float lo, float uh, float ul, f
   s = __fadd_rn(s, __fadd_rn(err, __fadd_rn(e, t)));
 }
 
+// Loads one vector per trajectory of the pass into shared memory in the
+// arithmetic type of the storage (F32X2: a hi plane, then a lo plane):
+// entry (b, k) = src(b, k) for k < len, where src returns 0 past the
+// meaningful length and for inactive trajectories.
+template <int ST, int NB, typename F>
+__device__ __forceinline__ void k1_load_vec(uint8_t* dst, int64_t len, F src) {
+  for (int64_t idx = threadIdx.x; idx < (int64_t)NB * len; idx += blockDim.x) {
+    const int b = (int)(idx / len);
+    const double v = src(b, idx - (int64_t)b * len);
+    if constexpr (ST == GROM_F64) {
+      reinterpret_cast<double*>(dst)[idx] = v;
+    } else if constexpr (ST == GROM_F32X2) {
+      const float h = __double2float_rn(v);
+      reinterpret_cast<float*>(dst)[idx] = h;
+      reinterpret_cast<float*>(dst)[(int64_t)NB * len + idx] = __double2float_rn(v - (double)h);
+    } else {
+      reinterpret_cast<float*>(dst)[idx] = __double2float_rn(v);
+    }
+  }
+}
+
+// u of the pass into ureg (np per trajectory) and, with separate middle
+// weights, those into the array after it (mp per trajectory).  Returns the
+// middle-weight array and its per-trajectory length through mreg and mp.
+template <int ST, int NB>
+__device__ __forceinline__ void k1_load_state(const K1Plan& pl, const K1Args& a, int b0, uint8_t* ureg,
+                                              const uint8_t*& mreg, int64_t& mp) {
+  const int64_t n = pl.n, np = pl.np;
+  auto live = [&](int b) { return b < a.nb && (a.active == nullptr || a.active[b0 + b]); };
+  k1_load_vec<ST, NB>(ureg, np, [&](int b, int64_t k) -> double {
+    if (!live(b) || k >= n) return 0.0;
+    const int bg = b0 + b;
+    const double* ub = a.taken ? a.hist + bg * a.hist_stride + (a.taken[bg] % 3) * n : a.u + bg * a.u_stride;
+    return ub[k];
+  });
+  mreg = ureg;
+  mp = np;
+  if (pl.has_mid) {
+    uint8_t* m = ureg + (int64_t)NB * np * K1Traits<ST>::U_BYTES;
+    k1_load_vec<ST, NB>(m, pl.mp, [&](int b, int64_t r) -> double {
+      if (!live(b) || r >= pl.m) return 0.0;
+      return a.mid[(int64_t)(b0 + b) * a.mid_stride + r];
+    });
+    mreg = m;
+    mp = pl.mp;
+  }
+}
+
 template <int ST, int QM, int NB>
 __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan pl, const K1Args a, const int b0) {
   using TR = K1Traits<ST>;
@@ -130,27 +173,11 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
     ptx::fence_mbar_init();
   }
 
-  // u of the NB trajectories of this pass, zero-padded to np, in the
-  // arithmetic type of the storage.
-  for (int64_t idx = tid; idx < (int64_t)NB * np; idx += K1_THREADS) {
-    const int b = (int)(idx / np);
-    const int64_t k = idx - (int64_t)b * np;
-    double v = 0.0;
-    const int bg = b0 + b;
-    if (b < a.nb && k < n && (a.active == nullptr || a.active[bg])) {
-      const double* ub = a.taken ? a.hist + bg * a.hist_stride + (a.taken[bg] % 3) * n : a.u + bg * a.u_stride;
-      v = ub[k];
-    }
-    if constexpr (ST == GROM_F64) {
-      reinterpret_cast<double*>(ureg)[idx] = v;
-    } else if constexpr (ST == GROM_F32X2) {
-      const float h = __double2float_rn(v);
-      reinterpret_cast<float*>(ureg)[idx] = h;
-      reinterpret_cast<float*>(ureg)[(int64_t)NB * np + idx] = __double2float_rn(v - (double)h);
-    } else {
-      reinterpret_cast<float*>(ureg)[idx] = __double2float_rn(v);
-    }
-  }
+  // u of the NB trajectories of this pass (zero-padded to np) and the middle
+  // weights (u itself for the G-ROM), in the arithmetic type of the storage
+  const uint8_t* mreg;
+  int64_t mp;
+  k1_load_state<ST, NB>(pl, a, b0, ureg, mreg, mp);
   __syncthreads();
 
   if (warp == K1_CONSUMERS / 32) {
@@ -167,10 +194,10 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
           break;
         }
         const int64_t j0 = jc * pl.rpc;
-        const int64_t rows = n - j0 < pl.rpc ? n - j0 : pl.rpc;
+        const int64_t rows = pl.m - j0 < pl.rpc ? pl.m - j0 : pl.rpc;
         const uint32_t bytes = (uint32_t)(rows * row_bytes);
         ptx::mbar_arrive_expect_tx(&full[s], bytes);
-        ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * n + j0) * row_bytes, bytes, &full[s]);
+        ptx::bulk_g2s(stages + (size_t)s * K1_STAGE_BYTES, a.tensor + (i * pl.m + j0) * row_bytes, bytes, &full[s]);
         if (++jc == pl.cpi) { jc = 0; ++i; }
         if (++s == K1_STAGES) { s = 0; ph ^= 1u; }
       }
@@ -265,7 +292,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
     for (int64_t c = c0; c < c1; ++c) {
       const int64_t i = ci;
       const int j0 = (int)(cj * pl.rpc);
-      const int rows = (int)(n - j0 < pl.rpc ? n - j0 : pl.rpc);
+      const int rows = (int)(pl.m - j0 < pl.rpc ? pl.m - j0 : pl.rpc);
       if (++cj == pl.cpi) { cj = 0; ++ci; }
       if (i != cur_i) {
         if (cur_i >= 0) flush(cur_i);
@@ -315,7 +342,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
         if constexpr (ST == GROM_F64) {
           double uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const double*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const double x0 = __hiloint2double((int)vec[t][q][0].y, (int)vec[t][q][0].x);
@@ -330,8 +357,8 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
           float uh[NB], ul[NB];
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
-            uh[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
-            ul[b] = reinterpret_cast<const float*>(ureg)[(NB + b) * (int)np + j];
+            uh[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
+            ul[b] = reinterpret_cast<const float*>(mreg)[(NB + b) * (int)mp + j];
           }
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
@@ -348,7 +375,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
         } else if constexpr (ST == GROM_F32) {
           float uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const uint4 x = vec[t][q][0];
@@ -363,7 +390,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
         } else {  // BF16
           float uj[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(ureg)[b * (int)np + j];
+          for (int b = 0; b < NB; ++b) uj[b] = reinterpret_cast<const float*>(mreg)[b * (int)mp + j];
 #pragma unroll
           for (int q = 0; q < QM; ++q) {
             const uint32_t ws[4] = {vec[t][q][0].x, vec[t][q][0].y, vec[t][q][0].z, vec[t][q][0].w};

@@ -48,12 +48,12 @@ cudaError_t convert_rows_launch(const double* src, int64_t rows, int64_t n, int6
 // position p < h = n/2 holds C[i][j][(i + 1 + p) mod n], except that for
 // even n the distance n/2 is kept only in rows with i < n/2; other
 // positions are zero.  Same rounding and F32X2 planes as k_convert_rows.
-__global__ void k_convert_rows_packed(const double* __restrict__ src, int64_t rows, int64_t n, int64_t i0, int64_t lp,
-                                      int storage, uint8_t* __restrict__ dst) {
+__global__ void k_convert_rows_packed(const double* __restrict__ src, int64_t rows, int64_t n, int64_t m, int64_t i0,
+                                      int64_t lp, int storage, uint8_t* __restrict__ dst) {
   const int64_t total = rows * lp, h = n / 2;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / lp, p = t - r * lp;
-    const int64_t i = i0 + r / n;
+    const int64_t i = i0 + r / m;
     double x = 0.0;
     if (p < h && !((n % 2 == 0) && p == h - 1 && i >= h)) {
       int64_t k = i + 1 + p;
@@ -82,13 +82,13 @@ __global__ void k_convert_rows_packed(const double* __restrict__ src, int64_t ro
   }
 }
 
-cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t n, int64_t i0, int64_t lp,
+cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t n, int64_t m, int64_t i0, int64_t lp,
                                        int storage, uint8_t* dst, cudaStream_t s) {
   const int64_t total = rows * lp;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 65536) blocks = 65536;
   if (blocks < 1) blocks = 1;
-  k_convert_rows_packed<<<(unsigned)blocks, 256, 0, s>>>(src, rows, n, i0, lp, storage, dst);
+  k_convert_rows_packed<<<(unsigned)blocks, 256, 0, s>>>(src, rows, n, m, i0, lp, storage, dst);
   return cudaGetLastError();
 }
 
@@ -103,14 +103,15 @@ __device__ __forceinline__ double probe_sign(int64_t idx, uint32_t salt) {
 }
 
 // For a skew tensor (C_ijk = -C_kji) sum_ijk x_i y_j x_k C_ijk vanishes for
-// every x, y.  One warp per row (i, j): adds x_i y_j sum_k C_ijk x_k for two
-// (x, y) pairs and sum_k C_ijk^2 into acc[0..2].
-__global__ void k_skew_probe(const double* __restrict__ src, int64_t rows, int64_t n, int64_t i0, double* acc) {
+// every x, y.  One warp per row (i, j) (m rows per test index): adds
+// x_i y_j sum_k C_ijk x_k for two (x, y) pairs and sum_k C_ijk^2 into acc[0..2].
+__global__ void k_skew_probe(const double* __restrict__ src, int64_t rows, int64_t n, int64_t m, int64_t i0,
+                             double* acc) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   double p1 = 0.0, p2 = 0.0, sq = 0.0;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
-    const int64_t i = i0 + r / n, j = (i0 * n + r) % n;
+    const int64_t i = i0 + r / m, j = r % m;
     double s1 = 0.0, s2 = 0.0, q = 0.0;
     for (int64_t k = lane; k < n; k += 32) {
       const double c = src[r * n + k];
@@ -135,11 +136,12 @@ __global__ void k_skew_probe(const double* __restrict__ src, int64_t rows, int64
   }
 }
 
-cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t i0, double* acc, cudaStream_t s) {
+cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t m, int64_t i0, double* acc,
+                              cudaStream_t s) {
   int64_t blocks = (rows + 7) / 8;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_skew_probe<<<(unsigned)blocks, 256, 0, s>>>(src, rows, n, i0, acc);
+  k_skew_probe<<<(unsigned)blocks, 256, 0, s>>>(src, rows, n, m, i0, acc);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ import numpy as np
 
 BASE_SEED = 20231106
 STREAM_S, STREAM_G, STREAM_U, STREAM_V, STREAM_W, STREAM_IC, STREAM_ARRIVAL = 1, 2, 3, 4, 5, 6, 7
+STREAM_SVD_U, STREAM_SVD_V = 8, 9
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_synth.so")
@@ -127,6 +128,17 @@ def cp_tensor(U, V, W, seed, resid_scale, i0=0, i1=None, block=16):
         flat = out.reshape(-1)
         _load().synth_add_skew_normal_slab(n, seed, STREAM_G, float(resid_scale), i0, i1, _ptr(flat))
     return out
+
+
+def svd_workload(n, rank, seed):
+    """Seeded factors shaped like the SVD-ROM's (Sec. 4.4.2): U (n x rank,
+    z / sqrt(n), stream 8), sigma_r = 1/r, and V (n x rank x n) whose slices
+    V[:, r, :] = (G_r - G_r^T)/n are exactly skew (G from stream 9)."""
+    U = normal(seed, STREAM_SVD_U, 0, n * rank).reshape(n, rank) / np.sqrt(n)
+    sigma = 1.0 / np.arange(1, rank + 1, dtype=np.float64)
+    G = normal(seed, STREAM_SVD_V, 0, n * rank * n).reshape(n, rank, n)
+    V = (G - G.transpose(2, 1, 0)) / n
+    return np.ascontiguousarray(U), sigma, np.ascontiguousarray(V)
 
 
 def initial_condition(n, seed, traj=0, count=1):

@@ -212,3 +212,42 @@ def test_profiling_inside_graph_replays(layout):
     t1.close()
     t2.close()
     rom.close()
+
+
+@pytest.mark.parametrize("layout", ["dense", "skew_packed"])
+def test_step_host_paths_agree(layout):
+    # grom_step_host with pinned buffers (one captured graph per call), with
+    # device buffers (graph) and with pageable numpy buffers (direct launches)
+    # gives the state grom_step gives, bit for bit
+    n, batch = 80, 2
+    seed = synth.seed_for(0) + 7900
+    C = synth.skew_normal_tensor(n, seed)
+    U0 = synth.initial_condition(n, seed, 0, batch)
+    rom = _rom(C, "bf16", layout=layout, max_batch=batch)
+    ref = grom.Trajectories(rom, U0)
+    ref.step(5)
+    want = ref.get_state()[:, :n]
+
+    pinned = torch.from_numpy(U0.copy()).pin_memory()
+    t1 = grom.Trajectories(rom, U0)
+    t1.step_host(1, pinned, pinned)
+    t1.step_host(1, pinned, pinned)   # graph reused
+    other = torch.empty_like(pinned).pin_memory()
+    t1.step_host(3, pinned, other)    # new buffers and count: graph captured again
+    np.testing.assert_array_equal(other.numpy(), want)
+
+    dev = torch.from_numpy(U0.copy()).cuda()
+    t2 = grom.Trajectories(rom, U0)
+    for _ in range(5):
+        t2.step_host(1, dev, dev)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), want)
+
+    host = U0.copy()
+    t3 = grom.Trajectories(rom, U0)
+    for _ in range(5):
+        t3.step_host(1, host, host)
+    np.testing.assert_array_equal(host, want)
+    for t in (ref, t1, t2, t3):
+        t.close()
+    rom.close()
