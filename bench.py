@@ -53,12 +53,12 @@ L2_BYTES = 129 * 2 ** 20
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="grom", choices=["grom", "reference"])
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--rank", type=int, default=0, help="CP rank (default N)")
-    p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64:skew_packed,cp_skew:bf16 (layout defaults to dense)")
+    p.add_argument("--variants", default="all", help="'all', 'none' or comma list like full:f64:skew_packed,cp_skew:bf16,aug (layout defaults to dense; aug = the model with the zeroth mode)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batches", default="16,64,256,1024", help="batched-trajectory sizes ('none' to skip)")
@@ -94,7 +94,15 @@ class ClockSampler:
                  "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        time.sleep(0.3)
+        # wait until nvidia-smi is polling (its start-up must not fall inside
+        # the timed region)
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 10.0:
+            with open(self.path) as fh:
+                if fh.readline():
+                    break
+            time.sleep(0.05)
+        time.sleep(0.2)
 
     def stop(self):
         if self.proc is None:
@@ -531,7 +539,8 @@ def main():
 
     # ------------------------------------------------------------ variants
     wanted = VARIANTS if args.variants == "all" else (
-        [] if args.variants == "none" else [tuple((v + ":dense").split(":")[:3]) for v in args.variants.split(",")])
+        [] if args.variants == "none" else [tuple((v + ":dense").split(":")[:3]) for v in args.variants.split(",")
+                                            if v != "aug"])
     flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device="cuda")
     variants = {}
     for form, storage, layout in wanted:
@@ -560,6 +569,32 @@ def main():
         entry["status"] = grom.ERRORS.get(vcode, "OK") if vcode else "OK"
         variants[key] = entry
         vrom.close()
+    # the model including the zeroth mode (Sec. 4.2): skew-packed BF16 core,
+    # zeroth-mode terms in the stepper's L and f (dense-L step)
+    if args.variants == "all" or "aug" in args.variants.split(","):
+        Cbar = synth.augment_tensor_device(C, seed)
+        vrom = grom.Rom(n, "full", "bf16", tensor=Cbar, stiffness=a, nu=NU, dt=DT, layout="skew_packed",
+                        augmented=True)
+        vsteps = max(10, min(args.steps, 200))
+        vms, vcode, _ = time_variant(grom, torch, vrom, u0, vsteps, 3)
+        entry = {"ms_per_step": vms, "steps_per_s": 1e3 / vms, "l2": "tensor > L2", "layout": "skew_packed",
+                 "zeroth_mode": "L += C1 + C2 (dense), f += c0"}
+        if rank_id == 0:
+            Cbh = Cbar.cpu().numpy()
+            ref_rom = oracle.Rom("full_aug", n, a, NU, DT, C=Cbh)
+            h = ref_rom.initial_history(u0[0])
+            ref_rom.step(h, 3)
+            vt = grom.Trajectories(vrom, u0)
+            vt.step(3)
+            entry["traj_rel_err_after_3_steps_vs_fp64_oracle"] = rel(vt.get_state()[0][:n], h[:n])
+            entry["tolerance"] = TOL["bf16"]
+            vt.close()
+            del Cbh
+        entry["status"] = grom.ERRORS.get(vcode, "OK") if vcode else "OK"
+        variants["full_bf16_packed_augmented"] = entry
+        vrom.close()
+        del Cbar
+        torch.cuda.empty_cache()
     # SVD-ROM (Sec. 4.4.2) at the requested ranks: skew-packed BF16 slices
     if args.svd_ranks and args.svd_ranks != "none" and args.variants != "none":
         ranks = [int(x) for x in args.svd_ranks.split(",")]

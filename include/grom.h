@@ -133,7 +133,19 @@ typedef struct grom_desc {
   int32_t max_batch;    /* largest batch passed to grom_nonlinear/grom_traj_create
                            (sizes the library's scratch); 0 means 1              */
   int32_t layout;       /* FULL and SVD: GROM_LAYOUT_DENSE (0) or GROM_LAYOUT_SKEW_PACKED */
-  int32_t reserved[3];  /* must be zero                                           */
+  /* 1: the operator includes the zeroth mode phi_0 (coefficient 1 in the
+   * augmented vector ubar = (1, u), eq. nse_ode; the "full" tensor of
+   * Sec. 4.2).  FULL: tensor holds n x (n+1) x (n+1) doubles Cbar[i][j][k]
+   * (j, k = 0 is the zeroth mode; defer_tensor not allowed).  The core
+   * j, k >= 1 becomes the advection tensor, and the zeroth-mode terms join the
+   * stepper (eq. nse_d1, eq. zeroth_contribution): L += C1 + C2 with
+   * C1_ik = Cbar[i][0][k], C2_ij = Cbar[i][j][0], and f += c0 with
+   * c0_i = Cbar[i][0][0].  CP (general form only): fb and fc have n+1 rows,
+   * row 0 the zeroth mode; L += A diag(fb_0) fc'^T + A diag(fc_0) fb'^T and
+   * f += A (fb_0 o fc_0), fb', fc' the rows 1..n.  grom_nonlinear then
+   * evaluates the core term only; grom_step advances the full model. */
+  int32_t augmented;
+  int32_t reserved[2];  /* must be zero                                           */
 } grom_desc;
 
 /* Creates a ROM on the current CUDA device.  Every input is copied; the caller

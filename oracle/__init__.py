@@ -64,6 +64,8 @@ def _load():
             "oracle_cp_skew_expand": [i64, i64, vp, vp, vp, vp, vp, vp],
             "oracle_cp_reconstruct": [i64, i64, vp, vp, vp, vp],
             "oracle_nonlinear_svd": [i64, i64, vp, vp, vp, vp, vp],
+            "oracle_nonlinear_full_augmented": [i64, vp, vp, vp],
+            "oracle_nonlinear_cp_augmented": [i64, i64, vp, vp, vp, vp, vp],
             "oracle_bdf_ext_coefficients": [ctypes.c_int, vp, vp],
             "oracle_cholesky_solve": [i64, vp, vp, vp],
             "oracle_set_threads": [ctypes.c_int],
@@ -164,6 +166,27 @@ def nonlinear_svd(U, sigma, V, u):
     return c
 
 
+def nonlinear_full_augmented(Cbar, u):
+    """c_i = sum_{j,k=0..n} Cbar_ijk ubar_j ubar_k, ubar = (1, u); Cbar is
+    n x (n+1) x (n+1) with index 0 the zeroth mode (Sec. 4.2)."""
+    Cbar, u = _f64(Cbar), _f64(u)
+    n = u.size
+    assert Cbar.shape == (n, n + 1, n + 1)
+    c = np.empty(n)
+    _load().oracle_nonlinear_full_augmented(n, _p(Cbar), _p(u), _p(c))
+    return c
+
+
+def nonlinear_cp_augmented(A, Bbar, Cbar, u):
+    """CP contraction with ubar = (1, u): A is n x r, Bbar and Cbar (n+1) x r."""
+    A, Bbar, Cbar, u = _f64(A), _f64(Bbar), _f64(Cbar), _f64(u)
+    n, r = A.shape
+    assert Bbar.shape == (n + 1, r) and Cbar.shape == (n + 1, r)
+    c = np.empty(n)
+    _load().oracle_nonlinear_cp_augmented(n, r, _p(A), _p(Bbar), _p(Cbar), _p(u), _p(c))
+    return c
+
+
 def advecting_matricization(C):
     """The tensor unfolded over its advecting index: row j holds the n x n
     matrix (i, k) -> C_ijk, flattened row-major (Sec. 4.4.1)."""
@@ -217,13 +240,14 @@ class Rom:
     """A reduced model for the oracle stepper.
 
     form: "full" (C is n x n x n), "cp" (factors A, B, Cf, each n x r),
-    "cp_skew" (blocks U, V, W, each n x r) or "svd" (factors U (n x r),
-    sigma (r), V (n x r x n)).  A is the stiffness matrix (n x n,
+    "cp_skew" (blocks U, V, W, each n x r), "svd" (factors U (n x r),
+    sigma (r), V (n x r x n)), "full_aug" (C is n x (n+1) x (n+1), index 0 the
+    zeroth mode) or "cp_aug" (A n x r, B and C (n+1) x r).  A is the stiffness matrix (n x n,
     or a length-n diagonal), B the mass matrix (None = identity), L an
     optional explicit linear operator and f an optional constant forcing.
     """
 
-    FORMS = {"full": 0, "cp": 1, "cp_skew": 2, "svd": 3}
+    FORMS = {"full": 0, "cp": 1, "cp_skew": 2, "svd": 3, "full_aug": 4, "cp_aug": 5}
 
     def __init__(self, form, n, A, nu, dt, order=3, C=None, factors=None, B=None, L=None, f=None):
         self.n = int(n)

@@ -11,6 +11,8 @@
  *   - skew CP structure A1=[U W], A2=[V V], A3=[W -U]              (Sec. 3.3, eq. skew_abc_struct)
  *   - CP reconstruction X_ijk = sum_r a_ir b_jr c_kr                (Sec. 2.3, eq. cpd)
  *   - SVD-ROM contraction c_i = sum_r sigma_r (sum_j U_jr u_j)(sum_k V[i][r][k] u_k)   (Sec. 4.4.2)
+ *   - the same contractions of operators that include the zeroth mode, with the
+ *     augmented vector ubar = (1, u)                                 (Sec. 2.2, eq. nse_ode; Sec. 4.2)
  *   - BDFk/EXTk step (beta0/dt B + nu A) u^{l+1} = -sum_i alpha_i (n^{l+1-i} + L u^{l+1-i} + f)
  *                                                  - B sum_i beta_i/dt u^{l+1-i}   (Sec. 2.2, eq. nse_d1)
  *     solved with a dense Cholesky factorisation written here.
@@ -160,6 +162,50 @@ void oracle_nonlinear_svd(int64_t n, int64_t r, const double* U, const double* s
   free(a);
 }
 
+/* Full tensor including the zeroth mode (Sec. 4.2): Cbar is n x (n+1) x (n+1)
+ * (test index 1..n, advecting and advected index 0..n, index 0 the zeroth
+ * mode) and c_i = sum_{j,k=0..n} Cbar_ijk ubar_j ubar_k with ubar = (1, u). */
+void oracle_nonlinear_full_augmented(int64_t n, const double* Cbar, const double* u, double* c) {
+  const int64_t n1 = n + 1;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t j = 0; j < n1; ++j) {
+      const double uj = j == 0 ? 1.0 : u[j - 1];
+      for (int64_t k = 0; k < n1; ++k) {
+        const double uk = k == 0 ? 1.0 : u[k - 1];
+        s += Cbar[(i * n1 + j) * n1 + k] * uj * uk;
+      }
+    }
+    c[i] = s;
+  }
+}
+
+/* CP form of a tensor including the zeroth mode: A is n x r, Bbar and Cbar
+ * are (n+1) x r (row 0 the zeroth mode), c_i = sum_m A_im (sum_j Bbar_jm
+ * ubar_j)(sum_k Cbar_km ubar_k). */
+void oracle_nonlinear_cp_augmented(int64_t n, int64_t r, const double* A, const double* Bbar, const double* Cbar,
+                                   const double* u, double* c) {
+  double* p = (double*)malloc((size_t)r * sizeof(double));
+  double* q = (double*)malloc((size_t)r * sizeof(double));
+  for (int64_t m = 0; m < r; ++m) {
+    double sp = Bbar[m], sq = Cbar[m];
+    for (int64_t j = 0; j < n; ++j) {
+      sp += Bbar[(j + 1) * r + m] * u[j];
+      sq += Cbar[(j + 1) * r + m] * u[j];
+    }
+    p[m] = sp;
+    q[m] = sq;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t m = 0; m < r; ++m) s += A[i * r + m] * p[m] * q[m];
+    c[i] = s;
+  }
+  free(p);
+  free(q);
+}
+
 /* ---------------------------------------------------------------- stepper */
 
 /* BDFk/EXTk coefficients for k = 1, 2, 3 (standard values; the paper states
@@ -216,7 +262,9 @@ void oracle_cholesky_solve(int64_t n, const double* L, const double* b, double* 
 /* The reduced model stepped by the oracle.  form: 0 = dense tensor C,
  * 1 = general CP factors (fa, fb, fc; n x rank), 2 = skew CP blocks
  * (fa = U, fb = V, fc = W; n x rank), 3 = SVD factors (fa = U, n x rank;
- * fb = sigma, rank; fc = V, n x rank x n).  A is n x n (dense), B is n x n or
+ * fb = sigma, rank; fc = V, n x rank x n), 4 = tensor including the zeroth
+ * mode (C is n x (n+1) x (n+1)), 5 = CP factors including the zeroth mode
+ * (fa n x rank, fb and fc (n+1) x rank).  A is n x n (dense), B is n x n or
  * NULL for the identity, L is n x n or NULL, f has n entries or is NULL. */
 typedef struct {
   int64_t n;
@@ -242,8 +290,12 @@ static void rom_nonlinear(const oracle_rom* m, const double* u, double* c) {
     oracle_nonlinear_cp(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
   else if (m->form == 2)
     oracle_nonlinear_cp_skew(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
-  else
+  else if (m->form == 3)
     oracle_nonlinear_svd(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
+  else if (m->form == 4)
+    oracle_nonlinear_full_augmented(m->n, m->C, u, c);
+  else
+    oracle_nonlinear_cp_augmented(m->n, m->rank, m->fa, m->fb, m->fc, u, c);
 }
 
 static void matvec(int64_t n, const double* M, const double* x, double* y) {

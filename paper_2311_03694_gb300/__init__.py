@@ -54,7 +54,7 @@ class _Desc(ctypes.Structure):
         ("linear", ctypes.c_void_p), ("linear_diag", ctypes.c_void_p), ("forcing", ctypes.c_void_p),
         ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("order", ctypes.c_int32),
         ("defer_tensor", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("layout", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("augmented", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -193,11 +193,13 @@ class Rom:
     diagonal or an n x n matrix; mass None means identity.
     layout (full and svd forms): "dense" or "skew_packed" (one entry of each
     pair C_ijk = -C_kji stored; the tensor, or each V slice, must be skew).
+    augmented: the operator includes the zeroth mode (full: tensor n x (n+1)
+    x (n+1); cp: fb and fc with n+1 rows); see grom_desc.augmented.
     """
 
     def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,
                  linear=None, forcing=None, nu=1e-2, dt=1e-3, order=3, max_batch=1, defer_tensor=False,
-                 stream=None, layout="dense"):
+                 stream=None, layout="dense", augmented=False):
         lib = load()
         keep = []
 
@@ -214,6 +216,7 @@ class Rom:
         d.nu, d.dt, d.order, d.max_batch = float(nu), float(dt), int(order), int(max_batch)
         d.defer_tensor = 1 if defer_tensor else 0
         d.layout = LAYOUTS[layout]
+        d.augmented = 1 if augmented else 0
         if form == "full":
             d.tensor = arr(tensor)
         else:

@@ -137,6 +137,48 @@ static grom_status upload_rows_packed(grom_rom* r, const double* src, int64_t i0
   return GROM_OK;
 }
 
+// Augmented FULL tensor (n x (n+1) x (n+1), index 0 the zeroth mode): the
+// core rows are converted like a plain tensor (dense or skew-packed), and the
+// zeroth-mode terms L = C1 + C2 and f = c0 come back on the host.
+static grom_status check_skew_probe(grom_rom* r);
+static grom_status upload_augmented_full(grom_rom* r, const double* src, std::vector<double>& L, std::vector<double>& f) {
+  const int64_t n = r->n, n1 = n + 1;
+  const int64_t per_src = n1 * n1, per_core = n * n;  // doubles per test index
+  const int64_t si = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)(256ll << 20) / (per_src * 8)));
+  const bool packed = r->layout == GROM_LAYOUT_SKEW_PACKED;
+  double *stage = nullptr, *core = nullptr, *dl = nullptr, *df = nullptr;
+  grom_status st = dmalloc(&stage, (size_t)(si * per_src * 8), nullptr);
+  if (!st) st = dmalloc(&core, (size_t)(si * per_core * 8), nullptr);
+  if (!st) st = dmalloc(&dl, (size_t)(n * n * 8), nullptr);
+  if (!st) st = dmalloc(&df, (size_t)(n * 8), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int64_t a = 0; !st && e == cudaSuccess && a < n; a += si) {
+    const int64_t cnt = std::min(si, n - a);
+    e = cudaMemcpyAsync(stage, src + a * per_src, (size_t)(cnt * per_src * 8), cudaMemcpyDefault, r->stream);
+    if (e == cudaSuccess) e = aug_split_launch(stage, cnt, n, core, dl + a * n, df + a, r->stream);
+    if (e == cudaSuccess && packed) {
+      e = skew_probe_launch(core, cnt * n, n, n, a, r->probe, r->stream);
+      if (e == cudaSuccess)
+        e = convert_rows_packed_launch(core, cnt * n, n, n, a, r->k1.lp, r->storage, r->op + a * n * r->k1.row_bytes,
+                                       r->stream);
+    } else if (e == cudaSuccess) {
+      e = convert_rows_launch(core, cnt * n, n, r->np, r->storage, r->op + a * n * r->k1.row_bytes, r->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  }
+  if (!st && e == cudaSuccess) {
+    L.resize((size_t)(n * n));
+    f.resize((size_t)n);
+    e = cudaMemcpy(L.data(), dl, (size_t)(n * n * 8), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(f.data(), df, (size_t)(n * 8), cudaMemcpyDeviceToHost);
+  }
+  for (double* p : {stage, core, dl, df})
+    if (p) cudaFree(p);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "augmented tensor upload");
+  return packed ? check_skew_probe(r) : GROM_OK;
+}
+
 // After the last row: the probes of a skew tensor vanish up to rounding.
 static grom_status check_skew_probe(grom_rom* r) {
   double acc[3];
@@ -248,8 +290,11 @@ int32_t grom_max_n(int32_t form, int32_t storage) {
 grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   if (!d || !out) return fail(GROM_ERR_INVALID_ARG, "grom_create: null argument");
   *out = nullptr;
-  for (int q = 0; q < 3; ++q)
+  for (int q = 0; q < 2; ++q)
     if (d->reserved[q]) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
+  if (d->augmented != 0 && d->augmented != 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: augmented must be 0 or 1");
+  if (d->augmented && !((d->form == GROM_FORM_FULL && d->tensor) || d->form == GROM_FORM_CP))
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: augmented needs the full form with its tensor, or the general CP form");
   if (d->layout != GROM_LAYOUT_DENSE && d->layout != GROM_LAYOUT_SKEW_PACKED)
     return fail(GROM_ERR_INVALID_ARG, "grom_create: unknown layout");
   if (d->layout != GROM_LAYOUT_DENSE && d->form != GROM_FORM_FULL && d->form != GROM_FORM_SVD)
@@ -295,6 +340,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   r->stream = static_cast<cudaStream_t>(stream);
   const int64_t n = r->n;
   grom_status st = GROM_OK;
+  std::vector<double> Laug, faug;  // zeroth-mode terms of an augmented operator
   auto bail = [&](grom_status s) {
     cudaStreamSynchronize(r->stream);
     rom_free(r);
@@ -337,7 +383,10 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
         if ((st = dmalloc(&r->k2_scratch, need, &r->total_bytes))) return bail(st);
       }
     }
-    if (d->tensor) {
+    if (d->tensor && d->augmented) {
+      if ((st = upload_augmented_full(r, d->tensor, Laug, faug))) return bail(st);
+      r->rows_uploaded = n;
+    } else if (d->tensor) {
       if (packed) {
         if ((st = upload_rows_packed(r, d->tensor, 0, n))) return bail(st);
         if ((st = check_skew_probe(r))) return bail(st);
@@ -388,7 +437,9 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     r->panel_bytes = (r->panel_bytes + 255) / 256 * 256;
     r->op_bytes = 3 * r->panel_bytes;
     if ((st = dmalloc(&r->op, r->op_bytes, &r->total_bytes))) return bail(st);
-    const double* f[3] = {d->fa, d->fb, d->fc};
+    // augmented factors: rows 1..n of fb and fc are the core factors
+    const int64_t off = d->augmented ? r->rank : 0;
+    const double* f[3] = {d->fa, d->fb + off, d->fc + off};
     for (int q = 0; q < 3; ++q)
       if ((st = upload_rows(r, f[q], n, r->rank, rp, r->op + q * r->panel_bytes, rp * storage_elem_bytes(r->storage))))
         return bail(st);
@@ -412,6 +463,29 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       return bail(cuda_fail(cudaGetLastError(), "grom_create"));
   }
 
+  if (d->augmented && r->form == GROM_FORM_CP) {
+    // zeroth-mode terms of the CP model: X_i0k = sum_m A_im b0_m C_km,
+    // X_ij0 = sum_m A_im B_jm c0_m, X_i00 = sum_m A_im b0_m c0_m
+    const int64_t R = r->rank;
+    std::vector<double> Af, Bf, Cf;
+    if ((st = fetch(Af, d->fa, (size_t)(n * R)))) return bail(st);
+    if ((st = fetch(Bf, d->fb, (size_t)((n + 1) * R)))) return bail(st);
+    if ((st = fetch(Cf, d->fc, (size_t)((n + 1) * R)))) return bail(st);
+    Laug.assign((size_t)(n * n), 0.0);
+    faug.assign((size_t)n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+      const double* Ai = Af.data() + i * R;
+      for (int64_t m = 0; m < R; ++m) faug[i] += Ai[m] * Bf[m] * Cf[m];
+      for (int64_t k = 0; k < n; ++k) {
+        const double* Bk = Bf.data() + (k + 1) * R;
+        const double* Ck = Cf.data() + (k + 1) * R;
+        double s = 0.0;
+        for (int64_t m = 0; m < R; ++m) s += Ai[m] * (Bf[m] * Ck[m] + Cf[m] * Bk[m]);
+        Laug[i * n + k] = s;
+      }
+    }
+  }
+
   // ------------------------------------------------------ linear operators
   std::vector<double> A, Bm, mdiag, adiag;
   const bool a_dense = d->stiffness != nullptr;
@@ -428,7 +502,8 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   } else {
     mdiag.assign((size_t)n, 1.0);
   }
-  r->diagonal = !a_dense && !b_dense && !d->linear;
+  const bool aug = d->augmented != 0;
+  r->diagonal = !a_dense && !b_dense && !d->linear && !aug;
   const bool h_diag = !a_dense && !b_dense;
   if (h_diag) {
     std::vector<double> hd((size_t)(3 * n));
@@ -460,10 +535,34 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   } else if (d->mass_diag) {
     if ((st = upload(&r->mass_diag, mdiag.data(), mdiag.size(), &r->total_bytes, r->stream))) return bail(st);
   }
-  if (d->linear && (st = upload(&r->linear, d->linear, (size_t)(n * n), &r->total_bytes, r->stream))) return bail(st);
-  if (d->linear_diag && (st = upload(&r->lin_diag, d->linear_diag, (size_t)n, &r->total_bytes, r->stream)))
-    return bail(st);
-  if (d->forcing && (st = upload(&r->forcing, d->forcing, (size_t)n, &r->total_bytes, r->stream))) return bail(st);
+  if (aug) {
+    // the caller's L and f plus the zeroth-mode terms, as a dense L
+    std::vector<double> Lh, fh, tmp;
+    if (d->linear) {
+      if ((st = fetch(Lh, d->linear, (size_t)(n * n)))) return bail(st);
+    } else {
+      Lh.assign((size_t)(n * n), 0.0);
+      if (d->linear_diag) {
+        if ((st = fetch(tmp, d->linear_diag, (size_t)n))) return bail(st);
+        for (int64_t i = 0; i < n; ++i) Lh[i * n + i] = tmp[i];
+      }
+    }
+    if (d->forcing) {
+      if ((st = fetch(fh, d->forcing, (size_t)n))) return bail(st);
+    } else {
+      fh.assign((size_t)n, 0.0);
+    }
+    for (size_t q = 0; q < Lh.size(); ++q) Lh[q] += Laug[q];
+    for (size_t q = 0; q < fh.size(); ++q) fh[q] += faug[q];
+    if ((st = upload(&r->linear, Lh.data(), Lh.size(), &r->total_bytes, r->stream))) return bail(st);
+    if ((st = upload(&r->forcing, fh.data(), fh.size(), &r->total_bytes, r->stream))) return bail(st);
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "upload"));
+  } else {
+    if (d->linear && (st = upload(&r->linear, d->linear, (size_t)(n * n), &r->total_bytes, r->stream))) return bail(st);
+    if (d->linear_diag && (st = upload(&r->lin_diag, d->linear_diag, (size_t)n, &r->total_bytes, r->stream)))
+      return bail(st);
+    if (d->forcing && (st = upload(&r->forcing, d->forcing, (size_t)n, &r->total_bytes, r->stream))) return bail(st);
+  }
   if ((st = dmalloc(&r->err, 2 * sizeof(int), &r->total_bytes))) return bail(st);
   if (cudaMemsetAsync(r->err, 0, 2 * sizeof(int), r->stream) != cudaSuccess ||
       cudaStreamSynchronize(r->stream) != cudaSuccess)

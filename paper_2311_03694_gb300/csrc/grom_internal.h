@@ -218,6 +218,11 @@ cudaError_t convert_rows_packed_launch(const double* src, int64_t rows, int64_t 
 // i0) into acc[0..2] (probe 1, probe 2, sum of squares).
 cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_t m, int64_t i0, double* acc,
                               cudaStream_t s);
+// Augmented tensor slab (cnt test indices of (n+1) x (n+1) values, index 0
+// the zeroth mode) -> the core rows (cnt x n x n) and, for those test
+// indices, L_ik = Cbar[i][0][k+1] + Cbar[i][k+1][0] and f_i = Cbar[i][0][0].
+cudaError_t aug_split_launch(const double* src, int64_t cnt, int64_t n, double* core, double* L, double* f,
+                             cudaStream_t s);
 // SVD-ROM middle weights beta[b][r] = sigma_r sum_j U_jr u_bj (k_svd.cu).
 cudaError_t svd_project_launch(const double* ut, const double* sigma, int64_t n, int64_t rank, int batch,
                                const double* u, int64_t u_stride, const double* hist, const int64_t* taken,

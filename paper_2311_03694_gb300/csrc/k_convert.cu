@@ -145,6 +145,32 @@ cudaError_t skew_probe_launch(const double* src, int64_t rows, int64_t n, int64_
   return cudaGetLastError();
 }
 
+// Splits an augmented tensor slab into its core rows and zeroth-mode terms
+// (eq. zeroth_contribution); see grom_desc.augmented.
+__global__ void k_aug_split(const double* __restrict__ src, int64_t cnt, int64_t n, double* __restrict__ core,
+                            double* __restrict__ L, double* __restrict__ f) {
+  const int64_t n1 = n + 1, total = cnt * n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / (n * n), rem = t - i * n * n, j = rem / n, k = rem - j * n;
+    const double* Ci = src + i * n1 * n1;
+    core[t] = Ci[(j + 1) * n1 + k + 1];
+    if (j == 0) {
+      L[i * n + k] = Ci[k + 1] + Ci[(k + 1) * n1];
+      if (k == 0) f[i] = Ci[0];
+    }
+  }
+}
+
+cudaError_t aug_split_launch(const double* src, int64_t cnt, int64_t n, double* core, double* L, double* f,
+                             cudaStream_t s) {
+  const int64_t total = cnt * n * n;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  if (blocks < 1) blocks = 1;
+  k_aug_split<<<(unsigned)blocks, 256, 0, s>>>(src, cnt, n, core, L, f);
+  return cudaGetLastError();
+}
+
 // n x r doubles -> n x rp stored elements (rank padded with zero columns).
 cudaError_t convert_panels_launch(const double* src, int64_t n, int64_t r, int64_t rp, int storage, uint8_t* dst,
                                   cudaStream_t s) {

@@ -30,6 +30,7 @@ import numpy as np
 BASE_SEED = 20231106
 STREAM_S, STREAM_G, STREAM_U, STREAM_V, STREAM_W, STREAM_IC, STREAM_ARRIVAL = 1, 2, 3, 4, 5, 6, 7
 STREAM_SVD_U, STREAM_SVD_V = 8, 9
+STREAM_ZEROTH = 10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_synth.so")
@@ -139,6 +140,40 @@ def svd_workload(n, rank, seed):
     G = normal(seed, STREAM_SVD_V, 0, n * rank * n).reshape(n, rank, n)
     V = (G - G.transpose(2, 1, 0)) / n
     return np.ascontiguousarray(U), sigma, np.ascontiguousarray(V)
+
+
+def augment_tensor(C, seed):
+    """Embeds a core tensor (n x n x n) into one that includes the zeroth mode
+    (n x (n+1) x (n+1), index 0 = phi_0): the planes j = 0 and k = 0 get
+    seeded normal entries / n (stream 10)."""
+    n = C.shape[0]
+    Cbar = np.zeros((n, n + 1, n + 1))
+    Cbar[:, 1:, 1:] = C
+    z = normal(seed, STREAM_ZEROTH, 0, n * (2 * n + 1)).reshape(n, 2 * n + 1) / n
+    Cbar[:, 0, :] = z[:, : n + 1]
+    Cbar[:, 1:, 0] = z[:, n + 1:]
+    return Cbar
+
+
+def augment_tensor_device(C, seed):
+    """augment_tensor for a core tensor held on a torch device."""
+    import torch
+
+    n = C.shape[0]
+    Cbar = torch.zeros((n, n + 1, n + 1), dtype=torch.float64, device=C.device)
+    Cbar[:, 1:, 1:] = C
+    z = torch.from_numpy(normal(seed, STREAM_ZEROTH, 0, n * (2 * n + 1)).reshape(n, 2 * n + 1) / n).to(C.device)
+    Cbar[:, 0, :] = z[:, : n + 1]
+    Cbar[:, 1:, 0] = z[:, n + 1:]
+    return Cbar
+
+
+def augment_cp(A, B, Cf, seed):
+    """General CP factors including the zeroth mode: B and C get a leading
+    row of seeded normal entries / sqrt(r) (stream 10)."""
+    n, r = A.shape
+    z = normal(seed, STREAM_ZEROTH, 0, 2 * r).reshape(2, r) / np.sqrt(r)
+    return A, np.vstack([z[0], B]), np.vstack([z[1], Cf])
 
 
 def initial_condition(n, seed, traj=0, count=1):
