@@ -214,6 +214,86 @@ def svd_reconstruct(U, sigma, V):
     return X
 
 
+# ------------------------------------------------------------ CP fitting
+def kr(P, Q):
+    """Khatri-Rao product: column r is kron(P[:, r], Q[:, r]), rows (a, b)
+    with the second index fastest."""
+    return np.einsum("ar,br->abr", _f64(P), _f64(Q)).reshape(P.shape[0] * Q.shape[0], P.shape[1])
+
+
+def mttkrp(X, factors, mode):
+    """X_(mode) times the Khatri-Rao product of the other two factors (mode
+    0, 1, 2 = first, second, third index), the right-hand side of the ALS
+    normal equations (Sec. 2.3)."""
+    A1, A2, A3 = factors
+    if mode == 0:
+        return _f64(X).reshape(X.shape[0], -1) @ kr(A2, A3)
+    if mode == 1:
+        return np.transpose(_f64(X), (1, 0, 2)).reshape(X.shape[1], -1) @ kr(A1, A3)
+    return np.transpose(_f64(X), (2, 0, 1)).reshape(X.shape[2], -1) @ kr(A1, A2)
+
+
+def gram_hadamard(factors, mode):
+    """Hadamard product of the Gram matrices of the two factors other than mode."""
+    G = np.ones((factors[0].shape[1],) * 2)
+    for q, F in enumerate(factors):
+        if q != mode:
+            G = G * (F.T @ F)
+    return G
+
+
+def als_update(X, factors, mode):
+    """Exact solution of the mode's linear least-squares subproblem of eq.
+    cp_als through its normal equations, A = MTTKRP (Hadamard of Grams)^-1."""
+    M = mttkrp(X, factors, mode)
+    return np.linalg.solve(gram_hadamard(factors, mode), M.T).T
+
+
+def cp_residual(X, factors):
+    """Relative residual ||X - [[A1, A2, A3]]||_F / ||X||_F (eq. cp_nls)."""
+    return float(np.linalg.norm(X - np.einsum("ir,jr,kr->ijk", *factors)) / np.linalg.norm(X))
+
+
+def cp_als(X, factors, iters):
+    """Plain ALS (Sec. 2.3, eq. cp_als): each iteration solves the three
+    subproblems in sequence.  Returns the factors and the relative residual
+    after every iteration."""
+    F = [_f64(f).copy() for f in factors]
+    res = []
+    for _ in range(iters):
+        for mode in range(3):
+            F[mode] = als_update(X, F, mode)
+        res.append(cp_residual(X, F))
+    return F, res
+
+
+def skew_structure(A1, B1):
+    """Skew-preserving factors (eq. skew_abc_struct) from the blocks: A1 = [A1_1 A1_2]
+    (n x R), A2 = [B1 B1], A3 = [A1_2, -A1_1]."""
+    h = A1.shape[1] // 2
+    return [A1, np.hstack([B1, B1]), np.hstack([A1[:, h:], -A1[:, :h]])]
+
+
+def cp_als_skew(X, A1, B1, iters, lam=0.5, subiters=1):
+    """ALS-skew (Sec. 3.3): A2 = [B1 B1] is updated as in ALS (its two halves,
+    equal for a skew X, are averaged); A1 takes `subiters` least-squares
+    subiterations of eq. cp_als_quad with A3 fixed, each followed by the
+    momentum update A1 <- lam A1 + (1 - lam) A1_next and A3 = [A1_2, -A1_1].
+    Returns (A1, B1) and the relative residual after every iteration."""
+    A1, B1 = _f64(A1).copy(), _f64(B1).copy()
+    h = A1.shape[1] // 2
+    res = []
+    for _ in range(iters):
+        F = skew_structure(A1, B1)
+        A2 = als_update(X, F, 1)
+        B1 = 0.5 * (A2[:, :h] + A2[:, h:])
+        for _ in range(subiters):
+            F = skew_structure(A1, B1)
+            A1 = lam * A1 + (1.0 - lam) * als_update(X, F, 0)
+        res.append(cp_residual(X, skew_structure(A1, B1)))
+    return (A1, B1), res
+
+
 def bdf_ext_coefficients(k):
     beta, alpha = np.empty(4), np.empty(3)
     _load().oracle_bdf_ext_coefficients(int(k), _p(beta), _p(alpha))
