@@ -67,6 +67,9 @@ def parse_args():
     p.add_argument("--serve-slots", type=int, default=64)
     p.add_argument("--json-out", default="")
     p.add_argument("--svd-ranks", default="64,256", help="SVD-ROM variant ranks ('none' to skip)")
+    p.add_argument("--als-ranks", default="128,512", help="CP fitting (ALS, ALS-skew) ranks ('none' to skip)")
+    p.add_argument("--als-iters", type=int, default=5)
+    p.add_argument("--als-ridge", type=float, default=1e-5, help="relative ridge of the ALS normal equations")
     p.add_argument("--layout", default="skew_packed", choices=["skew_packed", "dense"],
                    help="stored layout of the headline tensor")
     return p.parse_args()
@@ -684,6 +687,33 @@ def main():
                 ctr.close()
                 crom.close()
 
+    # -------------------------------------- CP fitting (ALS, ALS-skew)
+    fitting = {}
+    if args.als_ranks and args.als_ranks != "none":
+        als = grom.Als(C)
+        for r in [int(x) for x in args.als_ranks.split(",")]:
+            F0 = [synth.normal(seed, 30 + q, 0, n * r).reshape(n, r) / np.sqrt(n) for q in range(3)]
+            for method in ("plain", "skew"):
+                init = F0 if method == "plain" else (F0[0], F0[1][:, : r // 2])
+                als.fit(init, 1, method=method, ridge=args.als_ridge)  # warm-up (allocation, tensor maps)
+                als.stats()
+                t0 = time.perf_counter()
+                _, res = als.fit(init, args.als_iters, method=method, ridge=args.als_ridge)
+                wall = (time.perf_counter() - t0) / args.als_iters
+                mms, calls, solve = als.stats()
+                flops = 2.0 * float(n) ** 3 * r  # one MTTKRP: X_(m) (P kr Q)
+                per = mms / max(calls, 1)
+                fitting["%s_R%d" % (method, r)] = {
+                    "rank": r, "iterations": args.als_iters, "ridge": args.als_ridge, "s_per_iteration": wall,
+                    "mttkrp_per_iteration": calls / args.als_iters, "mttkrp_ms": per,
+                    "note": "one MTTKRP per iteration is the residual's <X, K>",
+                    "mttkrp_alg_tflops": flops / (per * 1e-3) / 1e12,
+                    "mttkrp_tc_frac_of_sustained_bf16": flops / (per * 1e-3) / 1e12 / tc_sustained,
+                    "host_solve_ms_per_iteration": solve / args.als_iters,
+                    "relative_residual": [float(x) for x in res],
+                    "init": "seeded normal factors / sqrt(N) (stream 30-32)"}
+        als.close()
+
     # ---------------------------------------------- CPU baseline (oracle)
     if rank_id == 0 and not args.no_cpu_baseline:
         a_rom = oracle.Rom("full", n, a, NU, DT, C=Ch)
@@ -731,6 +761,7 @@ def main():
         "variants": variants,
         "batched": batched,
         "serving": serving,
+        "fitting": fitting,
     }
     if errors:
         line["oracle"] = errors

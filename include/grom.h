@@ -325,6 +325,57 @@ grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, const void* 
  * GROM_ERR_TIMEOUT (once); the ROM stays usable.  Faults nothing. */
 grom_status grom_selftest_timeout(grom_rom* rom, int64_t limit_ns);
 
+/* ------------------------------------------------------------ CP fitting
+ * CP decomposition of a dense tensor by alternating least squares (Sec. 2.3,
+ * eq. cp_als) or by the skew-preserving ALS-skew (Sec. 3.3, eq.
+ * skew_abc_struct and cp_als_quad), the offline step that produces a
+ * CPD-ROM's factors.  Every least-squares subproblem is solved through its
+ * normal equations, A_m = MTTKRP_m (Hadamard product of the other two Gram
+ * matrices)^-1; the MTTKRP X_(m) (P kr Q) runs on the tensor cores (BF16
+ * tensor, Khatri-Rao product of the FP32 factors split into BF16 hi/lo
+ * parts, FP32 accumulation, split sums in FP64); the Gram matrices are FP64
+ * on the device and the rank x rank SPD solves FP64 Cholesky on the host. */
+typedef struct grom_als grom_als;
+#define GROM_ALS_PLAIN 0
+#define GROM_ALS_SKEW 1
+
+/* Fitting context for the n x n x n FP64 tensor (host or device, row-major
+ * [(i*n + j)*n + k], copied; the caller keeps ownership): three BF16 copies,
+ * one per matricization (3 n^2 round_up(n, 64) * 2 bytes of device memory),
+ * and ||X||_F^2 of that BF16 tensor (the one the fit sees) in FP64.  Runs on `stream` (cudaStream_t, may be NULL). */
+grom_status grom_als_create(int32_t n, const double* tensor, void* stream, grom_als** out);
+
+/* `iters` iterations from the given factors, updated in place (host arrays,
+ * row-major FP64):
+ *   GROM_ALS_PLAIN: fa, fb, fc are n x rank (A1, A2, A3); an iteration solves
+ *     the subproblems for A1, A2 and A3 in turn.
+ *   GROM_ALS_SKEW: rank even; fa = A1 = [A1_1 A1_2] (n x rank), fb = B1
+ *     (n x rank/2), fc unused (A2 = [B1 B1], A3 = [A1_2, -A1_1]).  An
+ *     iteration solves the A2 subproblem as in ALS (its two halves, equal for
+ *     a skew tensor, are averaged into B1), then `subiters` times solves the
+ *     A1 subproblem with A2, A3 fixed and sets A1 <- lambda A1 + (1 - lambda)
+ *     A1_next, A3 = [A1_2, -A1_1] (0 <= lambda < 1).
+ * ridge (>= 0): every normal matrix H gets ridge * max diag(H) added to its
+ * diagonal (Tikhonov; 0 = the exact normal equations of the paper).  The
+ * MTTKRP's relative noise (~1e-5 to 1e-3 under heavy cancellation) is
+ * amplified by the condition number of H, which ALS on tensors dominated by a
+ * few components drives to 1e9 and beyond; a ridge near 1e-5 keeps such fits
+ * stable.
+ * residual (nullable, iters entries): ||X - [[A1, A2, A3]]||_F / ||X||_F of the
+ * BF16 tensor after each iteration, from ||X||^2 - 2 <X, K> + ||K||^2 with
+ * <X, K> from one extra mode-1 MTTKRP of the final factors (the FP32
+ * accumulation limits it to about 1e-5 in the squared residual).  A numerically singular normal
+ * matrix is solved with a ridge mu I, mu = 1e-12 max diag, growing 100x up
+ * to three times.  Errors: INVALID_ARG (sizes, odd rank for SKEW, a
+ * Gram product that is not positive definite), OOM, CUDA, TIMEOUT. */
+grom_status grom_als_fit(grom_als* als, int32_t rank, int32_t method, int32_t iters, double lambda, int32_t subiters,
+                         double ridge, double* fa, double* fb, double* fc, double* residual);
+/* Time spent since the previous call: summed device time of the MTTKRP
+ * launches (CUDA events around each tensor-core launch), their number, and
+ * the host time of the SPD solves (ms).  Resets the counters. */
+grom_status grom_als_stats(grom_als* als, double* mttkrp_ms, int64_t* mttkrp_calls, double* solve_ms);
+grom_status grom_als_destroy(grom_als* als);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* grom_last_error(void);
 

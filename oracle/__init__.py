@@ -242,11 +242,29 @@ def gram_hadamard(factors, mode):
     return G
 
 
-def als_update(X, factors, mode):
+def spd_solve(H, B):
+    """H^-1 B for the symmetric positive (semi)definite H through its Cholesky
+    factor; a numerically singular H is retried with H + mu I, mu = 1e-12
+    max diag(H), growing 100x up to three times (the paper is silent on
+    singular normal equations)."""
+    mu = 0.0
+    for _ in range(4):
+        try:
+            L = np.linalg.cholesky(H + mu * np.eye(H.shape[0]))
+            return np.linalg.solve(L.T, np.linalg.solve(L, B))
+        except np.linalg.LinAlgError:
+            mu = 1e-12 * np.max(np.diag(H)) if mu == 0.0 else mu * 100.0
+    raise np.linalg.LinAlgError("Gram matrix is not positive definite")
+
+
+def als_update(X, factors, mode, ridge=0.0):
     """Exact solution of the mode's linear least-squares subproblem of eq.
-    cp_als through its normal equations, A = MTTKRP (Hadamard of Grams)^-1."""
+    cp_als through its normal equations, A = MTTKRP (Hadamard of Grams)^-1;
+    ridge > 0 adds ridge * max diag to the normal matrix (Tikhonov)."""
     M = mttkrp(X, factors, mode)
-    return np.linalg.solve(gram_hadamard(factors, mode), M.T).T
+    H = gram_hadamard(factors, mode)
+    H = H + ridge * np.max(np.diag(H)) * np.eye(H.shape[0])
+    return spd_solve(H, M.T).T
 
 
 def cp_residual(X, factors):
@@ -254,7 +272,7 @@ def cp_residual(X, factors):
     return float(np.linalg.norm(X - np.einsum("ir,jr,kr->ijk", *factors)) / np.linalg.norm(X))
 
 
-def cp_als(X, factors, iters):
+def cp_als(X, factors, iters, ridge=0.0):
     """Plain ALS (Sec. 2.3, eq. cp_als): each iteration solves the three
     subproblems in sequence.  Returns the factors and the relative residual
     after every iteration."""
@@ -262,7 +280,7 @@ def cp_als(X, factors, iters):
     res = []
     for _ in range(iters):
         for mode in range(3):
-            F[mode] = als_update(X, F, mode)
+            F[mode] = als_update(X, F, mode, ridge)
         res.append(cp_residual(X, F))
     return F, res
 
@@ -274,7 +292,7 @@ def skew_structure(A1, B1):
     return [A1, np.hstack([B1, B1]), np.hstack([A1[:, h:], -A1[:, :h]])]
 
 
-def cp_als_skew(X, A1, B1, iters, lam=0.5, subiters=1):
+def cp_als_skew(X, A1, B1, iters, lam=0.5, subiters=1, ridge=0.0):
     """ALS-skew (Sec. 3.3): A2 = [B1 B1] is updated as in ALS (its two halves,
     equal for a skew X, are averaged); A1 takes `subiters` least-squares
     subiterations of eq. cp_als_quad with A3 fixed, each followed by the
@@ -285,11 +303,11 @@ def cp_als_skew(X, A1, B1, iters, lam=0.5, subiters=1):
     res = []
     for _ in range(iters):
         F = skew_structure(A1, B1)
-        A2 = als_update(X, F, 1)
+        A2 = als_update(X, F, 1, ridge)
         B1 = 0.5 * (A2[:, :h] + A2[:, h:])
         for _ in range(subiters):
             F = skew_structure(A1, B1)
-            A1 = lam * A1 + (1.0 - lam) * als_update(X, F, 0)
+            A1 = lam * A1 + (1.0 - lam) * als_update(X, F, 0, ridge)
         res.append(cp_residual(X, skew_structure(A1, B1)))
     return (A1, B1), res
 

@@ -93,6 +93,14 @@ EXPORTS = {
     "grom_server_destroy": ([ctypes.c_void_p], ctypes.c_int32),
     "grom_selftest_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "grom_last_error": ([], ctypes.c_char_p),
+    "grom_als_create": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                        ctypes.c_int32),
+    "grom_als_fit": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                      ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p], ctypes.c_int32),
+    "grom_als_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "grom_als_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int32),
 }
 
 
@@ -335,6 +343,51 @@ class Trajectories:
     def close(self):
         if getattr(self, "_h", None):
             _check(load().grom_traj_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Als:
+    """CP fitting context (grom_als_create / grom_als_fit / grom_als_destroy)."""
+
+    METHODS = {"plain": 0, "skew": 1}
+
+    def __init__(self, tensor, stream=None):
+        n = int(tensor.shape[0])
+        if isinstance(tensor, np.ndarray):
+            tensor = np.ascontiguousarray(tensor, dtype=np.float64)
+        self._keep = tensor
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(load().grom_als_create(n, _ptr(tensor), ctypes.c_void_p(self._stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def fit(self, factors, iters, method="plain", lam=0.5, subiters=1, ridge=0.0):
+        """Runs `iters` iterations from `factors` ((A1, A2, A3) for "plain",
+        (A1, B1) for "skew"); returns the new factors and the residuals."""
+        fs = [np.array(f, dtype=np.float64, order="C") for f in factors]
+        rank = fs[0].shape[1]
+        res = np.empty(iters)
+        fc = _ptr(fs[2]) if len(fs) > 2 else None
+        _check(load().grom_als_fit(self._h, int(rank), self.METHODS[method], int(iters), float(lam), int(subiters),
+                                   float(ridge), _ptr(fs[0]), _ptr(fs[1]), fc, _ptr(res)))
+        return fs, res
+
+    def stats(self):
+        """(MTTKRP device ms, MTTKRP launches, host solve ms) since the last call."""
+        ms, calls, solve = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(load().grom_als_stats(self._h, ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(solve)))
+        return ms.value, calls.value, solve.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().grom_als_destroy(self._h)
             self._h = None
 
     def __del__(self):

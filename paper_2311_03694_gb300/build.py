@@ -21,6 +21,7 @@ SOURCES = [
     "k_convert.cu",
     "k_step.cu",
     "k_svd.cu",
+    "als.cu",
     "k3_cp.cu",
     "k3_gemm.cu",
     "k3_persistent.cu",

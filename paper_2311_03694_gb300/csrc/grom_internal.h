@@ -91,6 +91,12 @@ struct K2Args {
   void* scratch;  // k2_scratch_bytes(plan)
   int* err;
   cudaEvent_t ev0, ev1;
+  // MTTKRP: factor matrices P (middle index) and Q (inner index), row-major
+  // n x f_stride FP64 on the device; column b < batch is rank component b.
+  // Null for the contraction with the states.
+  const double* fp;
+  const double* fq;
+  int64_t f_stride;
 };
 K2Plan k2_plan(int64_t n, int batch, int sm_count);
 size_t k2_scratch_bytes(const K2Plan& p);

@@ -25,6 +25,10 @@
 // kernel sums the splits in a fixed order (deterministic) into FP64.
 // K-tiles are ordered with the advected block outer and j inner, so each
 // generator thread keeps its 64 u_bk values in registers across j.
+//
+// The same kernel computes the MTTKRP of CP fitting (Sec. 2.3, eq. cp_als):
+// with KR[(j,k), b] = P_jb Q_kb for two factor matrices P and Q (column b a
+// rank component) instead of u_bj u_bk, Cout = X_(1) (P kr Q).
 #include <cudaTypedefs.h>
 
 #include "grom_internal.h"
@@ -43,7 +47,8 @@ struct K2Dev {
   int64_t n, np;
   int btile, col_tiles, i_tiles, splits, stages_a, stages_b, tmem_cols;
   int64_t bp;  // padded batch = col_tiles * btile
-  float* ub;   // bp x np FP32 copy of the states (zero padded)
+  float* pb;   // bp x np FP32 weights of the middle index j (u, or factor P^T)
+  float* qb;   // bp x np FP32 weights of the inner index k (u, or factor Q^T), zero padded
   float* part; // splits x n x bp FP32 partials
   int* err;
 };
@@ -159,13 +164,14 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     const int g = threadIdx.x - 64;  // row b of the KR tile
     const bool row_on = g < p.btile;
     const int64_t bglob = (int64_t)col_tile * p.btile + g;
-    const float* urow = p.ub + bglob * p.np;
+    const float* prow = p.pb + bglob * p.np;
+    const float* urow = p.qb + bglob * p.np;
     float uk[64];
     int64_t cur_kb = -1;
     // u_bj of the next K2_PF K-tiles, in a ring indexed by t mod K2_PF
     float ring[K2_PF];
 #pragma unroll
-    for (int q = 0; q < K2_PF; ++q) ring[q] = (row_on && q < T) ? urow[k2_j(q, nj, j0)] : 0.f;
+    for (int q = 0; q < K2_PF; ++q) ring[q] = (row_on && q < T) ? prow[k2_j(q, nj, j0)] : 0.f;
     bool stop = false;
     for (int64_t t0 = 0; t0 < T && !stop; t0 += K2_PF) {
 #pragma unroll
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
         const uint32_t ph = (uint32_t)((t / SB) & 1);
         const int64_t kb = t / nj;
         const float uj = ring[q];
-        if (row_on && t + K2_PF < T) ring[q] = urow[k2_j(t + K2_PF, nj, j0)];
+        if (row_on && t + K2_PF < T) ring[q] = prow[k2_j(t + K2_PF, nj, j0)];
         if (row_on && kb != cur_kb) {
           const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
 #pragma unroll
@@ -257,18 +263,27 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
   }
 }
 
-// ub[b][k] = u_b[k] (FP32), zero for padding rows/columns and inactive trajectories.
+// qb[b][k] = u_b[k] (FP32), zero for padding rows/columns and inactive
+// trajectories; with factors, pb[b][k] = P[k][b] and qb[b][k] = Q[k][b]
+// (P, Q row-major n x f_stride).
 __global__ void k2_prep_kernel(const K2Dev p, const double* u, int64_t u_stride, const double* hist,
-                               const int64_t* taken, int64_t hist_stride, const int32_t* active, int batch) {
+                               const int64_t* taken, int64_t hist_stride, const int32_t* active, int batch,
+                               const double* fp, const double* fq, int64_t f_stride) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.bp * p.np) return;
   const int64_t b = t / p.np, k = t - b * p.np;
+  const bool in = b < batch && k < p.n;
+  if (fq) {
+    p.qb[t] = in ? __double2float_rn(fq[k * f_stride + b]) : 0.f;
+    p.pb[t] = in ? __double2float_rn(fp[k * f_stride + b]) : 0.f;
+    return;
+  }
   float v = 0.f;
-  if (b < batch && k < p.n && (active == nullptr || active[b])) {
+  if (in && (active == nullptr || active[b])) {
     const double* ub = taken ? hist + b * hist_stride + (taken[b] % 3) * p.n : u + b * u_stride;
     v = __double2float_rn(ub[k]);
   }
-  p.ub[t] = v;
+  p.qb[t] = v;
 }
 
 // c[b][i] = sum over splits of the FP32 partials, in split order, in FP64.
@@ -338,8 +353,10 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
   return p;
 }
 
+// FP32 operand rows (two arrays, the second used for factor pairs) and the
+// split-K partials.
 size_t k2_scratch_bytes(const K2Plan& p) {
-  return 4 * ((size_t)p.bp * p.np + (size_t)p.splits * p.n * p.bp);
+  return 4 * (2 * (size_t)p.bp * p.np + (size_t)p.splits * p.n * p.bp);
 }
 
 cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
@@ -354,12 +371,13 @@ cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a,
   d.stages_b = p.stages_b;
   d.tmem_cols = p.tmem_cols;
   d.bp = p.bp;
-  d.ub = reinterpret_cast<float*>(a.scratch);
-  d.part = d.ub + p.bp * p.np;
+  d.qb = reinterpret_cast<float*>(a.scratch);
+  d.pb = a.fq ? d.qb + p.bp * p.np : d.qb;
+  d.part = d.qb + 2 * p.bp * p.np;
   d.err = a.err;
   const int64_t prep = p.bp * p.np;
   k2_prep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(d, a.u, a.u_stride, a.hist, a.taken, a.hist_stride,
-                                                                a.active, a.batch);
+                                                                a.active, a.batch, a.fp, a.fq, a.f_stride);
   cudaError_t e = cudaFuncSetAttribute(k2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   if (a.ev0) prof_record(a.ev0, s);
