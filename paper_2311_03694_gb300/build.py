@@ -35,6 +35,10 @@ SOURCES = [
     "k1p_f32x2.cu",
     "k1p_f32.cu",
     "k1p_bf16.cu",
+    "k1pp_f64.cu",
+    "k1pp_f32x2.cu",
+    "k1pp_f32.cu",
+    "k1pp_bf16.cu",
     "k2_tc.cu",
     "serve.cu",
 ]

@@ -194,7 +194,7 @@ static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
-                  r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta};
+                  r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -366,7 +366,9 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       if ((st = dmalloc(&r->k1p_dg, k1p_dg_bytes(r->k1, r->storage), &r->total_bytes))) return bail(st);
       if ((st = dmalloc(&r->k1p_tg, k1p_tg_bytes(r->k1), &r->total_bytes))) return bail(st);
       if ((st = dmalloc(&r->probe, 3 * sizeof(double), &r->total_bytes))) return bail(st);
-      if (cudaMemsetAsync(r->probe, 0, 3 * sizeof(double), r->stream) != cudaSuccess)
+      if ((st = dmalloc(&r->k1pp_scratch, k1pp_scratch_bytes(r->k1), &r->total_bytes))) return bail(st);
+      if (cudaMemsetAsync(r->probe, 0, 3 * sizeof(double), r->stream) != cudaSuccess ||
+          cudaMemsetAsync(r->k1pp_scratch, 0, k1pp_scratch_bytes(r->k1), r->stream) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "grom_create"));
     }
     if (r->storage == GROM_BF16 && !packed) {
@@ -868,6 +870,27 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
                                r->storage, t->batch, nsteps, a, r->k3p_scratch, r->sm_count, r->stream);
     if (e != cudaSuccess) return cuda_fail(e, "grom_step persistent launch");
     return GROM_OK;
+  }
+  // full G-ROM with the skew-packed tensor and a few trajectories: all steps
+  // in one persistent launch (falls back to the graphs below when the launch
+  // cannot be placed)
+  if (r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
+      !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8) {
+    StepArgs a = step_args(t, energy, invariant);
+    K1Args k = k1_args(r);
+    k.hist = t->hist;
+    k.taken = t->taken;
+    k.hist_stride = 6 * (int64_t)r->n;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
+    k.ev0 = e0;
+    k.ev1 = e1;
+    const cudaError_t e = k1pp_launch(r->k1, r->storage, k, a, t->batch, nsteps, r->k1pp_scratch, r->stream);
+    if (e == cudaSuccess) return GROM_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorInvalidValue)
+      return cuda_fail(e, "grom_step persistent launch");
+    cudaGetLastError();
+    if (e0) --r->prof_used;  // the timing pair was not recorded
   }
   constexpr int G = 8;  // steps per captured graph
   int done = 0;

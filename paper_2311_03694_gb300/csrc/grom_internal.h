@@ -203,6 +203,13 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
                                 int nbk, cudaStream_t s);
 cudaError_t step_diag_packed_launch(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a, int b0,
                                     int nb, int nbk, cudaStream_t s);
+// Persistent skew-packed stepper (k1p_persist.cuh): nsteps diagonal steps of
+// up to 4 trajectories in one cooperative launch.  scratch: k1pp_scratch_bytes,
+// zeroed once at creation.  Returns an error without launching when the plan
+// or the device does not allow it (the caller then takes the regular path).
+size_t k1pp_scratch_bytes(const K1Plan& p);
+cudaError_t k1pp_launch(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch, int nsteps,
+                        void* scratch, cudaStream_t s);
 cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& a, const StepArgs& st, int batch,
                                  int step_index, cudaStream_t s);
 cudaError_t selftest_wait_launch(int* err, uint64_t limit_ns, cudaStream_t s);
@@ -261,6 +268,7 @@ struct grom_rom {
   double* part = nullptr;       // streaming / CP partials
   size_t part_bytes = 0;
   int* err = nullptr;           // device flags [0] = mask, [1] = first bad
+  void* k1pp_scratch = nullptr; // packed layout: persistent stepper barrier and partials
   void* k1p_dg = nullptr;       // packed layout: segment values D u_i
   double* k1p_tg = nullptr;     // packed layout: transposed-term windows
   double* probe = nullptr;      // packed layout: skew probe accumulators (3)

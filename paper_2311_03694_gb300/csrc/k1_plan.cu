@@ -1,5 +1,6 @@
 // K1 launch planning: chunking, persistent grid, trajectories per pass.
 #include "k1_stream.cuh"
+#include "k1p_persist.cuh"
 
 namespace grom {
 
@@ -11,6 +12,10 @@ cudaError_t k1p_dispatch_f64(int qm, int nb, const K1Plan&, const K1Args&, int, 
 cudaError_t k1p_dispatch_f32x2(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
 cudaError_t k1p_dispatch_f32(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
 cudaError_t k1p_dispatch_bf16(int qm, int nb, const K1Plan&, const K1Args&, int, cudaStream_t);
+cudaError_t k1pp_dispatch_f64(int, int, const K1Plan&, const K1Args&, const StepArgs&, const K1PPArgs&, cudaStream_t);
+cudaError_t k1pp_dispatch_f32x2(int, int, const K1Plan&, const K1Args&, const StepArgs&, const K1PPArgs&, cudaStream_t);
+cudaError_t k1pp_dispatch_f32(int, int, const K1Plan&, const K1Args&, const StepArgs&, const K1PPArgs&, cudaStream_t);
+cudaError_t k1pp_dispatch_bf16(int, int, const K1Plan&, const K1Args&, const StepArgs&, const K1PPArgs&, cudaStream_t);
 
 static int pow2_ceil(int64_t x) {
   int p = 1;
@@ -162,6 +167,35 @@ cudaError_t k1_launch_fused_step(const K1Plan& plan, int storage, const K1Args& 
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace grom
+
+namespace grom {
+
+size_t k1pp_scratch_bytes(const K1Plan& p) { return 256 + (size_t)p.grid * 4 * 2 * sizeof(double); }
+
+cudaError_t k1pp_launch(const K1Plan& plan, int storage, const K1Args& a0, const StepArgs& st, int batch, int nsteps,
+                        void* scratch, cudaStream_t s) {
+  if (!plan.packed || plan.has_mid || batch < 1 || batch > 4 || batch > plan.nb_max || nsteps < 1)
+    return cudaErrorInvalidValue;
+  K1Args a = a0;
+  a.nb = batch;
+  a.skip_finalize = 1;
+  const int nb = pow2_ceil(batch);
+  K1Plan pl = plan;
+  pl.smem = (size_t)(K1_SMEM_BASE + nb * k1_traj_smem(pl, storage));
+  K1PPArgs pp{};
+  pp.bar = reinterpret_cast<unsigned int*>(scratch);
+  pp.red = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(scratch) + 256);
+  pp.nsteps = nsteps;
+  switch (storage) {
+    case GROM_F64: return k1pp_dispatch_f64(pl.qm, nb, pl, a, st, pp, s);
+    case GROM_F32X2: return k1pp_dispatch_f32x2(pl.qm, nb, pl, a, st, pp, s);
+    case GROM_F32: return k1pp_dispatch_f32(pl.qm, nb, pl, a, st, pp, s);
+    case GROM_BF16: return k1pp_dispatch_bf16(pl.qm, nb, pl, a, st, pp, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace grom
