@@ -298,9 +298,13 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
         if (cur_i >= 0) flush(cur_i);
         cur_i = i;
       }
-      if (!ptx::mbar_wait(&full[s], ph, abort_flag)) {
-        *abort_flag = 1;
-        atomicOr(a.err, DEV_ERR_TIMEOUT);
+      // warp-uniform: a lane whose wait timed out takes its whole warp along
+      // (the flush shuffles need every lane)
+      if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[s], ph, abort_flag))) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(a.err, DEV_ERR_TIMEOUT);
+        }
         break;
       }
       const uint8_t* st = stages + s * K1_STAGE_BYTES + t_off;
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
         }
       }
     }
-    if (cur_i >= 0 && !*abort_flag) flush(cur_i);
+    if (cur_i >= 0 && !__any_sync(0xffffffffu, *abort_flag != 0)) flush(cur_i);
   }
   __syncthreads();
 }

@@ -192,8 +192,9 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
           }
           cur_kb = kb;
         }
-        if (t >= SB && !ptx::mbar_wait(&empty_b[r], ph ^ 1u, abort_flag)) {
-          k2_abort(abort_flag, p.err);
+        // warp-uniform (the warp stores and arrives together)
+        if (t >= SB && !__all_sync(0xffffffffu, ptx::mbar_wait(&empty_b[r], ph ^ 1u, abort_flag))) {
+          if (lane == 0) k2_abort(abort_flag, p.err);
           stop = true;
           break;
         }
@@ -224,11 +225,12 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     }
     // -------------------------------------------------------------- epilogue
     if (warp >= 2 && warp < 6) {
-      const bool ok = ptx::mbar_wait(accum, 0, nullptr);
-      if (!ok) atomicOr(p.err, DEV_ERR_TIMEOUT);
+      // warp-uniform: the tensor-memory loads below are collective
+      const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(accum, 0, nullptr));
+      if (!ok && lane == 0) atomicOr(p.err, DEV_ERR_TIMEOUT);
       tc::fence_after_sync();
       const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are readable by this warp
-      if (ok && !*abort_flag) {
+      if (ok && !__any_sync(0xffffffffu, *abort_flag != 0)) {
         for (int m = 0; m < K2_MT; ++m) {
           const int64_t i = (int64_t)i_pair * 256 + m * 128 + 32 * q + lane;
           for (int c0 = 0; c0 < p.btile; c0 += 32) {
