@@ -131,7 +131,11 @@ typedef struct grom_desc {
   int32_t order; /* BDF/EXT order k in 1..3; steps 1 and 2 use orders 1 and 2       */
   int32_t defer_tensor; /* FULL only: 1 = rows come from grom_upload_tensor_slab  */
   int32_t max_batch;    /* largest batch passed to grom_nonlinear/grom_traj_create
-                           (sizes the library's scratch); 0 means 1              */
+                           (sizes the library's scratch); 0 means 1.  FULL, BF16,
+                           dense layout, max_batch > 8: the library also keeps a
+                           tile-major copy of the tensor (another n^3 * 2 bytes)
+                           for the tensor-core kernel; if that allocation fails
+                           the kernel reads the row-major tensor instead      */
   int32_t layout;       /* FULL and SVD: GROM_LAYOUT_DENSE (0) or GROM_LAYOUT_SKEW_PACKED */
   /* 1: the operator includes the zeroth mode phi_0 (coefficient 1 in the
    * augmented vector ubar = (1, u), eq. nse_ode; the "full" tensor of

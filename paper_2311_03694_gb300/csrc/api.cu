@@ -190,11 +190,32 @@ static grom_status check_skew_probe(grom_rom* r) {
   return GROM_OK;
 }
 
+// Tile-major copy of a dense BF16 tensor for the tensor-core kernel (built
+// once, outside any stream capture).
+static grom_status build_k2_tiles(grom_rom* r) {
+  if (r->k2_tiles || !r->k2_ok || r->rows_uploaded != r->n) return GROM_OK;
+  // the copy only speeds K2 up: without room for it K2 reads the row-major tensor
+  grom_status st = dmalloc(&r->k2_tiles, k2_tiles_bytes(r->n), &r->total_bytes);
+  if (st) return st == GROM_ERR_OOM ? GROM_OK : st;
+  cudaError_t e = k2_build_tiles(r->op, r->n, r->k2_tiles, r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  if (e != cudaSuccess || !k2_make_tmap_tiled(&r->k2_tmap_tiled, r->k2_tiles, r->n)) {
+    cudaGetLastError();
+    cudaFree(r->k2_tiles);
+    r->total_bytes -= k2_tiles_bytes(r->n);
+    r->k2_tiles = nullptr;
+    return e != cudaSuccess ? cuda_fail(e, "tile-major copy") : GROM_OK;
+  }
+  ++r->version;  // captured graphs hold the other tensor map
+  return GROM_OK;
+}
+
 static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
-                  r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch};
+                  r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch,
+                  r->k2_tiles};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
@@ -396,6 +417,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
         return bail(st);
       }
       r->rows_uploaded = n;
+      if (r->max_batch > 8 && (st = build_k2_tiles(r))) return bail(st);
     } else {
       r->row_seen = new (std::nothrow) uint8_t[(size_t)n]();
       if (!r->row_seen) return bail(fail(GROM_ERR_OOM, "grom_create: host allocation"));
@@ -598,6 +620,7 @@ grom_status grom_upload_tensor_slab(grom_rom* r, int32_t i0, int32_t i1, const d
     r->rows_uploaded = n - 1;  // the ROM stays unusable
     return st;
   }
+  if (r->rows_uploaded == n && r->max_batch > 8 && (st = build_k2_tiles(r))) return st;
   return GROM_OK;
 }
 
@@ -645,7 +668,8 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.scratch = r->k2_scratch;
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
-    e = k2_launch(k2_plan(r->n, batch, r->sm_count), &r->k2_tmap, a, r->stream);
+    a.tiled = r->k2_tiles != nullptr;
+    e = k2_launch(k2_plan(r->n, batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, r->stream);
   } else if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.u = u;
@@ -754,7 +778,8 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.scratch = r->k2_scratch;
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
-    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), &r->k2_tmap, a, strm);
+    a.tiled = r->k2_tiles != nullptr;
+    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, strm);
   }
   if (!is_cp(r)) {
     K1Args a = k1_args(r);
@@ -1059,6 +1084,10 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
     return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
   if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
     return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form, dense layout");
+  if (kernel == GROM_KERNEL_TENSOR) {
+    grom_status st = build_k2_tiles(r);
+    if (st) return st;
+  }
   r->kernel_choice = kernel;
   ++r->version;
   return GROM_OK;

@@ -97,10 +97,16 @@ struct K2Args {
   const double* fp;
   const double* fq;
   int64_t f_stride;
+  int tiled;  // 1: the tensor map covers the tile-major copy (k2_build_tiles)
 };
 K2Plan k2_plan(int64_t n, int batch, int sm_count);
 size_t k2_scratch_bytes(const K2Plan& p);
 bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np);
+// Tile-major BF16 copy of the stored tensor for K2 (every 256 x 64 tile of
+// C_(1) contiguous) and its tensor map.
+size_t k2_tiles_bytes(int64_t n);
+cudaError_t k2_build_tiles(const void* rows, int64_t n, void* tiles, cudaStream_t s);
+bool k2_make_tmap_tiled(CUtensorMap* m, const void* tiles, int64_t n);
 cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s);
 
 // ------------------------------------------------------------- K3 (CP)
@@ -283,6 +289,8 @@ struct grom_rom {
   int version = 0;                   // bumped when cached launch graphs become stale
   bool k2_ok = false;                // tensor map built (BF16 full form)
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
+  void* k2_tiles = nullptr;          // tile-major copy for K2 (nullable)
+  CUtensorMap k2_tmap_tiled;         // its TMA descriptor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
   void* k3p_scratch = nullptr;       // persistent CP stepper: partials, h, barrier

@@ -15,7 +15,11 @@
 // the split the Khatri-Rao operand is exact to ~2^-17.
 //
 // CTA (10 warps): warp 0 issues TMA loads of 256 x 64 BF16 tiles of C (two
-// 128-row halves); warp 1 owns the tensor memory and issues tcgen05.mma
+// 128-row halves), either from the row layout of the stored tensor (rows
+// (i, j) of np values: a tile is 256 segments of 128 bytes, n*np*2 bytes
+// apart) or, when the ROM keeps one, from a tile-major copy in which every
+// 256 x 64 tile is one contiguous 32 KB block (full DRAM bursts, which the
+// small-batch, bandwidth-bound regime needs); warp 1 owns the tensor memory and issues tcgen05.mma
 // (M=128, N=btile, K=16) into two FP32 accumulators in TMEM, one per half,
 // both fed by the same KR tile, which halves KR generation per flop; warps 2-9
 // generate the KR tiles (one row b each, u_bj prefetched eight tiles ahead)
@@ -47,6 +51,7 @@ struct K2Dev {
   int64_t n, np;
   int btile, col_tiles, i_tiles, splits, stages_a, stages_b, tmem_cols;
   int64_t bp;  // padded batch = col_tiles * btile
+  int tiled;   // 1: the tensor map covers the tile-major copy
   float* pb;   // bp x np FP32 weights of the middle index j (u, or factor P^T)
   float* qb;   // bp x np FP32 weights of the inner index k (u, or factor Q^T), zero padded
   float* part; // splits x n x bp FP32 partials
@@ -61,7 +66,14 @@ __device__ __forceinline__ void k2_abort(volatile int* abort_flag, int* err) {
 // K-tile t of a CTA: advected block kb = t / nj (outer), advecting index j0 + t % nj (inner).
 __device__ __forceinline__ int64_t k2_j(int64_t t, int64_t nj, int64_t j0) { return j0 + t % nj; }
 
+// TPR generator threads share a Khatri-Rao row (each writes 8 / TPR of its
+// eight 16-byte swizzle chunks), so narrow column tiles still keep all eight
+// generator warps busy: TPR = min(8, 256 / btile).
+template <int TPR>
 __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_constant__ CUtensorMap tmap, const K2Dev p) {
+  // btile <= 128 (TPR >= 2): one MMA of N = 2 btile multiplies the hi and lo
+  // KR tiles together
+  constexpr bool MERGED = TPR > 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int SA = p.stages_a, SB = p.stages_b;
@@ -124,7 +136,11 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
         }
         const int64_t kb = t / nj, j = j0 + (t - kb * nj);
         ptx::mbar_arrive_expect_tx(&full_a[s], K2_A_BYTES);
-        tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, (int32_t)(j * p.np + kb * 64), i_pair * 256, &full_a[s]);
+        if (p.tiled)
+          tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, 0,
+                          (int32_t)((((int64_t)i_pair * p.n + j) * kblocks + kb) * 256), &full_a[s]);
+        else
+          tc::tma_load_2d(sa + (size_t)s * K2_A_BYTES, &tmap, (int32_t)(j * p.np + kb * 64), i_pair * 256, &full_a[s]);
       }
       for (int64_t q = t > SA ? t - SA : 0; q < t; ++q)
         if (!ptx::mbar_wait(&full_a[q % SA], (uint32_t)((q / SA) & 1), nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
@@ -132,8 +148,11 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(128, p.btile);
-      const uint32_t acc1 = tmem + (uint32_t)p.btile;  // second accumulator: columns btile..2 btile-1
+      // merged: the hi and lo KR tiles are adjacent in shared memory, so one
+      // MMA of N = 2 btile covers both (half the instructions); the
+      // accumulator of each 128-row half holds A hi^T | A lo^T side by side
+      const uint32_t idesc = tc::idesc_bf16_f32(128, MERGED ? 2 * p.btile : p.btile);
+      const uint32_t acc1 = tmem + (uint32_t)(MERGED ? 2 * p.btile : p.btile);
       for (int64_t t = 0; t < T; ++t) {
         const int s = (int)(t % SA), r = (int)(t % SB);
         if (!ptx::mbar_wait(&full_a[s], (uint32_t)((t / SA) & 1), abort_flag) ||
@@ -149,6 +168,11 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
 #pragma unroll
         for (int k = 0; k < 4; ++k) {  // 4 x K=16 inside the 128-byte swizzle span
           const uint32_t first = (t > 0 || k > 0) ? 1u : 0u;
+          if constexpr (MERGED) {
+            tc::mma_bf16(tmem, a0 + 2 * k, bh + 2 * k, idesc, first);
+            tc::mma_bf16(acc1, a1 + 2 * k, bh + 2 * k, idesc, first);
+            continue;
+          }
           tc::mma_bf16(tmem, a0 + 2 * k, bh + 2 * k, idesc, first);
           tc::mma_bf16(tmem, a0 + 2 * k, bl + 2 * k, idesc, 1u);
           tc::mma_bf16(acc1, a1 + 2 * k, bh + 2 * k, idesc, first);
@@ -161,12 +185,15 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
     }
   } else {
     // ------------------------------------------------ KR generators (8 warps)
-    const int g = threadIdx.x - 64;  // row b of the KR tile
+    constexpr int CPT = 8 / TPR;          // 16-byte chunks (8 columns each) per thread
+    const int gt = threadIdx.x - 64;
+    const int g = gt / TPR;               // row b of the KR tile
+    const int part = gt - g * TPR;        // this thread's chunks: part*CPT .. part*CPT + CPT-1
     const bool row_on = g < p.btile;
-    const int64_t bglob = (int64_t)col_tile * p.btile + g;
+    const int64_t bglob = (int64_t)col_tile * p.btile + (row_on ? g : 0);
     const float* prow = p.pb + bglob * p.np;
-    const float* urow = p.qb + bglob * p.np;
-    float uk[64];
+    const float* urow = p.qb + bglob * p.np + part * CPT * 8;
+    float uk[8 * CPT];
     int64_t cur_kb = -1;
     // u_bj of the next K2_PF K-tiles, in a ring indexed by t mod K2_PF
     float ring[K2_PF];
@@ -186,7 +213,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
         if (row_on && kb != cur_kb) {
           const float4* src = reinterpret_cast<const float4*>(urow + kb * 64);
 #pragma unroll
-          for (int v = 0; v < 16; ++v) {
+          for (int v = 0; v < 2 * CPT; ++v) {
             const float4 x = src[v];
             uk[4 * v] = x.x; uk[4 * v + 1] = x.y; uk[4 * v + 2] = x.z; uk[4 * v + 3] = x.w;
           }
@@ -202,11 +229,12 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
           uint8_t* row_hi = sb + (size_t)r * b_bytes + (size_t)g * 128;
           uint8_t* row_lo = row_hi + half_bytes;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int cc = 0; cc < CPT; ++cc) {
+            const int c = part * CPT + cc;  // chunk of the row
             uint32_t wh[4], wl[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const float p0 = uk[8 * c + 2 * h] * uj, p1 = uk[8 * c + 2 * h + 1] * uj;
+              const float p0 = uk[8 * cc + 2 * h] * uj, p1 = uk[8 * cc + 2 * h + 1] * uj;
               const __nv_bfloat162 hi = __floats2bfloat162_rn(p0, p1);
               const float2 hf = __bfloat1622float2(hi);
               const __nv_bfloat162 lo = __floats2bfloat162_rn(p0 - hf.x, p1 - hf.y);
@@ -235,8 +263,26 @@ __global__ void __launch_bounds__(K2_THREADS, 1) k2_tc_kernel(const __grid_const
           const int64_t i = (int64_t)i_pair * 256 + m * 128 + 32 * q + lane;
           for (int c0 = 0; c0 < p.btile; c0 += 32) {
             uint32_t rr[32];
-            tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * p.btile + c0), rr);
-            tc::tmem_ld_wait();
+            const uint32_t lanes = (uint32_t)(32 * q) << 16;
+            if constexpr (!MERGED) {
+              tc::tmem_ld_32x32b_x32(tmem + lanes + (uint32_t)(m * p.btile + c0), rr);
+              tc::tmem_ld_wait();
+            } else if (p.btile >= 32) {
+              // hi part + lo part of columns c0 .. c0+31
+              uint32_t rl[32];
+              const uint32_t base = tmem + lanes + (uint32_t)(m * 2 * p.btile);
+              tc::tmem_ld_32x32b_x32(base + (uint32_t)c0, rr);
+              tc::tmem_ld_32x32b_x32(base + (uint32_t)(p.btile + c0), rl);
+              tc::tmem_ld_wait();
+#pragma unroll
+              for (int v = 0; v < 32; ++v) rr[v] = __float_as_uint(__uint_as_float(rr[v]) + __uint_as_float(rl[v]));
+            } else {
+              // btile = 16: one load holds the hi (0..15) and lo (16..31) columns
+              tc::tmem_ld_32x32b_x32(tmem + lanes + (uint32_t)(m * 2 * p.btile), rr);
+              tc::tmem_ld_wait();
+#pragma unroll
+              for (int v = 0; v < 16; ++v) rr[v] = __float_as_uint(__uint_as_float(rr[v]) + __uint_as_float(rr[16 + v]));
+            }
             if (i < p.n) {
               float* dst = p.part + ((int64_t)split * p.n + i) * p.bp + (int64_t)col_tile * p.btile + c0;
               const int mm = p.btile - c0 < 32 ? p.btile - c0 : 32;
@@ -314,6 +360,53 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// Tile-major copy: tile t = (i_pair * n + j) * (np / 64) + kb holds rows
+// i_pair*256 .. +255 of columns j*np + kb*64 .. +63 of C_(1), 256 rows of 128
+// bytes, contiguous (rows past n are zero).
+__global__ void k_k2_tiles(const __nv_bfloat16* __restrict__ rows, int64_t n, int64_t np, int64_t tiles,
+                           __nv_bfloat16* __restrict__ out) {
+  const int64_t total = tiles * 256 * 8;  // 16-byte vectors
+  const int64_t kblocks = np / 64;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = v / (256 * 8), r = (v / 8) % 256, c = v % 8;
+    const int64_t kb = t % kblocks, j = (t / kblocks) % n, ip = t / (kblocks * n);
+    const int64_t i = ip * 256 + r;
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (i < n) x = *reinterpret_cast<const uint4*>(rows + (i * n + j) * np + kb * 64 + c * 8);
+    *reinterpret_cast<uint4*>(out + (t * 256 + r) * 64 + c * 8) = x;
+  }
+}
+
+size_t k2_tiles_bytes(int64_t n) {
+  const int64_t np = padded_n(n), i_tiles = (n + 255) / 256;
+  return (size_t)(i_tiles * n * (np / 64)) * 256 * 64 * sizeof(__nv_bfloat16);
+}
+
+cudaError_t k2_build_tiles(const void* rows, int64_t n, void* tiles, cudaStream_t s) {
+  const int64_t np = padded_n(n), i_tiles = (n + 255) / 256;
+  const int64_t nt = i_tiles * n * (np / 64);
+  const int64_t total = nt * 256 * 8;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  k_k2_tiles<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16*>(rows), n, np, nt,
+                                               reinterpret_cast<__nv_bfloat16*>(tiles));
+  return cudaGetLastError();
+}
+
+bool k2_make_tmap_tiled(CUtensorMap* m, const void* tiles, int64_t n) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int64_t np = padded_n(n), i_tiles = (n + 255) / 256;
+  cuuint64_t dims[2] = {64, (cuuint64_t)(i_tiles * n * (np / 64) * 256)};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {64, 256};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(tiles), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -348,7 +441,8 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
   if (sa < 2) sa = 2;
   p.stages_a = sa;
   int cols = 32;
-  while (cols < 2 * btile) cols <<= 1;  // two accumulators
+  const int acc_cols = btile <= 128 ? 4 * btile : 2 * btile;  // two accumulators (hi|lo side by side when merged)
+  while (cols < acc_cols) cols <<= 1;
   p.tmem_cols = cols;
   p.smem = 1024 + (size_t)sa * K2_A_BYTES + (size_t)p.stages_b * b_bytes + (size_t)(2 * sa + 2 * p.stages_b + 1) * 8 + 16;
   p.bp = (int64_t)p.col_tiles * btile;
@@ -363,6 +457,7 @@ size_t k2_scratch_bytes(const K2Plan& p) {
 
 cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
   K2Dev d{};
+  d.tiled = a.tiled;
   d.n = p.n;
   d.np = p.np;
   d.btile = p.btile;
@@ -380,10 +475,13 @@ cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a,
   const int64_t prep = p.bp * p.np;
   k2_prep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(d, a.u, a.u_stride, a.hist, a.taken, a.hist_stride,
                                                                 a.active, a.batch, a.fp, a.fq, a.f_stride);
-  cudaError_t e = cudaFuncSetAttribute(k2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  int tpr = 1;  // largest power of two <= 256 / btile, at most 8
+  while (tpr < 8 && 2 * tpr * p.btile <= 256) tpr *= 2;
+  auto kern = tpr == 8 ? k2_tc_kernel<8> : tpr == 4 ? k2_tc_kernel<4> : tpr == 2 ? k2_tc_kernel<2> : k2_tc_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   if (a.ev0) prof_record(a.ev0, s);
-  k2_tc_kernel<<<(unsigned)(p.i_tiles * p.col_tiles * p.splits), K2_THREADS, p.smem, s>>>(*tmap, d);
+  kern<<<(unsigned)(p.i_tiles * p.col_tiles * p.splits), K2_THREADS, p.smem, s>>>(*tmap, d);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.ev1) prof_record(a.ev1, s);
