@@ -678,6 +678,40 @@ def main():
             batched["B%d" % B] = entry
             btr.close()
             brom.close()
+            # the same batch on the skew-packed tensor: the factored K2P kernel
+            prom = grom.Rom(n, "full", "bf16", tensor=C, stiffness=a, nu=NU, dt=DT, max_batch=B,
+                            layout="skew_packed")
+            ptr = grom.Trajectories(prom, U0)
+            ptr.step(2)
+            torch.cuda.synchronize()
+            prom.profile(True)
+            e0b.record(stream)
+            ptr.step(bsteps)
+            e1b.record(stream)
+            torch.cuda.synchronize()
+            kms, kl = prom.profile_read()
+            prom.profile(False)
+            pms = e0b.elapsed_time(e1b) / bsteps
+            kavg = kms / max(1, kl)
+            pbytes = float(n) * n * _packed_len(n) * 2
+            pentry = {"ms_per_step": pms, "trajectory_steps_per_s": B * 1e3 / pms,
+                      "kernel": "k2p_tc_kernel (tcgen05, factored, skew-packed)" if B > 8 else "k1_packed_kernel",
+                      "kernel_ms": kavg, "alg_tflops": flops / (kavg * 1e-3) / 1e12,
+                      "issued_tflops": 2.0 * n * n * _packed_len(n) * B * 2 / (kavg * 1e-3) / 1e12,
+                      "stored_tensor_bytes": pbytes,
+                      "hbm_frac_per_tensor_read": pbytes / (kavg * 1e-3) / 1e9 / hbm_peak}
+            if rank_id == 0:
+                uf = torch.from_numpy(U0.copy()).cuda()
+                cf = torch.empty_like(uf)
+                prom.nonlinear(uf, cf)
+                torch.cuda.synchronize()
+                errs = [rel(cf[b].cpu().numpy(), oracle.nonlinear_full(Ch, U0[b])) for b in range(min(3, B))]
+                pentry["eval_rel_err_vs_fp64_oracle_max3"] = max(errs)
+            code_p, _ = ptr.status()
+            pentry["status"] = grom.ERRORS.get(code_p, "OK") if code_p else "OK"
+            batched["B%d_packed" % B] = pentry
+            ptr.close()
+            prom.close()
             # the CPD-ROM (skew CP factors, rank N) on the same batch
             for storage in ("bf16", "f64"):
                 crom = grom.Rom(n, "cp_skew", storage, factors=factors, stiffness=a, nu=NU, dt=DT, max_batch=B)

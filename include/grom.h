@@ -220,8 +220,12 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * the streaming kernel. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass   */
-#define GROM_KERNEL_TENSOR 2 /* K2: tcgen05 GEMM over the Khatri-Rao product of the states
-                                (BF16 storage only)                                          */
+#define GROM_KERNEL_TENSOR 2 /* BF16 storage only.  Dense layout, K2: tcgen05 GEMM over the
+                                Khatri-Rao product of the states (Sec. 2.2, eq. Cu with the
+                                mode-1 matricisation).  Skew-packed layout, K2P: the factored
+                                form, one tcgen05 GEMM D_i = P_i^T U^T per test index i over
+                                the stored half, then c_i += D_i u_k and c_k -= D_i u_i for
+                                every stored pair (i, k); half the bytes and MMA work of K2  */
 grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
 
 /* ------------------------------------------------------------ serving

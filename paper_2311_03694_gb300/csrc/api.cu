@@ -193,7 +193,7 @@ static grom_status check_skew_probe(grom_rom* r) {
 // Tile-major copy of a dense BF16 tensor for the tensor-core kernel (built
 // once, outside any stream capture).
 static grom_status build_k2_tiles(grom_rom* r) {
-  if (r->k2_tiles || !r->k2_ok || r->rows_uploaded != r->n) return GROM_OK;
+  if (r->k2_tiles || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE || r->rows_uploaded != r->n) return GROM_OK;
   // the copy only speeds K2 up: without room for it K2 reads the row-major tensor
   grom_status st = dmalloc(&r->k2_tiles, k2_tiles_bytes(r->n), &r->total_bytes);
   if (st) return st == GROM_ERR_OOM ? GROM_OK : st;
@@ -247,6 +247,15 @@ static bool prof_pair(grom_rom* r, cudaEvent_t* e0, cudaEvent_t* e1) {
 
 static bool use_k2(const grom_rom* r, int batch) {
   if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE) return false;
+  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
+  if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
+  return batch > 8;
+}
+
+// K2P: the factored tensor-core kernel of the skew-packed layout
+static bool use_k2p(const grom_rom* r, int batch) {
+  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_SKEW_PACKED)
+    return false;
   if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
   if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
   return batch > 8;
@@ -391,6 +400,20 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       if (cudaMemsetAsync(r->probe, 0, 3 * sizeof(double), r->stream) != cudaSuccess ||
           cudaMemsetAsync(r->k1pp_scratch, 0, k1pp_scratch_bytes(r->k1), r->stream) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    }
+    if (r->storage == GROM_BF16 && packed) {
+      r->k2_ok = k2p_make_tmap(&r->k2_tmap, r->op, n, r->k1.lp);
+      if (r->k2_ok) {
+        // scratch for the largest plan over the batch sizes this ROM accepts
+        size_t need = 0;
+        for (int b = 16;; b = b < 128 ? b + 16 : b + 128) {
+          const int bb = b < r->max_batch ? b : r->max_batch;
+          need = std::max(need, k2p_scratch_bytes(k2p_plan(n, r->k1.lp, bb, r->sm_count)));
+          if (bb >= r->max_batch) break;
+        }
+        r->k2_scratch_bytes = need;
+        if ((st = dmalloc(&r->k2_scratch, need, &r->total_bytes))) return bail(st);
+      }
     }
     if (r->storage == GROM_BF16 && !packed) {
       r->k2_ok = k2_make_tmap(&r->k2_tmap, r->op, n, r->np);
@@ -670,6 +693,17 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
     a.tiled = r->k2_tiles != nullptr;
     e = k2_launch(k2_plan(r->n, batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, r->stream);
+  } else if (use_k2p(r, batch)) {
+    K2Args a{};
+    a.u = u;
+    a.u_stride = r->n;
+    a.c = c;
+    a.c_stride = r->n;
+    a.batch = batch;
+    a.scratch = r->k2_scratch;
+    a.err = r->err;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
+    e = k2p_launch(k2p_plan(r->n, r->k1.lp, batch, r->sm_count), &r->k2_tmap, a, r->stream);
   } else if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.u = u;
@@ -781,6 +815,18 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.tiled = r->k2_tiles != nullptr;
     return k2_launch(k2_plan(r->n, t->batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, strm);
   }
+  if (use_k2p(r, t->batch)) {
+    K2Args a{};
+    a.hist = t->hist;
+    a.taken = t->taken;
+    a.hist_stride = 6 * (int64_t)r->n;
+    a.active = t->active;
+    a.batch = t->batch;
+    a.scratch = r->k2_scratch;
+    a.err = r->err;
+    if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
+    return k2p_launch(k2p_plan(r->n, r->k1.lp, t->batch, r->sm_count), &r->k2_tmap, a, strm);
+  }
   if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.hist = t->hist;
@@ -846,7 +892,7 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
 static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double* invariant, cudaStream_t strm) {
   grom_rom* r = t->rom;
   StepArgs a = step_args(t, energy, invariant);
-  const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch);
+  const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch) && !use_k2p(r, t->batch);
   const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
@@ -900,7 +946,7 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   // in one persistent launch (falls back to the graphs below when the launch
   // cannot be placed)
   if (r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
-      !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8) {
+      !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8 && !use_k2p(r, t->batch)) {
     StepArgs a = step_args(t, energy, invariant);
     K1Args k = k1_args(r);
     k.hist = t->hist;
@@ -1083,7 +1129,7 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   if (kernel < GROM_KERNEL_AUTO || kernel > GROM_KERNEL_TENSOR)
     return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
   if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
-    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernel needs the BF16 full form, dense layout");
+    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernels need the BF16 full form");
   if (kernel == GROM_KERNEL_TENSOR) {
     grom_status st = build_k2_tiles(r);
     if (st) return st;

@@ -109,6 +109,29 @@ cudaError_t k2_build_tiles(const void* rows, int64_t n, void* tiles, cudaStream_
 bool k2_make_tmap_tiled(CUtensorMap* m, const void* tiles, int64_t n);
 cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s);
 
+// ------------------- K2P (tensor cores, BF16, skew-packed layout, factored)
+struct K2PPlan {
+  int64_t n, np, lp;
+  int btile;       // trajectories per column tile (multiple of 16, <= 128)
+  int col_tiles;   // column tiles
+  int pblks;       // 128-position blocks of a stored row
+  int m;           // test indices per CTA tile
+  int ranges;      // ceil(n / m)
+  int tiles;       // ranges * pblks * col_tiles
+  int stages;      // pipeline depth (C tile + U hi/lo tiles)
+  int tmem_cols;   // two accumulators of btile columns
+  int wrows;       // rows of the mirrored-entry window (m + 127)
+  int wpitch;      // its pitch in floats (btile + 1)
+  int grid;        // persistent CTAs
+  int64_t bp;      // padded batch
+  size_t smem;
+};
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count);
+size_t k2p_scratch_bytes(const K2PPlan& p);
+bool k2p_make_tmap(CUtensorMap* m, const void* packed, int64_t n, int64_t lp);
+// Same arguments as K2 (fp/fq and tiled unused).
+cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s);
+
 // ------------------------------------------------------------- K3 (CP)
 constexpr int K3_THREADS = 256;
 struct K3Plan {
@@ -287,7 +310,7 @@ struct grom_rom {
   int traj_count = 0;
   int kernel_choice = 0;             // GROM_KERNEL_* override
   int version = 0;                   // bumped when cached launch graphs become stale
-  bool k2_ok = false;                // tensor map built (BF16 full form)
+  bool k2_ok = false;                // tensor map built (BF16 full form; K2P's map for the packed layout)
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_tiles = nullptr;          // tile-major copy for K2 (nullable)
   CUtensorMap k2_tmap_tiled;         // its TMA descriptor

@@ -341,8 +341,19 @@ __global__ void k2_reduce_kernel(const K2Dev p, double* c, int64_t c_stride, dou
   if (t >= (int64_t)batch * p.n) return;
   const int64_t i = t / batch, b = t - i * batch;  // consecutive threads: consecutive b (coalesced reads)
   if (active && !active[b]) return;
+  // loads issued eight at a time, added in split order
+  const float* src = p.part + i * p.bp + b;
+  const int64_t stride = p.n * p.bp;
   double s = 0.0;
-  for (int q = 0; q < p.splits; ++q) s += (double)p.part[((int64_t)q * p.n + i) * p.bp + b];
+  int q = 0;
+  for (; q + 8 <= p.splits; q += 8) {
+    float v[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) v[x] = src[(q + x) * stride];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) s += (double)v[x];
+  }
+  for (; q < p.splits; ++q) s += (double)src[q * stride];
   double* dst = taken ? hist + b * hist_stride + (3 + taken[b] % 3) * p.n : c + b * c_stride;
   dst[i] = s;
 }

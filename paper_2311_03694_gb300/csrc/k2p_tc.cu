@@ -1,0 +1,489 @@
+// K2P: batched contraction on the tcgen05 tensor cores for the skew-packed
+// BF16 layout (the factored form of the batched contraction).
+//
+// The skew-packed layout keeps one entry of each pair C_ijk = -C_kji: row
+// (i, j) holds P[i][j][p] = C[i][j][(i+1+p) mod n] for p < h (Sec. 2.2,
+// skew-symmetry of the advection tensor).  For B states the contraction is
+// factored through
+//   D_i[p, b] = sum_j P[i][j][p] u_bj                       (one GEMM per i)
+// after which every stored entry feeds both halves of its pair:
+//   c_ib     += D_i[p, b] u_b,k      k = (i+1+p) mod n       (direct entry)
+//   c_kb     -= D_i[p, b] u_bi                               (mirrored entry)
+// The GEMM is M = packed position p (128 per tile), N = trajectories, K = j.
+// The stored rows have p contiguous, so A is read MN-major straight from the
+// stored tensor (two 64-position TMA boxes per K step); B is U^T split into
+// BF16 hi and lo parts, side by side in shared memory, so one MMA of
+// N = 2 btile multiplies both (the states exact to ~2^-17); the epilogue adds
+// the hi and lo halves of the accumulator.
+// Both halves of a pair use the same FP32 D and the same FP32 state, so
+// u^T c(u) vanishes up to FP32 rounding of the sums.  Against the dense K2
+// this reads half the tensor bytes and issues half the MMA work, and needs no
+// Khatri-Rao generation.
+//
+// A CTA tile is (m consecutive test indices i, one 128-position block, one
+// column tile of trajectories); CTAs are persistent over tiles.  Warp 0
+// issues the TMA loads, warp 1 owns the tensor memory and issues
+// tcgen05.mma into two FP32 accumulators of 2 btile columns (double buffered
+// over i), warps 2-5
+// read each accumulator back (tcgen05.ld, lane = position p):
+//   * the direct entries are weighted with u_b,k (a coalesced gather) and
+//     summed over the 32 lanes of the warp (transpose-reduce with shuffles);
+//     each warp writes its partial for (i, b);
+//   * the mirrored entries D u_bi are added into a shared-memory window
+//     indexed by k - (i0+1+p0): lane p of index i writes row (i-i0) + p, so a
+//     tile touches m + 127 rows, conflict-free with an odd row pitch.  The
+//     window is written out once per tile.
+// A finish kernel adds, for every (k, b), the direct partials and subtracts
+// the window rows that cover k, in a fixed order (deterministic), in FP64.
+#include <cudaTypedefs.h>
+
+#include "grom_internal.h"
+#include "tc.cuh"
+
+namespace grom {
+
+constexpr int K2P_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
+constexpr int K2P_A_BYTES = 128 * 64 * 2;        // 128 positions x 64 advecting indices (two boxes)
+constexpr int K2P_SMEM_MAX = 232448;             // opt-in shared memory per CTA
+
+struct K2PDev {
+  int64_t n, np, lp, bp;
+  int btile, col_tiles, pblks, m, ranges, tiles, stages, tmem_cols, wrows, wpitch;
+  const float* uf;  // bp x np FP32 states (zero padded)
+  float* cdp;       // pblks x 4 x n x bp direct partials (per position block and warp)
+  float* ep;        // tiles x wrows x btile mirrored-entry windows
+  int* err;
+};
+
+__device__ __forceinline__ void k2p_tile(const K2PDev& p, int tile, int& ct, int& pb, int64_t& i0, int64_t& i1) {
+  ct = tile % p.col_tiles;
+  const int rest = tile / p.col_tiles;
+  pb = rest % p.pblks;
+  const int r = rest / p.pblks;
+  i0 = (int64_t)r * p.m;
+  i1 = i0 + p.m < p.n ? i0 + p.m : p.n;
+}
+
+__device__ __forceinline__ void k2p_abort(volatile int* abort_flag, int* err) {
+  *abort_flag = 1;
+  atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(K2P_THREADS, 1)
+    k2p_tc_kernel(const __grid_constant__ CUtensorMap tmap_c, const __grid_constant__ CUtensorMap tmap_uh,
+                  const __grid_constant__ CUtensorMap tmap_ul, const K2PDev p) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned, kept as an offset into the shared array so that the
+  // compiler sees shared-memory accesses (not generic ones) in the epilogue
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int S = p.stages;
+  const int b_half = p.btile * 128;  // one BF16 tile of U^T (hi or lo)
+  const int stage_b = 2 * b_half;
+  uint8_t* sa = smem;                                   // S x (128 positions x 64 j)
+  uint8_t* sb = sa + (size_t)S * K2P_A_BYTES;           // S x (hi | lo)
+  float* win = reinterpret_cast<float*>(sb + (size_t)S * stage_b);
+  const size_t wbytes = ((size_t)p.wrows * p.wpitch * 4 + 15) / 16 * 16;
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(win) + wbytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;  // accumulator b holds a finished D_i
+  uint64_t* acce = accf + 2;   // accumulator b has been read back
+  uint64_t* drain = acce + 2;  // every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* ep_abort = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jblocks = (int)((p.n + 63) / 64);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], 4);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    *ep_abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_c);
+    tc::prefetch_tmap(&tmap_uh);
+    tc::prefetch_tmap(&tmap_ul);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, (uint32_t)p.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int64_t q = 0;  // K steps issued
+      bool run = true;
+      for (int tile = blockIdx.x; run && tile < p.tiles; tile += gridDim.x) {
+        int ct, pb;
+        int64_t i0, i1;
+        k2p_tile(p, tile, ct, pb, i0, i1);
+        for (int64_t i = i0; run && i < i1; ++i) {
+          for (int jb = 0; jb < jblocks; ++jb, ++q) {
+            const int s = (int)(q % S);
+            if (q >= S && !ptx::mbar_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), abort_flag)) {
+              k2p_abort(abort_flag, p.err);
+              run = false;
+              break;
+            }
+            ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(K2P_A_BYTES + stage_b));
+            uint8_t* a = sa + (size_t)s * K2P_A_BYTES;
+            tc::tma_load_3d(a, &tmap_c, pb * 128, jb * 64, (int32_t)i, &full[s]);
+            tc::tma_load_3d(a + K2P_A_BYTES / 2, &tmap_c, pb * 128 + 64, jb * 64, (int32_t)i, &full[s]);
+            uint8_t* b = sb + (size_t)s * stage_b;
+            tc::tma_load_2d(b, &tmap_uh, jb * 64, ct * p.btile, &full[s]);
+            tc::tma_load_2d(b + b_half, &tmap_ul, jb * 64, ct * p.btile, &full[s]);
+          }
+        }
+      }
+      // the copies still in flight land before the CTA exits
+      for (int64_t x = q > S ? q - S : 0; x < q; ++x)
+        if (!ptx::mbar_wait(&full[x % S], (uint32_t)((x / S) & 1), nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32_amn(128, 2 * p.btile);  // hi | lo
+      int64_t q = 0, icnt = 0;
+      bool run = true;
+      for (int tile = blockIdx.x; run && tile < p.tiles; tile += gridDim.x) {
+        int ct, pb;
+        int64_t i0, i1;
+        k2p_tile(p, tile, ct, pb, i0, i1);
+        for (int64_t i = i0; run && i < i1; ++i, ++icnt) {
+          const int bi = (int)(icnt & 1);
+          if (icnt >= 2 && !ptx::mbar_wait(&acce[bi], (uint32_t)(((icnt >> 1) - 1) & 1), abort_flag)) {
+            k2p_abort(abort_flag, p.err);
+            run = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + (uint32_t)(bi * 2 * p.btile);
+          for (int jb = 0; jb < jblocks; ++jb, ++q) {
+            const int s = (int)(q % S);
+            if (!ptx::mbar_wait(&full[s], (uint32_t)((q / S) & 1), abort_flag)) {
+              k2p_abort(abort_flag, p.err);
+              run = false;
+              break;
+            }
+            tc::fence_after_sync();
+            // A: two 64-position boxes 8 KB apart along M, 8-row K atoms 1 KB apart
+            const uint64_t a0 = tc::sw128_mnmajor_desc(sa + (size_t)s * K2P_A_BYTES, K2P_A_BYTES / 2, 1024);
+            const uint64_t bhl = tc::sw128_kmajor_desc(sb + (size_t)s * stage_b);  // 2 btile rows
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // K = 16: two 8-row atoms of A, 32 bytes of B
+              const uint32_t accum = (jb > 0 || k > 0) ? 1u : 0u;
+              tc::mma_bf16(acc, a0 + (uint64_t)(128 * k), bhl + 2 * k, idesc, accum);
+            }
+            tc::commit(&empty[s]);
+          }
+          if (run) tc::commit(&accf[bi]);
+        }
+      }
+      tc::commit(drain);
+      if (!ptx::mbar_wait(drain, 0, nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
+    }
+  } else {
+    // ----------------------------------------------- epilogue (warps 2-5)
+    const int q = warp & 3;  // tensor-memory lanes 32q .. 32q+31 belong to this warp
+    const int et = threadIdx.x - 64;
+    for (int x = et; x < p.wrows * p.wpitch; x += 128) win[x] = 0.f;
+    ptx::named_sync(1, 128);
+    int64_t icnt = 0;
+    bool run = true;
+    for (int tile = blockIdx.x; run && tile < p.tiles; tile += gridDim.x) {
+      int ct, pb;
+      int64_t i0, i1;
+      k2p_tile(p, tile, ct, pb, i0, i1);
+      const int64_t pp = (int64_t)pb * 128 + 32 * q + lane;  // this lane's packed position
+      const float* ut = p.uf + (int64_t)ct * p.btile * p.np;
+      float* cd = p.cdp + ((int64_t)pb * 4 + q) * p.n * p.bp + (int64_t)ct * p.btile;
+      for (int64_t i = i0; i < i1; ++i, ++icnt) {
+        const int bi = (int)(icnt & 1);
+        // warp-uniform: the tensor-memory loads below are collective
+        const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(&accf[bi], (uint32_t)((icnt >> 1) & 1), abort_flag));
+        if (!got && lane == 0) {
+          *ep_abort = 1;
+          k2p_abort(abort_flag, p.err);
+        }
+        ptx::named_sync(1, 128);
+        if (*ep_abort) {  // read by all four warps between the same two barriers
+          run = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int64_t k = (i + 1 + pp) % p.n;
+        float* wrow = win + ((int)(i - i0) + 32 * q + lane) * p.wpitch;
+        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(bi * 2 * p.btile);
+        for (int c0 = 0; c0 < p.btile; c0 += 32) {
+          uint32_t v[32], w[32];  // hi and lo products of columns c0 ..
+          if (p.btile == 16) {
+            tc::tmem_ld_32x32b_x32(acc, v);  // hi 0..15 | lo 16..31
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) w[cc] = v[(cc + 16) & 31];
+          } else {
+            tc::tmem_ld_32x32b_x32(acc + (uint32_t)c0, v);
+            tc::tmem_ld_32x32b_x32(acc + (uint32_t)(p.btile + c0), w);
+          }
+          // the states of this chunk: lane l holds u_{c0+l, i}; u_{b, k} is
+          // gathered per column (consecutive lanes, consecutive k)
+          const int nb = p.btile - c0 < 32 ? p.btile - c0 : 32;  // 32, or 16 in a last half chunk
+          const float ui_l = lane < nb ? __ldg(ut + (int64_t)(c0 + lane) * p.np + i) : 0.f;
+          float uk[32];
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) uk[cc] = cc < nb ? __ldg(ut + (int64_t)(c0 + cc) * p.np + k) : 0.f;
+          tc::tmem_ld_wait();
+          float t[32];
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) {
+            // columns past the tile hold other data: select, never multiply
+            const float d = cc < nb ? __uint_as_float(v[cc]) + __uint_as_float(w[cc]) : 0.f;
+            t[cc] = d * uk[cc];
+            const float ui = __shfl_sync(0xffffffffu, ui_l, cc);
+            if (cc < nb) wrow[c0 + cc] = fmaf(d, ui, wrow[c0 + cc]);
+          }
+          // transpose-reduce: afterwards lane l holds the sum over the warp's
+          // 32 positions of column c0 + l
+#pragma unroll
+          for (int s = 16; s >= 1; s >>= 1) {
+            const bool up = (lane & s) != 0;
+#pragma unroll
+            for (int cc = 0; cc < s; ++cc) {
+              const float send = up ? t[cc] : t[cc + s];
+              const float keep = up ? t[cc + s] : t[cc];
+              t[cc] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+            }
+          }
+          if (lane < nb) cd[i * p.bp + c0 + lane] = t[0];
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&acce[bi]);
+        ptx::named_sync(1, 128);  // consecutive i of different warps share window rows
+      }
+      if (!run) break;
+      float* dst = p.ep + (int64_t)tile * p.wrows * p.btile;
+      for (int x = et; x < p.wrows * p.btile; x += 128) {
+        const int w = x / p.btile, b = x - w * p.btile;
+        dst[x] = win[w * p.wpitch + b];
+        win[w * p.wpitch + b] = 0.f;
+      }
+      ptx::named_sync(1, 128);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, (uint32_t)p.tmem_cols);
+  }
+}
+
+// uf[b][k] = u_b[k] (FP32) and its BF16 hi/lo parts, zero for padding and
+// inactive trajectories.
+__global__ void k2p_prep_kernel(const K2PDev p, float* uf, __nv_bfloat16* uh, __nv_bfloat16* ul, const double* u,
+                                int64_t u_stride, const double* hist, const int64_t* taken, int64_t hist_stride,
+                                const int32_t* active, int batch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.bp * p.np) return;
+  const int64_t b = t / p.np, k = t - b * p.np;
+  float v = 0.f;
+  if (b < batch && k < p.n && (active == nullptr || active[b])) {
+    const double* ub = taken ? hist + b * hist_stride + (taken[b] % 3) * p.n : u + b * u_stride;
+    v = __double2float_rn(ub[k]);
+  }
+  uf[t] = v;
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  uh[t] = hi;
+  ul[t] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// c[b][k] = direct partials of row k - mirrored-entry windows covering k,
+// summed in a fixed order in FP64.
+__global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, double* hist, const int64_t* taken,
+                                  int64_t hist_stride, const int32_t* active, int batch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)batch * p.n) return;
+  const int64_t k = t / batch, b = t - k * batch;  // consecutive threads: consecutive b
+  if (active && !active[b]) return;
+  const int ct = (int)(b / p.btile), bl = (int)(b - (int64_t)ct * p.btile);
+  double s = 0.0;
+  for (int pb = 0; pb < p.pblks; ++pb)
+    for (int q = 0; q < 4; ++q) s += (double)p.cdp[(((int64_t)pb * 4 + q) * p.n + k) * p.bp + b];
+  // window row w of tile (range r, block pb) holds the mirrored entries of
+  // k = (r m + 1 + 128 pb + w) mod n
+  for (int pb = 0; pb < p.pblks; ++pb) {
+    const int64_t x = ((k - 1 - (int64_t)pb * 128) % p.n + p.n) % p.n;
+    auto add = [&](int r) {
+      int64_t w = x - (int64_t)r * p.m;
+      if (w < 0) w += p.n;
+      const float* e = p.ep + ((int64_t)(r * p.pblks + pb) * p.col_tiles + ct) * p.wrows * p.btile + bl;
+      for (; w < p.wrows; w += p.n) s -= (double)e[w * p.btile];
+    };
+    if (p.n <= p.wrows) {
+      for (int r = 0; r < p.ranges; ++r) add(r);
+    } else {
+      // w = x - r m for r m <= x, w = x - r m + n for r m > x; at most one row per tile
+      const int rhi = (int)(x / p.m);
+      const int rlo = x - p.wrows < 0 ? 0 : (int)((x - p.wrows) / p.m) + 1;
+      for (int r = rlo; r <= rhi; ++r) add(r);
+      const int64_t y = x + p.n - p.wrows;
+      int r2 = y < 0 ? 0 : (int)(y / p.m) + 1;
+      if (r2 < rhi + 1) r2 = rhi + 1;
+      for (int r = r2; r < p.ranges; ++r) add(r);
+    }
+  }
+  double* dst = taken ? hist + b * hist_stride + (3 + taken[b] % 3) * p.n : c + b * c_stride;
+  dst[k] = s;
+}
+
+// ------------------------------------------------------------------- host
+static PFN_cuTensorMapEncodeTiled_v12000 k2p_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// The stored rows as a 3-D tensor (p, j, i); boxes of 64 positions x 64 j.
+bool k2p_make_tmap(CUtensorMap* m, const void* packed, int64_t n, int64_t lp) {
+  auto fn = k2p_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)lp, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[2] = {(cuuint64_t)(lp * 2), (cuuint64_t)(n * lp * 2)};
+  cuuint32_t box[3] = {64, 64, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(packed), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static bool k2p_make_tmap_u(CUtensorMap* m, const void* u, int64_t np, int64_t bp, int btile) {
+  auto fn = k2p_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)bp};
+  cuuint64_t strides[1] = {(cuuint64_t)(np * 2)};
+  cuuint32_t box[2] = {64, (cuuint32_t)btile};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(u), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static size_t k2p_window_bytes(int wrows, int wpitch) { return ((size_t)wrows * wpitch * 4 + 15) / 16 * 16; }
+
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
+  K2PPlan p{};
+  p.n = n;
+  p.np = padded_n(n);
+  p.lp = lp;
+  int btile = (batch + 15) / 16 * 16;
+  if (btile > 128) btile = 128;
+  p.btile = btile;
+  p.col_tiles = (batch + btile - 1) / btile;
+  p.bp = (int64_t)p.col_tiles * btile;
+  p.pblks = (int)((lp + 127) / 128);
+  p.wpitch = btile + 1;  // odd pitch: the 32 lanes of a warp hit 32 banks
+  // test indices per tile: the largest m in [8, 32] whose tile count fills
+  // whole waves of SMs best
+  double best = -1.0;
+  int bm = 8;
+  for (int m = 32; m >= 8; --m) {
+    const int64_t tiles = (n + m - 1) / m * p.pblks * p.col_tiles;
+    const int64_t waves = (tiles + sm_count - 1) / sm_count;
+    const double eff = (double)tiles / (double)(waves * sm_count);
+    if (eff > best + 1e-9) {
+      best = eff;
+      bm = m;
+    }
+  }
+  p.m = bm;
+  p.ranges = (int)((n + bm - 1) / bm);
+  p.tiles = p.ranges * p.pblks * p.col_tiles;
+  p.wrows = bm + 127;
+  const size_t wbytes = k2p_window_bytes(p.wrows, p.wpitch);
+  const int stage = K2P_A_BYTES + 2 * btile * 128;
+  const size_t fixed = 1024 + wbytes + (size_t)(2 * 8 + 5) * 8 + 16;
+  int st = (int)(((size_t)K2P_SMEM_MAX - fixed) / (size_t)stage);
+  if (st > 8) st = 8;
+  if (st < 2) st = 2;
+  p.stages = st;
+  p.smem = 1024 + (size_t)st * stage + wbytes + (size_t)(2 * st + 5) * 8 + 16;
+  int cols = 64;  // two accumulators of 2 btile columns (hi | lo); chunks of 32 stay inside
+  while (cols < 4 * btile) cols <<= 1;
+  p.tmem_cols = cols;
+  p.grid = p.tiles < sm_count ? p.tiles : sm_count;
+  return p;
+}
+
+// uf | uh | ul | direct partials | windows
+size_t k2p_scratch_bytes(const K2PPlan& p) {
+  const size_t st = (size_t)p.bp * p.np;
+  return st * (4 + 2 + 2) + 4 * ((size_t)p.pblks * 4 * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
+}
+
+cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
+  K2PDev d{};
+  d.n = p.n;
+  d.np = p.np;
+  d.lp = p.lp;
+  d.bp = p.bp;
+  d.btile = p.btile;
+  d.col_tiles = p.col_tiles;
+  d.pblks = p.pblks;
+  d.m = p.m;
+  d.ranges = p.ranges;
+  d.tiles = p.tiles;
+  d.stages = p.stages;
+  d.tmem_cols = p.tmem_cols;
+  d.wrows = p.wrows;
+  d.wpitch = p.wpitch;
+  d.err = a.err;
+  const size_t st = (size_t)p.bp * p.np;
+  float* uf = reinterpret_cast<float*>(a.scratch);
+  __nv_bfloat16* uh = reinterpret_cast<__nv_bfloat16*>(uf + st);
+  __nv_bfloat16* ul = uh + st;
+  d.uf = uf;
+  d.cdp = reinterpret_cast<float*>(ul + st);
+  d.ep = d.cdp + (size_t)p.pblks * 4 * p.n * p.bp;
+  CUtensorMap mh, ml;
+  if (!k2p_make_tmap_u(&mh, uh, p.np, p.bp, p.btile) || !k2p_make_tmap_u(&ml, ul, p.np, p.bp, p.btile))
+    return cudaErrorInvalidValue;
+  const int64_t prep = p.bp * p.np;
+  k2p_prep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(d, uf, uh, ul, a.u, a.u_stride, a.hist, a.taken,
+                                                                 a.hist_stride, a.active, a.batch);
+  cudaError_t e = cudaFuncSetAttribute(k2p_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  if (a.ev0) prof_record(a.ev0, s);
+  k2p_tc_kernel<<<(unsigned)p.grid, K2P_THREADS, p.smem, s>>>(*tmap, mh, ml, d);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.ev1) prof_record(a.ev1, s);
+  const int64_t red = (int64_t)a.batch * p.n;
+  k2p_finish_kernel<<<(unsigned)((red + 255) / 256), 256, 0, s>>>(d, a.c, a.c_stride, a.hist, a.taken,
+                                                                  a.hist_stride, a.active, a.batch);
+  return cudaGetLastError();
+}
+
+}  // namespace grom

@@ -44,6 +44,18 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(const void* smem_tile) {
   return addr | (lbo << 16) | (sbo << 32) | (1ull << 46) /* descriptor version */ | (2ull << 61) /* SWIZZLE_128B */;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand in the 128-byte
+// swizzled canonical layout: rows of 128 bytes hold 64 bf16 along M (or N),
+// consecutive rows are consecutive K, 8-row atoms of 1024 bytes.  `sbo` is the
+// byte offset between atoms along K (8 rows further), `lbo` the byte offset
+// between 64-element blocks along M.  Advancing K by 16 adds 2 atoms
+// (2 * sbo bytes) to the start address.
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(const void* smem_tile, uint32_t lbo, uint32_t sbo) {
+  const uint64_t addr = (uint64_t)(ptx::smem_addr(smem_tile) >> 4) & 0x3FFFull;
+  return addr | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands
 // K-major, dense, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -52,6 +64,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | (1u << 10)                      // B format: BF16
          | ((uint32_t)(N >> 3) << 17)      // N / 8
          | ((uint32_t)(M >> 4) << 24);     // M / 16
+}
+
+// The same with A MN-major (the "transpose A" bit) and B K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_amn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 15);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
@@ -101,6 +118,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
           "r"(ptx::smem_addr(dst)),
       "l"(tmap), "r"(x), "r"(y), "r"(ptx::smem_addr(bar))
+      : "memory");
+}
+
+// 3D tiled load of box (x, y, z) into shared memory, completing on an
+// mbarrier.  x * element size must be a multiple of 16.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int32_t x, int32_t y, int32_t z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(ptx::smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(ptx::smem_addr(bar))
       : "memory");
 }
 

@@ -88,10 +88,13 @@ def test_full_size_stepping_headline_configuration(tensor, layout):
     rom.close()
 
 
+@pytest.mark.parametrize("layout", ["dense", "skew_packed"])
 @pytest.mark.parametrize("batch", [16, 256])
-def test_full_size_batched_tensor_cores(tensor, batch):
+def test_full_size_batched_tensor_cores(tensor, batch, layout):
+    # dense: K2 over the Khatri-Rao product; skew-packed: the factored K2P
     U0 = synth.initial_condition(N, SEED, 0, batch)
-    rom = grom.Rom(N, "full", "bf16", tensor=tensor, stiffness=synth.diag_stiffness(N), max_batch=batch)
+    rom = grom.Rom(N, "full", "bf16", tensor=tensor, stiffness=synth.diag_stiffness(N), max_batch=batch,
+                   layout=layout)
     rom.set_kernel("tensor")
     ud = torch.from_numpy(U0).cuda()
     cd = torch.empty_like(ud)

@@ -138,14 +138,19 @@ def test_packed_slab_upload():
     rom.close()
 
 
-def test_packed_has_no_tensor_core_path():
+def test_packed_kernel_choice():
+    # BF16 packed ROMs have the factored tensor-core kernel (K2P, tested in
+    # test_gpu_k2p.py); the other storage types have none
     n = 64
     C = synth.skew_normal_tensor(n, synth.seed_for(0) + 7500)
-    rom = _rom(C, "bf16", max_batch=32)
+    rom = _rom(C, "f32", max_batch=32)
     with pytest.raises(grom.GromError) as e:
         rom.set_kernel("tensor")
     assert e.value.name == "UNSUPPORTED"
-    # batches beyond the tensor-core threshold still run (streaming kernel)
+    rom.close()
+    # batches beyond the tensor-core threshold, forced onto the streaming kernel
+    rom = _rom(C, "bf16", max_batch=32)
+    rom.set_kernel("stream")
     U = synth.initial_condition(n, 11, 0, 32)
     c = _eval(rom, U)
     for b in (0, 31):

@@ -22,7 +22,7 @@ def models():
     nf, nc, r = 64, 48, 12
     Cf = synth.skew_normal_tensor(nf, 21)
     U, V, W, _, seed = synth.cp_workload(nc, r, 1)
-    s1, s2, s3 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    s1, s2, s3, s4 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     roms = {
         "full_bf16": grom.Rom(nf, "full", "bf16", tensor=Cf, stiffness=synth.diag_stiffness(nf), max_batch=12,
                               stream=s1),
@@ -30,6 +30,9 @@ def models():
                            max_batch=20, stream=s2),
         "full_f64": grom.Rom(nf, "full", "f64", tensor=Cf, stiffness=synth.diag_stiffness(nf), max_batch=4,
                              stream=s3),
+        # skew-packed BF16: 12 slots step through the factored tensor-core kernel
+        "packed_bf16": grom.Rom(nf, "full", "bf16", tensor=Cf, stiffness=synth.diag_stiffness(nf), max_batch=12,
+                                stream=s4, layout="skew_packed"),
     }
     return roms, (Cf, (U, V, W))
 
@@ -37,20 +40,21 @@ def models():
 def test_mixed_requests_match_alone(models):
     roms, (Cf, fac) = models
     srv = grom.Server(150 * 2 ** 30, quantum=8)
-    ids = [srv.add_rom(roms["full_bf16"], 12), srv.add_rom(roms["cp_f64"], 20), srv.add_rom(roms["full_f64"], 4)]
+    ids = [srv.add_rom(roms["full_bf16"], 12), srv.add_rom(roms["cp_f64"], 20), srv.add_rom(roms["full_f64"], 4),
+           srv.add_rom(roms["packed_bf16"], 12)]
     rng = np.random.default_rng(3)
-    count = 60
-    which = rng.integers(0, 3, count)
+    count = 80
+    which = rng.integers(0, 4, count)
     horizons = rng.integers(5, 120, count)
     arrivals = np.sort(rng.random(count) * 0.02)
-    n_of = [64, 48, 64]
+    n_of = [64, 48, 64, 64]
     u0s = [synth.initial_condition(n_of[w], 100 + q)[0] for q, w in enumerate(which)]
     out = srv.serve([ids[w] for w in which], horizons, arrivals, u0s, want_final=True)
     assert np.all(out["status"] == 0), out["status"]
     np.testing.assert_array_equal(out["steps"], horizons)
     assert out["stats"]["peak_active"] > 1
-    names = ["full_bf16", "cp_f64", "full_f64"]
-    tol = {"full_bf16": 1e-5, "cp_f64": 1e-11, "full_f64": 1e-12}
+    names = ["full_bf16", "cp_f64", "full_f64", "packed_bf16"]
+    tol = {"full_bf16": 1e-5, "cp_f64": 1e-11, "full_f64": 1e-12, "packed_bf16": 1e-5}
     for q in range(0, count, 3):
         rom = roms[names[which[q]]]
         tr = grom.Trajectories(rom, u0s[q][None, :])
