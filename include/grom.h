@@ -149,7 +149,14 @@ typedef struct grom_desc {
    * f += A (fb_0 o fc_0), fb', fc' the rows 1..n.  grom_nonlinear then
    * evaluates the core term only; grom_step advances the full model. */
   int32_t augmented;
-  int32_t reserved[2];  /* must be zero                                           */
+  /* FULL, dense layout, BF16 storage and max_batch > 8: by default the
+   * library keeps a tile-major copy of the stored tensor beside it for the
+   * tensor-core kernel K2 (every 256 x 64 operand tile one contiguous block;
+   * round_up(n, 256) * n * round_up(n, 64) * 2 bytes).  1: keep the row layout
+   * only (less memory; K2 then reads the row layout, at lower bandwidth for
+   * small batches).  The skew-packed layout keeps no copy. */
+  int32_t no_tile_copy;
+  int32_t reserved;     /* must be zero                                           */
 } grom_desc;
 
 /* Creates a ROM on the current CUDA device.  Every input is copied; the caller

@@ -54,7 +54,7 @@ class _Desc(ctypes.Structure):
         ("linear", ctypes.c_void_p), ("linear_diag", ctypes.c_void_p), ("forcing", ctypes.c_void_p),
         ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("order", ctypes.c_int32),
         ("defer_tensor", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("layout", ctypes.c_int32),
-        ("augmented", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("augmented", ctypes.c_int32), ("no_tile_copy", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -207,7 +207,7 @@ class Rom:
 
     def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,
                  linear=None, forcing=None, nu=1e-2, dt=1e-3, order=3, max_batch=1, defer_tensor=False,
-                 stream=None, layout="dense", augmented=False):
+                 stream=None, layout="dense", augmented=False, tile_copy=True):
         lib = load()
         keep = []
 
@@ -225,6 +225,7 @@ class Rom:
         d.defer_tensor = 1 if defer_tensor else 0
         d.layout = LAYOUTS[layout]
         d.augmented = 1 if augmented else 0
+        d.no_tile_copy = 0 if tile_copy else 1
         if form == "full":
             d.tensor = arr(tensor)
         else:

@@ -193,7 +193,9 @@ static grom_status check_skew_probe(grom_rom* r) {
 // Tile-major copy of a dense BF16 tensor for the tensor-core kernel (built
 // once, outside any stream capture).
 static grom_status build_k2_tiles(grom_rom* r) {
-  if (r->k2_tiles || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE || r->rows_uploaded != r->n) return GROM_OK;
+  if (r->k2_tiles || !r->k2_ok || r->no_tile_copy || r->form != GROM_FORM_FULL || r->layout != GROM_LAYOUT_DENSE ||
+      r->rows_uploaded != r->n)
+    return GROM_OK;
   // the copy only speeds K2 up: without room for it K2 reads the row-major tensor
   grom_status st = dmalloc(&r->k2_tiles, k2_tiles_bytes(r->n), &r->total_bytes);
   if (st) return st == GROM_ERR_OOM ? GROM_OK : st;
@@ -320,8 +322,9 @@ int32_t grom_max_n(int32_t form, int32_t storage) {
 grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   if (!d || !out) return fail(GROM_ERR_INVALID_ARG, "grom_create: null argument");
   *out = nullptr;
-  for (int q = 0; q < 2; ++q)
-    if (d->reserved[q]) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
+  if (d->reserved) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
+  if (d->no_tile_copy != 0 && d->no_tile_copy != 1)
+    return fail(GROM_ERR_INVALID_ARG, "grom_create: no_tile_copy must be 0 or 1");
   if (d->augmented != 0 && d->augmented != 1) return fail(GROM_ERR_INVALID_ARG, "grom_create: augmented must be 0 or 1");
   if (d->augmented && !((d->form == GROM_FORM_FULL && d->tensor) || d->form == GROM_FORM_CP))
     return fail(GROM_ERR_INVALID_ARG, "grom_create: augmented needs the full form with its tensor, or the general CP form");
@@ -367,6 +370,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
   r->dt = d->dt;
   r->max_batch = d->max_batch > 0 ? d->max_batch : 1;
   r->layout = d->layout;
+  r->no_tile_copy = d->no_tile_copy != 0;
   r->stream = static_cast<cudaStream_t>(stream);
   const int64_t n = r->n;
   grom_status st = GROM_OK;
@@ -432,6 +436,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     if (d->tensor && d->augmented) {
       if ((st = upload_augmented_full(r, d->tensor, Laug, faug))) return bail(st);
       r->rows_uploaded = n;
+      if (r->max_batch > 8 && (st = build_k2_tiles(r))) return bail(st);
     } else if (d->tensor) {
       if (packed) {
         if ((st = upload_rows_packed(r, d->tensor, 0, n))) return bail(st);

@@ -313,6 +313,7 @@ struct grom_rom {
   bool k2_ok = false;                // tensor map built (BF16 full form; K2P's map for the packed layout)
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_tiles = nullptr;          // tile-major copy for K2 (nullable)
+  bool no_tile_copy = false;         // grom_desc.no_tile_copy
   CUtensorMap k2_tmap_tiled;         // its TMA descriptor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2

@@ -24,11 +24,12 @@
 // column tile of trajectories); CTAs are persistent over tiles.  Warp 0
 // issues the TMA loads, warp 1 owns the tensor memory and issues
 // tcgen05.mma into two FP32 accumulators of 2 btile columns (double buffered
-// over i), warps 2-5
-// read each accumulator back (tcgen05.ld, lane = position p):
+// over i), warps 2-9 read each accumulator back (tcgen05.ld, lane = position
+// p; two warps per lane quadrant, splitting the 32-column chunks):
 //   * the direct entries are weighted with u_b,k (a coalesced gather) and
 //     summed over the 32 lanes of the warp (transpose-reduce with shuffles);
-//     each warp writes its partial for (i, b);
+//     the four lane quadrants' sums are added in shared memory, in a fixed
+//     order, and written once per (i, b);
 //   * the mirrored entries D u_bi are added into a shared-memory window
 //     indexed by k - (i0+1+p0): lane p of index i writes row (i-i0) + p, so a
 //     tile touches m + 127 rows, conflict-free with an odd row pitch.  The
@@ -42,7 +43,8 @@
 
 namespace grom {
 
-constexpr int K2P_THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
+constexpr int K2P_THREADS = 320;                 // TMA warp, MMA warp, 8 epilogue warps
+constexpr int K2P_EPI = 256;                     // epilogue threads
 constexpr int K2P_A_BYTES = 128 * 64 * 2;        // 128 positions x 64 advecting indices (two boxes)
 constexpr int K2P_SMEM_MAX = 232448;             // opt-in shared memory per CTA
 
@@ -50,7 +52,7 @@ struct K2PDev {
   int64_t n, np, lp, bp;
   int btile, col_tiles, pblks, m, ranges, tiles, stages, tmem_cols, wrows, wpitch;
   const float* uf;  // bp x np FP32 states (zero padded)
-  float* cdp;       // pblks x 4 x n x bp direct partials (per position block and warp)
+  float* cdp;       // pblks x n x bp direct partials (per position block)
   float* ep;        // tiles x wrows x btile mirrored-entry windows
   int* err;
 };
@@ -69,6 +71,54 @@ __device__ __forceinline__ void k2p_abort(volatile int* abort_flag, int* err) {
   atomicOr(err, DEV_ERR_TIMEOUT);
 }
 
+// One chunk of NB (32 or 16) trajectory columns of an accumulator, for the
+// 32 positions of this warp's lanes: the direct entries D u_k summed over the
+// lanes into cdst[0 .. NB) (shared memory), the mirrored entries D u_i added into this lane's
+// window row.  acc_hi / acc_lo address the hi and lo products of the chunk,
+// ucol the FP32 states of its first column (row stride np).
+template <int NB>
+__device__ __forceinline__ void k2p_chunk(uint32_t acc_hi, uint32_t acc_lo, const float* __restrict__ ucol,
+                                          int64_t np, int64_t k, int64_t i, float* wrow, float* cdst, int lane) {
+  uint32_t v[NB], w[NB];
+  if constexpr (NB == 32) {
+    tc::tmem_ld_32x32b_x32(acc_hi, v);
+    tc::tmem_ld_32x32b_x32(acc_lo, w);
+  } else {
+    tc::tmem_ld_32x32b_x16(acc_hi, v);
+    tc::tmem_ld_32x32b_x16(acc_lo, w);
+  }
+  // lane l holds u_{c0+l, i}; u_{b, k} is gathered per column (consecutive
+  // lanes read consecutive k)
+  const float ui_l = lane < NB ? __ldg(ucol + lane * np + i) : 0.f;
+  float uk[NB];
+  const float* pk = ucol + k;
+#pragma unroll
+  for (int cc = 0; cc < NB; ++cc, pk += np) uk[cc] = __ldg(pk);
+  tc::tmem_ld_wait();
+  float t[32];
+#pragma unroll
+  for (int cc = 0; cc < NB; ++cc) {
+    const float d = __uint_as_float(v[cc]) + __uint_as_float(w[cc]);
+    t[cc] = d * uk[cc];
+    wrow[cc] = fmaf(d, __shfl_sync(0xffffffffu, ui_l, cc), wrow[cc]);
+  }
+#pragma unroll
+  for (int cc = NB; cc < 32; ++cc) t[cc] = 0.f;
+  // transpose-reduce: afterwards lane l holds the sum over the warp's 32
+  // positions of column l
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int cc = 0; cc < s; ++cc) {
+      const float send = up ? t[cc] : t[cc + s];
+      const float keep = up ? t[cc + s] : t[cc];
+      t[cc] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  if (lane < NB) cdst[lane] = t[0];
+}
+
 __global__ void __launch_bounds__(K2P_THREADS, 1)
     k2p_tc_kernel(const __grid_constant__ CUtensorMap tmap_c, const __grid_constant__ CUtensorMap tmap_uh,
                   const __grid_constant__ CUtensorMap tmap_ul, const K2PDev p) {
@@ -83,7 +133,8 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
   uint8_t* sb = sa + (size_t)S * K2P_A_BYTES;           // S x (hi | lo)
   float* win = reinterpret_cast<float*>(sb + (size_t)S * stage_b);
   const size_t wbytes = ((size_t)p.wrows * p.wpitch * 4 + 15) / 16 * 16;
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(win) + wbytes);
+  float* red = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(win) + wbytes);  // 4 quadrants x 128 columns
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + 4 * 128);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;  // accumulator b holds a finished D_i
   uint64_t* acce = accf + 2;   // accumulator b has been read back
@@ -102,7 +153,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&accf[b], 1);
-      ptx::mbar_init(&acce[b], 4);
+      ptx::mbar_init(&acce[b], K2P_EPI / 32);
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -198,11 +249,12 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
       if (!ptx::mbar_wait(drain, 0, nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
     }
   } else {
-    // ----------------------------------------------- epilogue (warps 2-5)
-    const int q = warp & 3;  // tensor-memory lanes 32q .. 32q+31 belong to this warp
+    // ----------------------------------------------- epilogue (warps 2-9)
+    const int q = warp & 3;             // tensor-memory lanes 32q .. 32q+31 belong to this warp
+    const int half = (warp - 2) >> 2;   // the pair of a quadrant takes alternate 32-column chunks
     const int et = threadIdx.x - 64;
-    for (int x = et; x < p.wrows * p.wpitch; x += 128) win[x] = 0.f;
-    ptx::named_sync(1, 128);
+    for (int x = et; x < p.wrows * p.wpitch; x += K2P_EPI) win[x] = 0.f;
+    ptx::named_sync(1, K2P_EPI);
     int64_t icnt = 0;
     bool run = true;
     for (int tile = blockIdx.x; run && tile < p.tiles; tile += gridDim.x) {
@@ -211,7 +263,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
       k2p_tile(p, tile, ct, pb, i0, i1);
       const int64_t pp = (int64_t)pb * 128 + 32 * q + lane;  // this lane's packed position
       const float* ut = p.uf + (int64_t)ct * p.btile * p.np;
-      float* cd = p.cdp + ((int64_t)pb * 4 + q) * p.n * p.bp + (int64_t)ct * p.btile;
+      float* cd = p.cdp + (int64_t)pb * p.n * p.bp + (int64_t)ct * p.btile;
       for (int64_t i = i0; i < i1; ++i, ++icnt) {
         const int bi = (int)(icnt & 1);
         // warp-uniform: the tensor-memory loads below are collective
@@ -220,8 +272,8 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
           *ep_abort = 1;
           k2p_abort(abort_flag, p.err);
         }
-        ptx::named_sync(1, 128);
-        if (*ep_abort) {  // read by all four warps between the same two barriers
+        ptx::named_sync(1, K2P_EPI);
+        if (*ep_abort) {  // read by all epilogue warps between the same two barriers
           run = false;
           break;
         }
@@ -229,60 +281,29 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
         const int64_t k = (i + 1 + pp) % p.n;
         float* wrow = win + ((int)(i - i0) + 32 * q + lane) * p.wpitch;
         const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(bi * 2 * p.btile);
-        for (int c0 = 0; c0 < p.btile; c0 += 32) {
-          uint32_t v[32], w[32];  // hi and lo products of columns c0 ..
-          if (p.btile == 16) {
-            tc::tmem_ld_32x32b_x32(acc, v);  // hi 0..15 | lo 16..31
-#pragma unroll
-            for (int cc = 0; cc < 32; ++cc) w[cc] = v[(cc + 16) & 31];
-          } else {
-            tc::tmem_ld_32x32b_x32(acc + (uint32_t)c0, v);
-            tc::tmem_ld_32x32b_x32(acc + (uint32_t)(p.btile + c0), w);
-          }
-          // the states of this chunk: lane l holds u_{c0+l, i}; u_{b, k} is
-          // gathered per column (consecutive lanes, consecutive k)
-          const int nb = p.btile - c0 < 32 ? p.btile - c0 : 32;  // 32, or 16 in a last half chunk
-          const float ui_l = lane < nb ? __ldg(ut + (int64_t)(c0 + lane) * p.np + i) : 0.f;
-          float uk[32];
-#pragma unroll
-          for (int cc = 0; cc < 32; ++cc) uk[cc] = cc < nb ? __ldg(ut + (int64_t)(c0 + cc) * p.np + k) : 0.f;
-          tc::tmem_ld_wait();
-          float t[32];
-#pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
-            // columns past the tile hold other data: select, never multiply
-            const float d = cc < nb ? __uint_as_float(v[cc]) + __uint_as_float(w[cc]) : 0.f;
-            t[cc] = d * uk[cc];
-            const float ui = __shfl_sync(0xffffffffu, ui_l, cc);
-            if (cc < nb) wrow[c0 + cc] = fmaf(d, ui, wrow[c0 + cc]);
-          }
-          // transpose-reduce: afterwards lane l holds the sum over the warp's
-          // 32 positions of column c0 + l
-#pragma unroll
-          for (int s = 16; s >= 1; s >>= 1) {
-            const bool up = (lane & s) != 0;
-#pragma unroll
-            for (int cc = 0; cc < s; ++cc) {
-              const float send = up ? t[cc] : t[cc + s];
-              const float keep = up ? t[cc + s] : t[cc];
-              t[cc] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-            }
-          }
-          if (lane < nb) cd[i * p.bp + c0 + lane] = t[0];
+        for (int c0 = 32 * half; c0 < p.btile; c0 += 64) {
+          const uint32_t ahi = acc + (uint32_t)c0, alo = acc + (uint32_t)(p.btile + c0);
+          const float* ucol = ut + (int64_t)c0 * p.np;
+          if (p.btile - c0 >= 32)
+            k2p_chunk<32>(ahi, alo, ucol, p.np, k, i, wrow + c0, red + q * 128 + c0, lane);
+          else  // a last half chunk (btile an odd multiple of 16)
+            k2p_chunk<16>(ahi, alo, ucol, p.np, k, i, wrow + c0, red + q * 128 + c0, lane);
         }
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&acce[bi]);
-        ptx::named_sync(1, 128);  // consecutive i of different warps share window rows
+        ptx::named_sync(1, K2P_EPI);  // consecutive i of different quadrants share window rows
+        // the four quadrants' direct sums (read before the next i's first barrier)
+        if (et < p.btile) cd[i * p.bp + et] = ((red[et] + red[128 + et]) + red[256 + et]) + red[384 + et];
       }
       if (!run) break;
       float* dst = p.ep + (int64_t)tile * p.wrows * p.btile;
-      for (int x = et; x < p.wrows * p.btile; x += 128) {
+      for (int x = et; x < p.wrows * p.btile; x += K2P_EPI) {
         const int w = x / p.btile, b = x - w * p.btile;
         dst[x] = win[w * p.wpitch + b];
         win[w * p.wpitch + b] = 0.f;
       }
-      ptx::named_sync(1, 128);
+      ptx::named_sync(1, K2P_EPI);
     }
   }
   tc::fence_before_sync();
@@ -322,8 +343,7 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
   if (active && !active[b]) return;
   const int ct = (int)(b / p.btile), bl = (int)(b - (int64_t)ct * p.btile);
   double s = 0.0;
-  for (int pb = 0; pb < p.pblks; ++pb)
-    for (int q = 0; q < 4; ++q) s += (double)p.cdp[(((int64_t)pb * 4 + q) * p.n + k) * p.bp + b];
+  for (int pb = 0; pb < p.pblks; ++pb) s += (double)p.cdp[((int64_t)pb * p.n + k) * p.bp + b];
   // window row w of tile (range r, block pb) holds the mirrored entries of
   // k = (r m + 1 + 128 pb + w) mod n
   for (int pb = 0; pb < p.pblks; ++pb) {
@@ -340,6 +360,7 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
       // w = x - r m for r m <= x, w = x - r m + n for r m > x; at most one row per tile
       const int rhi = (int)(x / p.m);
       const int rlo = x - p.wrows < 0 ? 0 : (int)((x - p.wrows) / p.m) + 1;
+#pragma unroll 4
       for (int r = rlo; r <= rhi; ++r) add(r);
       const int64_t y = x + p.n - p.wrows;
       int r2 = y < 0 ? 0 : (int)(y / p.m) + 1;
@@ -405,11 +426,20 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
   p.bp = (int64_t)p.col_tiles * btile;
   p.pblks = (int)((lp + 127) / 128);
   p.wpitch = btile + 1;  // odd pitch: the 32 lanes of a warp hit 32 banks
+  const int stage = K2P_A_BYTES + 2 * btile * 128;
+  auto stages_for = [&](int m) {
+    const size_t fixed = 1024 + k2p_window_bytes(m + 127, p.wpitch) + 4 * 128 * 4 + (size_t)(2 * 8 + 5) * 8 + 16;
+    int st = (int)(((size_t)K2P_SMEM_MAX - fixed) / (size_t)stage);
+    return st > 8 ? 8 : st;
+  };
   // test indices per tile: the largest m in [8, 32] whose tile count fills
-  // whole waves of SMs best
+  // whole waves of SMs best, among those that keep the deepest pipeline the
+  // shared memory allows at m = 8 (the window grows with m)
+  const int st_max = stages_for(8) < 3 ? stages_for(8) : 3;
   double best = -1.0;
   int bm = 8;
   for (int m = 32; m >= 8; --m) {
+    if (stages_for(m) < st_max) continue;
     const int64_t tiles = (n + m - 1) / m * p.pblks * p.col_tiles;
     const int64_t waves = (tiles + sm_count - 1) / sm_count;
     const double eff = (double)tiles / (double)(waves * sm_count);
@@ -422,14 +452,10 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
   p.ranges = (int)((n + bm - 1) / bm);
   p.tiles = p.ranges * p.pblks * p.col_tiles;
   p.wrows = bm + 127;
-  const size_t wbytes = k2p_window_bytes(p.wrows, p.wpitch);
-  const int stage = K2P_A_BYTES + 2 * btile * 128;
-  const size_t fixed = 1024 + wbytes + (size_t)(2 * 8 + 5) * 8 + 16;
-  int st = (int)(((size_t)K2P_SMEM_MAX - fixed) / (size_t)stage);
-  if (st > 8) st = 8;
+  int st = stages_for(bm);
   if (st < 2) st = 2;
   p.stages = st;
-  p.smem = 1024 + (size_t)st * stage + wbytes + (size_t)(2 * st + 5) * 8 + 16;
+  p.smem = 1024 + (size_t)st * stage + k2p_window_bytes(p.wrows, p.wpitch) + 4 * 128 * 4 + (size_t)(2 * st + 5) * 8 + 16;
   int cols = 64;  // two accumulators of 2 btile columns (hi | lo); chunks of 32 stay inside
   while (cols < 4 * btile) cols <<= 1;
   p.tmem_cols = cols;
@@ -440,7 +466,7 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
 // uf | uh | ul | direct partials | windows
 size_t k2p_scratch_bytes(const K2PPlan& p) {
   const size_t st = (size_t)p.bp * p.np;
-  return st * (4 + 2 + 2) + 4 * ((size_t)p.pblks * 4 * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
+  return st * (4 + 2 + 2) + 4 * ((size_t)p.pblks * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
 }
 
 cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
@@ -466,7 +492,7 @@ cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& 
   __nv_bfloat16* ul = uh + st;
   d.uf = uf;
   d.cdp = reinterpret_cast<float*>(ul + st);
-  d.ep = d.cdp + (size_t)p.pblks * 4 * p.n * p.bp;
+  d.ep = d.cdp + (size_t)p.pblks * p.n * p.bp;
   CUtensorMap mh, ml;
   if (!k2p_make_tmap_u(&mh, uh, p.np, p.bp, p.btile) || !k2p_make_tmap_u(&ml, ul, p.np, p.bp, p.btile))
     return cudaErrorInvalidValue;

@@ -175,3 +175,27 @@ def test_k2p_augmented_model():
         ref.step(h, steps)
         assert _rel(H[b][:n], h[:n]) <= TOL_BF16, b
     rom.close()
+
+
+@pytest.mark.parametrize("n,batch", [(96, 16), (129, 40), (200, 130), (256, 256)])
+def test_k2_tile_copy_and_row_layout_agree_bitwise(n, batch):
+    # dense ROMs created for batches above 8 keep a tile-major copy of the
+    # tensor for K2; without it (no_tile_copy) K2 reads the row layout.  Same
+    # operands, same accumulation order: same bits.
+    C = synth.skew_normal_tensor(n, synth.seed_for(0) + 8600 + n)
+    U = synth.initial_condition(n, 9, 0, batch)
+    tiled = _rom(C, layout="dense", max_batch=batch)
+    rows = _rom(C, layout="dense", max_batch=batch, tile_copy=False)
+    c1, c2 = _eval(tiled, U), _eval(rows, U)
+    np.testing.assert_array_equal(c1, c2)
+    for b in (0, batch - 1):
+        assert _rel(c1[b], oracle.nonlinear_full(C, U[b])) <= TOL_BF16
+    # the copy is the only difference in the footprint: 256-row tiles of C_(1)
+    npad = (n + 63) // 64 * 64
+    assert tiled.nbytes - rows.nbytes == (n + 255) // 256 * 256 * n * npad * 2
+    # the skew-packed layout keeps no copy
+    packed = _rom(C, max_batch=batch)
+    packed_rows = _rom(C, max_batch=batch, tile_copy=False)
+    assert packed.nbytes == packed_rows.nbytes
+    for r in (tiled, rows, packed, packed_rows):
+        r.close()
