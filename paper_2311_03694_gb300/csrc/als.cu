@@ -11,19 +11,23 @@
 //   X1[i][j][k]  (rows i: P = A2 over j, Q = A3 over k)
 //   X2[j][i][k]  (rows j: P = A1 over i, Q = A3 over k)
 //   X3[k][i][j]  (rows k: P = A1 over i, Q = A2 over j)
-// The Gram matrices are FP64 on the device; the rank x rank SPD solves are
-// FP64 Cholesky on the host (rank^3/3 + 2 n rank^2 flops per update).
+// Everything after the upload stays on the device: the factors, their FP64
+// Gram matrices, and the rank x rank SPD solves (a blocked FP64 Cholesky of
+// the normal matrix, then one warp per row for the two triangular solves;
+// rank^3/3 + 2 n rank^2 flops per update).  Only the Cholesky breakdown flag,
+// the residual's two sums and the final factors come back to the host.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "grom_internal.h"
 
 using namespace grom;
+
+constexpr int ALS_PARTS = 256;  // blocks of the residual's reductions
 
 struct grom_als {
   int64_t n = 0, np = 0;
@@ -33,15 +37,22 @@ struct grom_als {
   CUtensorMap tmap[3];
   double xnorm2 = 0.0;  // ||X||_F^2 of the BF16 tensor the fit sees
   int* err = nullptr;
-  // per-fit buffers (grown on demand)
+  // per-fit buffers (grown on demand), FP64 on the device
   int64_t rcap = 0;
-  double* f[3] = {nullptr, nullptr, nullptr};  // factors on the device, n x rank FP64
-  double* mt = nullptr;                        // MTTKRP output, rank x n FP64
-  double* gram = nullptr;                      // rank x rank FP64
+  double* f[3] = {nullptr, nullptr, nullptr};     // factors, n x rank
+  double* anew = nullptr;                         // a least-squares update, n x rank
+  double* b1 = nullptr;                           // ALS-skew's shared factor, n x rank/2
+  double* mt = nullptr;                           // MTTKRP output, rank x n
+  double* gram[3] = {nullptr, nullptr, nullptr};  // Gram matrices of the factors, rank x rank
+  double* h = nullptr;                            // normal matrix, then its Cholesky factor L
+  double* lt = nullptr;                           // L^T
+  double* rdiag = nullptr;                        // reciprocals of L's diagonal
+  double* part = nullptr;                         // 2 x ALS_PARTS reduction partials
+  int* flag = nullptr;                            // Cholesky breakdown
   void* k2s = nullptr;
   size_t k2s_bytes = 0;
   // timing since the last grom_als_stats: MTTKRP device time (CUDA events
-  // around each tensor-core launch) and host time of the SPD solves
+  // around each tensor-core launch) and wall time of the SPD solves
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double mttkrp_ms = 0.0, solve_ms = 0.0;
   int64_t mttkrp_calls = 0;
@@ -119,48 +130,304 @@ __global__ void k_gram(const double* __restrict__ F, int64_t n, int64_t r, doubl
   if (row < r && col < r) G[row * r + col] = s;
 }
 
-// Cholesky factor of the SPD matrix H (r x r, row-major) in place (lower).
-bool cholesky(std::vector<double>& H, int64_t r) {
-  for (int64_t j = 0; j < r; ++j) {
-    double d = H[j * r + j];
-    for (int64_t q = 0; q < j; ++q) d -= H[j * r + q] * H[j * r + q];
-    if (!(d > 0.0) || !std::isfinite(d)) return false;
-    d = std::sqrt(d);
-    H[j * r + j] = d;
-    for (int64_t i = j + 1; i < r; ++i) {
-      double s = H[i * r + j];
-      for (int64_t q = 0; q < j; ++q) s -= H[i * r + q] * H[j * r + q];
-      H[i * r + j] = s / d;
-    }
+// ------------------------------------------------ SPD solves on the device
+// The normal equations A = M H^-1 with H = Ga o Gb + (ridge + mu) max diag(Ga o Gb) I.
+
+// H, with the diagonal maximum found by every block (r entries).
+__global__ void k_als_normal(const double* __restrict__ Ga, const double* __restrict__ Gb, int64_t r, double rel,
+                             double* __restrict__ H) {
+  __shared__ double wm[32];
+  double m = 0.0;
+  for (int64_t a = threadIdx.x; a < r; a += blockDim.x) m = fmax(m, Ga[a * r + a] * Gb[a * r + a]);
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
+  const double add = rel * m;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r * r; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t / r;
+    H[t] = Ga[t] * Gb[t] + (t == a * r + a ? add : 0.0);
   }
-  return true;
 }
 
-// A[i][:] = H^{-1} M[i][:] for every row i, with M given transposed (Mt,
-// r x n) and H = L L^T; rows in parallel.
-void solve_rows(const std::vector<double>& L, int64_t r, const std::vector<double>& Mt, int64_t n,
-                std::vector<double>& A) {
-  A.assign((size_t)(n * r), 0.0);
-  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 32));
-  auto work = [&](int tid) {
-    std::vector<double> y((size_t)r);
-    for (int64_t i = tid; i < n; i += nt) {
-      for (int64_t a = 0; a < r; ++a) {
-        double s = Mt[a * n + i];
-        for (int64_t q = 0; q < a; ++q) s -= L[a * r + q] * y[q];
-        y[a] = s / L[a * r + a];
-      }
-      for (int64_t a = r - 1; a >= 0; --a) {
-        double s = y[a];
-        for (int64_t q = a + 1; q < r; ++q) s -= L[q * r + a] * A[i * r + q];
-        A[i * r + a] = s / L[a * r + a];
+constexpr int CH = 32;  // Cholesky block
+constexpr int UT = 16;  // trailing-update tile
+
+// 1/sqrt(d) for a positive finite d: the exponent is split off so that the
+// mantissa part m in [1, 4) takes an FP32 estimate, which two Newton-Raphson
+// steps for the reciprocal square root, y <- y (3 - m y^2) / 2, bring to FP64
+// precision (each step about doubles the correct bits).  FP64 division and
+// square root cost thousands of cycles on this part, a step of this a few
+// hundred.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  const int e = ilogb(d) >> 1;
+  const double m = scalbn(d, -2 * e);
+  double y = (double)rsqrtf((float)m);
+  y = y * (1.5 - 0.5 * m * y * y);
+  y = y * (1.5 - 0.5 * m * y * y);
+  return scalbn(y, -e);
+}
+
+// Factors the diagonal block at (kb, kb) in place (lower), one thread per
+// entry (32 x 32), right-looking, and stores the reciprocals of its pivots
+// in rdiag[kb ..].  A pivot that is not positive and finite sets *flag.
+__global__ void __launch_bounds__(CH * CH) k_chol_diag(double* H, int64_t r, int64_t kb, double* rdiag, int* flag) {
+  __shared__ double A[CH][CH + 1];
+  __shared__ double ry;
+  __shared__ int bad;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // entry A[ty][tx]
+  const int nb = (int)(r - kb < CH ? r - kb : CH);
+  if (ty < nb && tx < nb) A[ty][tx] = H[(kb + ty) * r + kb + tx];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x == 0) {
+      const double d = A[c][c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        const double y = rsqrt_nr(d);
+        A[c][c] = d * y;
+        ry = y;
+        rdiag[kb + c] = y;
       }
     }
-  };
-  std::vector<std::thread> th;
-  for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
-  work(0);
-  for (auto& t : th) t.join();
+    __syncthreads();
+    if (bad) break;  // read by every thread between the same two barriers
+    if (tx == c && ty > c && ty < nb) A[ty][c] *= ry;
+    __syncthreads();
+    if (ty > c && ty < nb && tx > c && tx <= ty) A[ty][tx] -= A[ty][c] * A[tx][c];
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+    return;
+  }
+  if (ty < nb && tx < nb) H[(kb + ty) * r + kb + tx] = tx <= ty ? A[ty][tx] : 0.0;
+}
+
+// Rows i >= kb + CH: H[i][kb .. kb+CH) <- H[i][kb .. kb+CH) L11^-T (one warp
+// per row, forward substitution with lane = column).
+__global__ void k_chol_panel(double* H, int64_t r, int64_t kb, const double* __restrict__ rdiag) {
+  __shared__ double L11[CH][CH + 1];  // column CH: reciprocals of the pivots
+  const int lane = threadIdx.x & 31;
+  for (int t = threadIdx.x >> 5; t < CH; t += blockDim.x >> 5) L11[t][lane] = H[(kb + t) * r + kb + lane];
+  if (threadIdx.x < CH) L11[threadIdx.x][CH] = rdiag[kb + threadIdx.x];
+  __syncthreads();
+  const int64_t i = kb + CH + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= r) return;
+  double v = H[i * r + kb + lane];
+  for (int c = 0; c < CH; ++c) {
+    const double xc = __shfl_sync(0xffffffffu, v, c) * L11[c][CH];
+    if (lane == c) v = xc;
+    else if (lane > c) v -= L11[lane][c] * xc;
+  }
+  H[i * r + kb + lane] = v;
+}
+
+// H[i][j] -= sum_t L[i][kb+t] L[j][kb+t] for kb + CH <= j <= i < r, one CTA
+// (one thread per entry) per UT x UT tile of the lower trailing matrix.
+__global__ void __launch_bounds__(UT * UT) k_chol_update(double* H, int64_t r, int64_t kb) {
+  __shared__ double Pi[UT][CH + 1], Pj[UT][CH + 1];
+  const int64_t x = blockIdx.x;
+  int64_t ti = (int64_t)((sqrt((double)(8 * x + 1)) - 1.0) / 2.0);
+  while ((ti + 1) * (ti + 2) / 2 <= x) ++ti;
+  while (ti * (ti + 1) / 2 > x) --ti;
+  const int64_t tj = x - ti * (ti + 1) / 2;
+  const int64_t i0 = kb + CH + ti * UT, j0 = kb + CH + tj * UT;
+  const int tx = threadIdx.x % UT, ty = threadIdx.x / UT;
+  for (int e = threadIdx.x; e < UT * CH; e += UT * UT) {
+    const int q = e / CH, t = e % CH;
+    Pi[q][t] = i0 + q < r ? H[(i0 + q) * r + kb + t] : 0.0;
+    Pj[q][t] = j0 + q < r ? H[(j0 + q) * r + kb + t] : 0.0;
+  }
+  __syncthreads();
+  const int64_t i = i0 + ty, j = j0 + tx;
+  if (i < r && j <= i) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < CH; ++t) acc = fma(Pi[ty][t], Pj[tx][t], acc);
+    H[i * r + j] -= acc;
+  }
+}
+
+__global__ void k_transpose(const double* __restrict__ L, int64_t r, double* __restrict__ Lt) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r * r; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t / r, b = t - a * r;
+    Lt[t] = L[b * r + a];
+  }
+}
+
+// Lane t of the warp ends with the sum over the 32 lanes of v[t].
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int c = 0; c < s; ++c) {
+      const double send = up ? v[c] : v[c + s];
+      const double keep = up ? v[c + s] : v[c];
+      v[c] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+constexpr int SOLVE_WARPS = 4;
+
+// A[i][:] = M[i][:] H^-1 (M given transposed, r x n; H = L L^T): forward
+// L z = m_i, backward L^T a_i = z, one warp per row i, 32 unknowns at a
+// time.  Per block the earlier unknowns' contribution is summed with lanes
+// over the contracted index (coalesced rows of L or L^T, a transpose-reduce
+// across the lanes), then the 32 x 32 triangle, staged in shared memory with
+// the reciprocals of its pivots, is solved with shuffles.
+
+// The 32 x 32 block of M (row-major, stride r) at (a0, a0) into B (pitch 33)
+// and the reciprocals of its diagonal (rdiag) into column 32; one warp.
+__device__ __forceinline__ void stage_block(const double* __restrict__ M, const double* __restrict__ rdiag, int64_t r,
+                                            int64_t a0, int nb, double (*B)[33], int lane) {
+  for (int t = 0; t < nb; ++t)
+    if (lane < nb) B[t][lane] = M[(a0 + t) * r + a0 + lane];
+  if (lane < nb) B[lane][32] = rdiag[a0 + lane];
+  __syncwarp();
+}
+__global__ void __launch_bounds__(32 * SOLVE_WARPS)
+    k_als_rowsolve(const double* __restrict__ L, const double* __restrict__ Lt, const double* __restrict__ rdiag,
+                   const double* __restrict__ Mt, int64_t n, int64_t r, double* __restrict__ A) {
+  extern __shared__ double ybuf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * SOLVE_WARPS + w;
+  if (i >= n) return;  // warp-uniform
+  double(*B)[33] = reinterpret_cast<double(*)[33]>(ybuf + (size_t)SOLVE_WARPS * r) + w * 32;
+  double* y = ybuf + (size_t)w * r;
+  for (int64_t c = lane; c < r; c += 32) y[c] = Mt[c * n + i];
+  __syncwarp();
+  for (int64_t a0 = 0; a0 < r; a0 += 32) {
+    const int nb = (int)(r - a0 < 32 ? r - a0 : 32);
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+    for (int64_t q = lane; q < a0; q += 32) {
+      const double yq = y[q];
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < nb) acc[t] = fma(L[(a0 + t) * r + q], yq, acc[t]);
+    }
+    double v = warp_transpose_sum(acc, lane);
+    v = lane < nb ? y[a0 + lane] - v : 0.0;
+    stage_block(L, rdiag, r, a0, nb, B, lane);
+    for (int c = 0; c < nb; ++c) {
+      const double xc = __shfl_sync(0xffffffffu, v, c) * B[c][32];
+      if (lane == c) v = xc;
+      else if (lane > c && lane < nb) v -= B[lane][c] * xc;
+    }
+    if (lane < nb) y[a0 + lane] = v;
+    __syncwarp();
+  }
+  for (int64_t a0 = (r - 1) / 32 * 32; a0 >= 0; a0 -= 32) {
+    const int nb = (int)(r - a0 < 32 ? r - a0 : 32);
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+    for (int64_t q = a0 + nb + lane; q < r; q += 32) {
+      const double yq = y[q];
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < nb) acc[t] = fma(Lt[(a0 + t) * r + q], yq, acc[t]);
+    }
+    double v = warp_transpose_sum(acc, lane);
+    v = lane < nb ? y[a0 + lane] - v : 0.0;
+    stage_block(Lt, rdiag, r, a0, nb, B, lane);
+    for (int c = nb - 1; c >= 0; --c) {
+      const double xc = __shfl_sync(0xffffffffu, v, c) * B[c][32];
+      if (lane == c) v = xc;
+      else if (lane < c) v -= B[lane][c] * xc;
+    }
+    if (lane < nb) {
+      y[a0 + lane] = v;
+      A[i * r + a0 + lane] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// Block b of ALS_PARTS: partial sums of <A, M> (A n x r, M^T r x n) into
+// part[b] and of sum G0 o G1 o G2 (r x r) into part[ALS_PARTS + b], each in a
+// fixed order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+__global__ void k_als_residual_parts(const double* __restrict__ A, const double* __restrict__ Mt, int64_t n, int64_t r,
+                                     const double* __restrict__ G0, const double* __restrict__ G1,
+                                     const double* __restrict__ G2, double* part) {
+  __shared__ double sh[32];
+  double ip = 0.0, kk = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * r; t += stride) {
+    const int64_t i = t / r, a = t - i * r;
+    ip = fma(A[t], Mt[a * n + i], ip);
+  }
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r * r; t += stride) kk += G0[t] * G1[t] * G2[t];
+  const double s1 = block_sum(ip, sh);
+  __syncthreads();
+  const double s2 = block_sum(kk, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1;
+    part[ALS_PARTS + blockIdx.x] = s2;
+  }
+}
+
+// ALS-skew factors from A1 = [A1_1 A1_2] (n x r) and B1 (n x h):
+// A2 = [B1 B1], A3 = [A1_2, -A1_1].
+__global__ void k_skew_derive(const double* __restrict__ A1, const double* __restrict__ B1, int64_t n, int64_t h,
+                              double* __restrict__ A2, double* __restrict__ A3) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * h; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / h, a = t - i * h, r = 2 * h;
+    if (A2) A2[i * r + a] = A2[i * r + h + a] = B1[t];
+    if (A3) {
+      A3[i * r + a] = A1[i * r + h + a];
+      A3[i * r + h + a] = -A1[i * r + a];
+    }
+  }
+}
+
+// B1 = mean of the two halves of a fresh A2 update.
+__global__ void k_skew_halves(const double* __restrict__ An, int64_t n, int64_t h, double* __restrict__ B1) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * h; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / h, a = t - i * h;
+    B1[t] = 0.5 * (An[i * 2 * h + a] + An[i * 2 * h + h + a]);
+  }
+}
+
+// A1 = lambda A1 + (1 - lambda) An.
+__global__ void k_momentum(double* __restrict__ A1, const double* __restrict__ An, int64_t cnt, double lambda) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+    A1[t] = lambda * A1[t] + (1.0 - lambda) * An[t];
+}
+
+unsigned grid_for(int64_t cnt) {
+  const int64_t b = (cnt + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : b > 4096 ? 4096 : b);
+}
+
+void als_free_fit(grom_als* s) {
+  for (double*& p : s->f)
+    if (p) cudaFree(p), p = nullptr;
+  for (double*& p : s->gram)
+    if (p) cudaFree(p), p = nullptr;
+  for (double** p : {&s->anew, &s->b1, &s->mt, &s->h, &s->lt, &s->rdiag, &s->part})
+    if (*p) cudaFree(*p), *p = nullptr;
+  if (s->flag) cudaFree(s->flag), s->flag = nullptr;
+  if (s->k2s) cudaFree(s->k2s), s->k2s = nullptr;
+  s->rcap = 0;
+  s->k2s_bytes = 0;
 }
 
 grom_status als_grow(grom_als* s, int64_t r) {
@@ -171,48 +438,49 @@ grom_status als_grow(grom_als* s, int64_t r) {
     s->k2s = nullptr;
     if (cudaMalloc(&s->k2s, need) != cudaSuccess) {
       cudaGetLastError();
-      s->rcap = 0;
+      als_free_fit(s);
       return fail(GROM_ERR_OOM, "grom_als_fit: device allocation");
     }
     s->k2s_bytes = need;
   }
   if (r <= s->rcap) return GROM_OK;
-  for (double*& p : s->f)
-    if (p) cudaFree(p), p = nullptr;
-  if (s->mt) cudaFree(s->mt), s->mt = nullptr;
-  if (s->gram) cudaFree(s->gram), s->gram = nullptr;
-  if (s->k2s) cudaFree(s->k2s), s->k2s = nullptr;
-  s->rcap = 0;
-  const size_t fb = (size_t)(s->n * r) * sizeof(double);
+  als_free_fit(s);
+  const size_t fb = (size_t)(s->n * r) * sizeof(double), gb = (size_t)(r * r) * sizeof(double);
   cudaError_t e = cudaSuccess;
   for (double*& p : s->f)
     if (e == cudaSuccess) e = cudaMalloc(&p, fb);
+  for (double*& p : s->gram)
+    if (e == cudaSuccess) e = cudaMalloc(&p, gb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->anew, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->b1, fb);
   if (e == cudaSuccess) e = cudaMalloc(&s->mt, fb);
-  if (e == cudaSuccess) e = cudaMalloc(&s->gram, (size_t)(r * r) * sizeof(double));
-  s->k2s_bytes = need;
-  if (e == cudaSuccess) e = cudaMalloc(&s->k2s, s->k2s_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->h, gb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->lt, gb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->rdiag, (size_t)r * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, 2 * ALS_PARTS * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&s->k2s, need);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    als_free_fit(s);
     return fail(e == cudaErrorMemoryAllocation ? GROM_ERR_OOM : GROM_ERR_CUDA, "grom_als_fit: device allocation");
   }
+  s->k2s_bytes = need;
   s->rcap = r;
   return GROM_OK;
 }
 
-// Gram matrix of device factor q into host G.
-grom_status gram_of(grom_als* s, int q, int64_t r, std::vector<double>& G) {
+// Gram matrix of factor q (on the device).
+grom_status gram_of(grom_als* s, int q, int64_t r) {
   dim3 grid((unsigned)((r + 15) / 16), (unsigned)((r + 15) / 16));
-  k_gram<<<grid, dim3(16, 16), 0, s->stream>>>(s->f[q], s->n, r, s->gram);
+  k_gram<<<grid, dim3(16, 16), 0, s->stream>>>(s->f[q], s->n, r, s->gram[q]);
   GROM_CUDA_TRY(cudaGetLastError());
-  G.resize((size_t)(r * r));
-  GROM_CUDA_TRY(cudaMemcpyAsync(G.data(), s->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return GROM_OK;
 }
 
 // MTTKRP of layout m (0, 1, 2) with factors P (middle index) and Q (inner
-// index) on the device into host Mt (r x n).
-grom_status mttkrp(grom_als* s, int m, int fp, int fq, int64_t r, std::vector<double>& Mt) {
+// index) into s->mt (r x n).
+grom_status mttkrp(grom_als* s, int m, int fp, int fq, int64_t r) {
   const K2Plan pl = k2_plan(s->n, (int)r, s->sm_count);
   K2Args a{};
   a.fp = s->f[fp];
@@ -226,8 +494,6 @@ grom_status mttkrp(grom_als* s, int m, int fp, int fq, int64_t r, std::vector<do
   a.ev0 = s->ev0;
   a.ev1 = s->ev1;
   GROM_CUDA_TRY(k2_launch(pl, &s->tmap[m], a, s->stream));
-  Mt.resize((size_t)(r * s->n));
-  GROM_CUDA_TRY(cudaMemcpyAsync(Mt.data(), s->mt, Mt.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
   float ms = 0.f;
   GROM_CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
@@ -242,53 +508,78 @@ grom_status mttkrp(grom_als* s, int m, int fp, int fq, int64_t r, std::vector<do
   return GROM_OK;
 }
 
-// The normal-equation update A = M H^-1, H = Ga o Gb + ridge max diag(Ga o Gb) I.
-grom_status ls_update(grom_als* s, const std::vector<double>& Mt, const std::vector<double>& Ga,
-                      const std::vector<double>& Gb, int64_t n, int64_t r, double ridge, std::vector<double>& A) {
+// Cholesky of s->h in place (lower); false if a pivot broke down.
+grom_status cholesky_dev(grom_als* s, int64_t r, bool* ok) {
+  GROM_CUDA_TRY(cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+  for (int64_t kb = 0; kb < r; kb += CH) {
+    k_chol_diag<<<1, CH * CH, 0, s->stream>>>(s->h, r, kb, s->rdiag, s->flag);
+    if (kb + CH < r) {
+      const int64_t rows = r - kb - CH, m = (rows + UT - 1) / UT;
+      k_chol_panel<<<(unsigned)((rows + 7) / 8), 256, 0, s->stream>>>(s->h, r, kb, s->rdiag);
+      k_chol_update<<<(unsigned)(m * (m + 1) / 2), UT * UT, 0, s->stream>>>(s->h, r, kb);
+    }
+  }
+  GROM_CUDA_TRY(cudaGetLastError());
+  int flag = 0;
+  GROM_CUDA_TRY(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  *ok = flag == 0;
+  return GROM_OK;
+}
+
+// The normal-equation update dst = M H^-1 (M = s->mt), H = Ga o Gb +
+// ridge max diag(Ga o Gb) I.  If H is numerically singular (ALS on a tensor
+// dominated by a few components drives the factor columns towards each
+// other), retry with an extra mu max diag I, mu = 1e-12 growing 100x up to
+// three times.
+grom_status ls_update(grom_als* s, const double* Ga, const double* Gb, int64_t r, double ridge, double* dst) {
   const auto t0 = std::chrono::steady_clock::now();
-  // Cholesky of H = Ga o Gb; if H is numerically singular (ALS on a tensor
-  // dominated by a few components drives the factor columns towards each
-  // other), retry with a ridge mu I, mu = 1e-12 max diag(H), growing 100x up
-  // to three times
-  std::vector<double> H0((size_t)(r * r)), H;
-  double dmax = 0.0;
-  for (size_t q = 0; q < H0.size(); ++q) H0[q] = Ga[q] * Gb[q];
-  for (int64_t a = 0; a < r; ++a) dmax = std::max(dmax, H0[a * r + a]);
-  for (int64_t a = 0; a < r; ++a) H0[a * r + a] += ridge * dmax;
+  const int64_t n = s->n;
   bool ok = false;
   double mu = 0.0;
+  grom_status st;
   for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
-    H = H0;
-    for (int64_t a = 0; a < r; ++a) H[a * r + a] += mu;
-    ok = cholesky(H, r);
-    mu = mu == 0.0 ? 1e-12 * dmax : mu * 100.0;
+    k_als_normal<<<grid_for(r * r), 256, 0, s->stream>>>(Ga, Gb, r, ridge + mu, s->h);
+    if ((st = cholesky_dev(s, r, &ok))) return st;
+    mu = mu == 0.0 ? 1e-12 : mu * 100.0;
   }
   if (!ok) return fail(GROM_ERR_INVALID_ARG, "grom_als_fit: a Gram matrix is not positive definite");
-  solve_rows(H, r, Mt, n, A);
+  k_transpose<<<grid_for(r * r), 256, 0, s->stream>>>(s->h, r, s->lt);
+  const size_t smem = (size_t)SOLVE_WARPS * (r + 32 * 33) * sizeof(double);
+  if (smem > 48 * 1024)
+    GROM_CUDA_TRY(cudaFuncSetAttribute(k_als_rowsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_als_rowsolve<<<(unsigned)((n + SOLVE_WARPS - 1) / SOLVE_WARPS), 32 * SOLVE_WARPS, smem, s->stream>>>(
+      s->h, s->lt, s->rdiag, s->mt, n, r, dst);
+  GROM_CUDA_TRY(cudaGetLastError());
+  GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
   s->solve_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return GROM_OK;
 }
 
-grom_status put(grom_als* s, int q, const std::vector<double>& A) {
-  GROM_CUDA_TRY(cudaMemcpyAsync(s->f[q], A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+// Relative residual ||X - [[A1, A2, A3]]|| / ||X|| from <X, K> = <A1, M_1>
+// (s->mt holds the mode-1 MTTKRP of the current factors) and
+// ||K||^2 = sum G1 o G2 o G3.
+grom_status residual_of(grom_als* s, int64_t r, double* out) {
+  k_als_residual_parts<<<ALS_PARTS, 256, 0, s->stream>>>(s->f[0], s->mt, s->n, r, s->gram[0], s->gram[1], s->gram[2],
+                                                        s->part);
+  GROM_CUDA_TRY(cudaGetLastError());
+  double ph[2 * ALS_PARTS];
+  GROM_CUDA_TRY(cudaMemcpyAsync(ph, s->part, sizeof(ph), cudaMemcpyDeviceToHost, s->stream));
   GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double ip = 0.0, kk = 0.0;
+  for (int q = 0; q < ALS_PARTS; ++q) {
+    ip += ph[q];
+    kk += ph[ALS_PARTS + q];
+  }
+  const double r2 = s->xnorm2 - 2.0 * ip + kk;
+  *out = std::sqrt(std::max(r2, 0.0) / s->xnorm2);
   return GROM_OK;
 }
 
-double relres(const grom_als* s, double ip, const std::vector<double>& G0, const std::vector<double>& G1,
-              const std::vector<double>& G2) {
-  double kk = 0.0;
-  for (size_t q = 0; q < G0.size(); ++q) kk += G0[q] * G1[q] * G2[q];
-  const double r2 = s->xnorm2 - 2.0 * ip + kk;
-  return std::sqrt(std::max(r2, 0.0) / s->xnorm2);
-}
-
-// <X, [[A1, A2, A3]]> = sum_{i,r} A_m[i][r] MTTKRP_m[i][r].
-double inner(const std::vector<double>& A, const std::vector<double>& Mt, int64_t n, int64_t r) {
-  double s = 0.0;
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t a = 0; a < r; ++a) s += A[i * r + a] * Mt[a * n + i];
-  return s;
+grom_status copy(grom_als* s, void* dst, const void* src, size_t bytes) {
+  GROM_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s->stream));
+  GROM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return GROM_OK;
 }
 
 }  // namespace
@@ -376,73 +667,55 @@ grom_status grom_als_fit(grom_als* s, int32_t rank, int32_t method, int32_t iter
   const int64_t n = s->n, r = rank, h = r / 2;
   grom_status st = als_grow(s, r);
   if (st) return st;
-  std::vector<double> F[3], G[3], Mt, Anew;
+  const size_t fbytes = (size_t)(n * r) * sizeof(double);
   if (method == GROM_ALS_PLAIN) {
-    F[0].assign(fa, fa + n * r);
-    F[1].assign(fb, fb + n * r);
-    F[2].assign(fc, fc + n * r);
+    if ((st = copy(s, s->f[0], fa, fbytes)) || (st = copy(s, s->f[1], fb, fbytes)) ||
+        (st = copy(s, s->f[2], fc, fbytes)))
+      return st;
     for (int q = 0; q < 3; ++q)
-      if ((st = put(s, q, F[q])) || (st = gram_of(s, q, r, G[q]))) return st;
+      if ((st = gram_of(s, q, r))) return st;
     for (int it = 0; it < iters; ++it) {
       for (int m = 0; m < 3; ++m) {
         // layout m: rows of mode m; P, Q = the factors of its middle and inner index
         const int fp = m == 0 ? 1 : 0, fq = m == 2 ? 1 : 2;
-        if ((st = mttkrp(s, m, fp, fq, r, Mt))) return st;
-        if ((st = ls_update(s, Mt, G[fp], G[fq], n, r, ridge, F[m]))) return st;
-        if ((st = put(s, m, F[m])) || (st = gram_of(s, m, r, G[m]))) return st;
+        if ((st = mttkrp(s, m, fp, fq, r)) || (st = ls_update(s, s->gram[fp], s->gram[fq], r, ridge, s->f[m])) ||
+            (st = gram_of(s, m, r)))
+          return st;
       }
       // <X, K> from a fresh mode-1 MTTKRP with the final factors: the M the
       // last update used carries the noise that update amplified along the
       // near-null directions of its normal matrix, and would hide it
-      if (residual) {
-        if ((st = mttkrp(s, 0, 1, 2, r, Mt))) return st;
-        residual[it] = relres(s, inner(F[0], Mt, n, r), G[0], G[1], G[2]);
-      }
+      if (residual && ((st = mttkrp(s, 0, 1, 2, r)) || (st = residual_of(s, r, &residual[it])))) return st;
     }
-    std::memcpy(fa, F[0].data(), F[0].size() * sizeof(double));
-    std::memcpy(fb, F[1].data(), F[1].size() * sizeof(double));
-    std::memcpy(fc, F[2].data(), F[2].size() * sizeof(double));
+    if ((st = copy(s, fa, s->f[0], fbytes)) || (st = copy(s, fb, s->f[1], fbytes)) || (st = copy(s, fc, s->f[2], fbytes)))
+      return st;
     return GROM_OK;
   }
-  // ALS-skew: A1 = [A1_1 A1_2], A2 = [B1 B1], A3 = [A1_2, -A1_1]
-  std::vector<double> A1(fa, fa + n * r), B1(fb, fb + n * h);
-  auto derive = [&]() {
-    F[0] = A1;
-    F[1].resize((size_t)(n * r));
-    F[2].resize((size_t)(n * r));
-    for (int64_t i = 0; i < n; ++i)
-      for (int64_t a = 0; a < h; ++a) {
-        F[1][i * r + a] = F[1][i * r + h + a] = B1[i * h + a];
-        F[2][i * r + a] = A1[i * r + h + a];
-        F[2][i * r + h + a] = -A1[i * r + a];
-      }
-  };
-  derive();
+  // ALS-skew: A1 = [A1_1 A1_2] (factor 0), A2 = [B1 B1], A3 = [A1_2, -A1_1]
+  const unsigned gh = grid_for(n * h);
+  if ((st = copy(s, s->f[0], fa, fbytes)) || (st = copy(s, s->b1, fb, (size_t)(n * h) * sizeof(double)))) return st;
+  k_skew_derive<<<gh, 256, 0, s->stream>>>(s->f[0], s->b1, n, h, s->f[1], s->f[2]);
+  GROM_CUDA_TRY(cudaGetLastError());
   for (int q = 0; q < 3; ++q)
-    if ((st = put(s, q, F[q])) || (st = gram_of(s, q, r, G[q]))) return st;
+    if ((st = gram_of(s, q, r))) return st;
   for (int it = 0; it < iters; ++it) {
     // A2 as in ALS (layout X2: P = A1, Q = A3), halves averaged
-    if ((st = mttkrp(s, 1, 0, 2, r, Mt)) || (st = ls_update(s, Mt, G[0], G[2], n, r, ridge, Anew))) return st;
-    for (int64_t i = 0; i < n; ++i)
-      for (int64_t a = 0; a < h; ++a) B1[i * h + a] = 0.5 * (Anew[i * r + a] + Anew[i * r + h + a]);
-    derive();
-    if ((st = put(s, 1, F[1])) || (st = gram_of(s, 1, r, G[1]))) return st;
+    if ((st = mttkrp(s, 1, 0, 2, r)) || (st = ls_update(s, s->gram[0], s->gram[2], r, ridge, s->anew))) return st;
+    k_skew_halves<<<gh, 256, 0, s->stream>>>(s->anew, n, h, s->b1);
+    k_skew_derive<<<gh, 256, 0, s->stream>>>(s->f[0], s->b1, n, h, s->f[1], nullptr);
+    GROM_CUDA_TRY(cudaGetLastError());
+    if ((st = gram_of(s, 1, r))) return st;
     for (int sub = 0; sub < subiters; ++sub) {
       // A1_next with A2, A3 fixed (layout X1: P = A2, Q = A3), then momentum
-      if ((st = mttkrp(s, 0, 1, 2, r, Mt)) || (st = ls_update(s, Mt, G[1], G[2], n, r, ridge, Anew))) return st;
-      for (size_t q = 0; q < A1.size(); ++q) A1[q] = lambda * A1[q] + (1.0 - lambda) * Anew[q];
-      derive();
-      if ((st = put(s, 0, F[0])) || (st = put(s, 2, F[2])) || (st = gram_of(s, 0, r, G[0])) ||
-          (st = gram_of(s, 2, r, G[2])))
-        return st;
+      if ((st = mttkrp(s, 0, 1, 2, r)) || (st = ls_update(s, s->gram[1], s->gram[2], r, ridge, s->anew))) return st;
+      k_momentum<<<grid_for(n * r), 256, 0, s->stream>>>(s->f[0], s->anew, n * r, lambda);
+      k_skew_derive<<<gh, 256, 0, s->stream>>>(s->f[0], s->b1, n, h, nullptr, s->f[2]);
+      GROM_CUDA_TRY(cudaGetLastError());
+      if ((st = gram_of(s, 0, r)) || (st = gram_of(s, 2, r))) return st;
     }
-    if (residual) {
-      if ((st = mttkrp(s, 0, 1, 2, r, Mt))) return st;
-      residual[it] = relres(s, inner(F[0], Mt, n, r), G[0], G[1], G[2]);
-    }
+    if (residual && ((st = mttkrp(s, 0, 1, 2, r)) || (st = residual_of(s, r, &residual[it])))) return st;
   }
-  std::memcpy(fa, A1.data(), A1.size() * sizeof(double));
-  std::memcpy(fb, B1.data(), B1.size() * sizeof(double));
+  if ((st = copy(s, fa, s->f[0], fbytes)) || (st = copy(s, fb, s->b1, (size_t)(n * h) * sizeof(double)))) return st;
   return GROM_OK;
 }
 
@@ -463,11 +736,7 @@ grom_status grom_als_destroy(grom_als* s) {
   if (s->ev1) cudaEventDestroy(s->ev1);
   for (auto p : s->x)
     if (p) cudaFree(p);
-  for (auto p : s->f)
-    if (p) cudaFree(p);
-  if (s->mt) cudaFree(s->mt);
-  if (s->gram) cudaFree(s->gram);
-  if (s->k2s) cudaFree(s->k2s);
+  als_free_fit(s);
   if (s->err) cudaFree(s->err);
   delete s;
   return GROM_OK;
