@@ -753,7 +753,7 @@ def main():
                     "note": "one MTTKRP per iteration is the residual's <X, K>",
                     "mttkrp_alg_tflops": flops / (per * 1e-3) / 1e12,
                     "mttkrp_tc_frac_of_sustained_bf16": flops / (per * 1e-3) / 1e12 / tc_sustained,
-                    "host_solve_ms_per_iteration": solve / args.als_iters,
+                    "solve_ms_per_iteration": solve / args.als_iters,
                     "relative_residual": [float(x) for x in res],
                     "init": "seeded normal factors / sqrt(N) (stream 30-32)"}
         als.close()

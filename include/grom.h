@@ -348,8 +348,9 @@ grom_status grom_selftest_timeout(grom_rom* rom, int64_t limit_ns);
  * normal equations, A_m = MTTKRP_m (Hadamard product of the other two Gram
  * matrices)^-1; the MTTKRP X_(m) (P kr Q) runs on the tensor cores (BF16
  * tensor, Khatri-Rao product of the FP32 factors split into BF16 hi/lo
- * parts, FP32 accumulation, split sums in FP64); the Gram matrices are FP64
- * on the device and the rank x rank SPD solves FP64 Cholesky on the host. */
+ * parts, FP32 accumulation, split sums in FP64); the Gram matrices and the
+ * rank x rank SPD solves (blocked Cholesky, then two triangular solves per
+ * row) are FP64 on the device, where the factors stay for the whole fit. */
 typedef struct grom_als grom_als;
 #define GROM_ALS_PLAIN 0
 #define GROM_ALS_SKEW 1
@@ -387,7 +388,8 @@ grom_status grom_als_fit(grom_als* als, int32_t rank, int32_t method, int32_t it
                          double ridge, double* fa, double* fb, double* fc, double* residual);
 /* Time spent since the previous call: summed device time of the MTTKRP
  * launches (CUDA events around each tensor-core launch), their number, and
- * the host time of the SPD solves (ms).  Resets the counters. */
+ * the wall time of the SPD solves, each from its first launch to its end on
+ * the device (ms).  Resets the counters. */
 grom_status grom_als_stats(grom_als* als, double* mttkrp_ms, int64_t* mttkrp_calls, double* solve_ms);
 grom_status grom_als_destroy(grom_als* als);
 
