@@ -381,7 +381,7 @@ class Als:
         return fs, res
 
     def stats(self):
-        """(MTTKRP device ms, MTTKRP launches, host solve ms) since the last call."""
+        """(MTTKRP device ms, MTTKRP launches, SPD solve ms) since the last call."""
         ms, calls, solve = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
         _check(load().grom_als_stats(self._h, ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(solve)))
         return ms.value, calls.value, solve.value
