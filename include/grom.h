@@ -222,17 +222,21 @@ grom_status grom_sync(grom_rom* rom);
 /* Bytes of device memory held by the ROM (operators, caches and scratch). */
 int64_t grom_rom_bytes(const grom_rom* rom);
 
-/* Choice of the dense-contraction kernel (full form).  AUTO picks the
- * tensor-core kernel for BF16 storage and batches above 8 trajectories, else
- * the streaming kernel. */
+/* Choice of the contraction kernel.  AUTO picks the tensor-core kernel for
+ * BF16 storage and batches above 8 trajectories (full form) or of 32 and more
+ * (CP forms), else the streaming (full) or SIMT (CP) kernels. */
 #define GROM_KERNEL_AUTO 0
-#define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass   */
+#define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass;
+                                CP forms: the SIMT kernels (K3, K3g)                        */
 #define GROM_KERNEL_TENSOR 2 /* BF16 storage only.  Dense layout, K2: tcgen05 GEMM over the
                                 Khatri-Rao product of the states (Sec. 2.2, eq. Cu with the
                                 mode-1 matricisation).  Skew-packed layout, K2P: the factored
                                 form, one tcgen05 GEMM D_i = P_i^T U^T per test index i over
                                 the stored half, then c_i += D_i u_k and c_k -= D_i u_i for
-                                every stored pair (i, k); half the bytes and MMA work of K2  */
+                                every stored pair (i, k); half the bytes and MMA work of K2.
+                                CP forms, K3T: the projections [B C]^T X (skew: [V W U]^T X)
+                                and the expansion A Z (skew: [U, -W] Z) of the batch as two
+                                tcgen05 GEMMs (Sec. 3.1, eq. tc_ap; Sec. 3.3)              */
 grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
 
 /* ------------------------------------------------------------ serving

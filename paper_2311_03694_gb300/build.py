@@ -41,6 +41,7 @@ SOURCES = [
     "k1pp_bf16.cu",
     "k2_tc.cu",
     "k2p_tc.cu",
+    "k3t_tc.cu",
     "serve.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -216,6 +216,7 @@ static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
+                  r->k3t_factors, r->k3t_scratch,
                   r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch,
                   r->k2_tiles};
   for (void* p : ptrs)
@@ -267,6 +268,14 @@ static bool is_cp(const grom_rom* r) { return r->form == GROM_FORM_CP || r->form
 
 static bool use_k3g(const grom_rom* r, int batch) {
   return is_cp(r) && batch >= K3G_MIN_BATCH && r->k3g_scratch;
+}
+
+// K3T: the batched CP form on the tensor cores (BF16 factors)
+static bool use_k3t(const grom_rom* r, int batch) {
+  if (!is_cp(r) || !r->k3t_factors) return false;
+  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
+  if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
+  return batch >= K3T_MIN_BATCH;
 }
 
 static K1Args k1_args(grom_rom* r) {
@@ -505,6 +514,25 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
                                           k3g_scratch_bytes(n, rp, r->max_batch, r->storage, r->sm_count),
                                           r->stream) != cudaSuccess)
       return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    if (r->storage == GROM_BF16) {
+      // the factors again, laid out for the tensor-core GEMMs (K3T), and the
+      // scratch of the largest plan over the batch sizes this ROM accepts
+      if ((st = dmalloc(&r->k3t_factors, k3t_factor_bytes(n, r->rank, r->form), &r->total_bytes))) return bail(st);
+      uint8_t* ft = static_cast<uint8_t*>(r->k3t_factors);
+      const K3TPlan p0 = k3t_plan(n, r->rank, r->form, 16, r->sm_count);
+      uint8_t* ae = ft + (size_t)p0.m1 * p0.np * 2;
+      if (k3t_build_factors(r->op, r->op + r->panel_bytes, r->op + 2 * r->panel_bytes, n, rp, r->rank, r->form, ft,
+                            ae, r->stream) != cudaSuccess ||
+          !k3t_make_tmaps(&r->k3t_tmap_ft, &r->k3t_tmap_ae, ft, ae, n, r->rank, r->form))
+        return bail(cuda_fail(cudaGetLastError(), "grom_create: tensor-core factor copies"));
+      size_t need = 0;
+      for (int b = 16;; b = b < 128 ? b + 16 : b + 128) {
+        const int bb = b < r->max_batch ? b : r->max_batch;
+        need = std::max(need, k3t_scratch_bytes(k3t_plan(n, r->rank, r->form, bb, r->sm_count)));
+        if (bb >= r->max_batch) break;
+      }
+      if ((st = dmalloc(&r->k3t_scratch, need, &r->total_bytes))) return bail(st);
+    }
     // persistent stepper (its grid-barrier word starts at zero)
     const size_t kp = k3p_scratch_bytes(n, rp, r->storage, r->sm_count);
     if ((st = dmalloc(&r->k3p_scratch, kp, &r->total_bytes))) return bail(st);
@@ -727,8 +755,10 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     cudaEvent_t e0, e1;
     if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
     if (e0) prof_record(e0, r->stream);
-    e = use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
-                          : k3_launch(r->k3, r->storage, a, batch, r->stream);
+    e = use_k3t(r, batch) ? k3t_launch(k3t_plan(r->n, r->rank, r->form, batch, r->sm_count), &r->k3t_tmap_ft,
+                                       &r->k3t_tmap_ae, a, batch, r->k3t_scratch, r->err, r->stream)
+        : use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
+                            : k3_launch(r->k3, r->storage, a, batch, r->stream);
     if (e1) prof_record(e1, r->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear launch");
@@ -853,8 +883,12 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   cudaEvent_t e0, e1;
   if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
   if (e0) prof_record(e0, strm);
-  cudaError_t e = use_k3g(r, t->batch) ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
-                                       : k3_launch(r->k3, r->storage, a, t->batch, strm);
+  cudaError_t e = use_k3t(r, t->batch)
+                      ? k3t_launch(k3t_plan(r->n, r->rank, r->form, t->batch, r->sm_count), &r->k3t_tmap_ft,
+                                   &r->k3t_tmap_ae, a, t->batch, r->k3t_scratch, r->err, strm)
+                  : use_k3g(r, t->batch)
+                      ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
+                      : k3_launch(r->k3, r->storage, a, t->batch, strm);
   if (e1 && e == cudaSuccess) e = prof_record(e1, strm);
   return e;
 }
@@ -898,7 +932,7 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   grom_rom* r = t->rom;
   StepArgs a = step_args(t, energy, invariant);
   const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch) && !use_k2p(r, t->batch);
-  const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch);
+  const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch) && !use_k3t(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
     if (fused_k3) {
@@ -939,7 +973,7 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
   // CP forms with a few trajectories: all steps in one persistent launch
   if (r->diagonal && is_cp(r) && r->k3p_scratch && !t->active && !r->prof &&
-      t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 &&
+      t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 && !use_k3t(r, t->batch) &&
       k3p_fits(r->n, r->k3.rb, r->storage, t->batch, r->sm_count)) {
     StepArgs a = step_args(t, energy, invariant);
     cudaError_t e = k3p_launch(r->op, r->op + r->panel_bytes, r->op + 2 * r->panel_bytes, r->form, r->n, r->k3.rb,
@@ -1133,8 +1167,9 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: null rom");
   if (kernel < GROM_KERNEL_AUTO || kernel > GROM_KERNEL_TENSOR)
     return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
-  if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok))
-    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernels need the BF16 full form");
+  if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok) &&
+      !(is_cp(r) && r->k3t_factors))
+    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernels need BF16 storage (full or CP form)");
   if (kernel == GROM_KERNEL_TENSOR) {
     grom_status st = build_k2_tiles(r);
     if (st) return st;

@@ -167,6 +167,28 @@ size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int 
 cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
                        int sm_count, cudaStream_t s);
 constexpr int K3G_MIN_BATCH = 16;
+// Batched CP form on the tensor cores (BF16 factors): projections and
+// expansion as two tcgen05 GEMMs over copies of the factors laid out for them.
+struct K3TPlan {
+  int64_t n, np, r, rp;  // rank padded to 64
+  int nseg, nz;          // projection segments (2 general, 3 skew), expansion blocks (1, 2)
+  int64_t m1, k1, m2, k2;
+  int btile, ctiles;     // trajectories per column tile (<= 128), column tiles
+  int64_t bp;
+  int s1, s2;            // K splits of the two GEMMs
+  int stages, tmem_cols;
+  size_t smem;
+};
+constexpr int K3T_MIN_BATCH = 32;
+K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count);
+size_t k3t_scratch_bytes(const K3TPlan& p);
+size_t k3t_factor_bytes(int64_t n, int64_t r, int form);
+cudaError_t k3t_build_factors(const void* fa, const void* fb, const void* fc, int64_t n, int64_t rb, int64_t r,
+                              int form, void* ft, void* ae, cudaStream_t s);
+bool k3t_make_tmaps(CUtensorMap* m_ft, CUtensorMap* m_ae, const void* ft, const void* ae, int64_t n, int64_t r,
+                    int form);
+cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a, int batch,
+                       void* scratch, int* err, cudaStream_t s);
 // Persistent cooperative CPD-ROM stepper for a few trajectories.
 size_t k3p_scratch_bytes(int64_t n, int64_t rp, int storage, int sm_count);
 int k3p_max_batch(int storage);
@@ -317,6 +339,9 @@ struct grom_rom {
   CUtensorMap k2_tmap_tiled;         // its TMA descriptor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
+  void* k3t_factors = nullptr;       // batched CP on tensor cores: FT | AE (BF16)
+  void* k3t_scratch = nullptr;
+  CUtensorMap k3t_tmap_ft, k3t_tmap_ae;
   void* k3p_scratch = nullptr;       // persistent CP stepper: partials, h, barrier
   size_t k2_scratch_bytes = 0;
   bool prof = false;                 // kernel timing enabled
