@@ -900,6 +900,11 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
   a.batch = t->batch;
   a.order = r->order;
   a.dt = r->dt;
+  a.inv_dt = 1.0 / r->dt;
+  // beta_1 .. beta_k of BDFk over dt (the same products the device forms)
+  static const double kBetaQ[3][3] = {{-1.0, 0.0, 0.0}, {-2.0, 0.5, 0.0}, {-3.0, 1.5, -1.0 / 3.0}};
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 3; ++q) a.bdt[k][q] = kBetaQ[k][q] * a.inv_dt;
   a.nu = r->nu;
   a.hist = t->hist;
   a.hist_stride = 6 * (int64_t)r->n;
@@ -920,7 +925,10 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
   a.first_bad = t->err + 1;
   a.red = t->red;
   a.cnt = t->cnt;
-  a.nblk = step_mc_blocks(r->n);
+  // large batches: four elements per thread, so the per-block FP64
+  // reduction of energy and invariant is paid once per four elements
+  a.ept = t->batch >= 64 ? 4 : 1;
+  a.nblk = (int)((r->n + (int64_t)STEP_MC_THREADS * a.ept - 1) / ((int64_t)STEP_MC_THREADS * a.ept));
   a.active = t->active;
   a.active_rw = t->active;
   a.steps_left = t->steps_left;

@@ -203,6 +203,8 @@ struct StepArgs {
   int batch;
   int order;
   double dt, nu;
+  double inv_dt;         // 1 / dt, rounded once on the host (FP64 division is slow on the device)
+  double bdt[3][3];      // beta_{q+1} / dt of BDF order k (rows k = 1..3), from the host
   double* hist;          // batch x 6 x n ring (u slots 0..2, n slots 3..5)
   int64_t hist_stride;   // 6 * n
   int64_t* taken;        // batch
@@ -226,6 +228,7 @@ struct StepArgs {
   double* red;              // batch x nblk x 2
   unsigned int* cnt;        // batch (zero between launches)
   int nblk;                 // CTAs per trajectory
+  int ept;                  // elements per thread of the multi-CTA diagonal step
   // serving: per-trajectory remaining steps; a trajectory whose count
   // reaches zero is deactivated (active[b] = 0) by the step that ends it
   int32_t* steps_left;      // nullable

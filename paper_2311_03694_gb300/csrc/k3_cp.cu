@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256) k3_expand_kernel(const K3Shape sh, const 
     const double mb = st.mass_diag ? st.mass_diag[i] : 1.0;
     const double ld = st.lin_diag ? st.lin_diag[i] : 0.0;
     const double f = st.forcing ? st.forcing[i] : 0.0;
-    const double inv_dt = 1.0 / st.dt;
+    const double inv_dt = st.inv_dt;
     double ext = 0.0, bdf = 0.0, u0 = 0.0;
     for (int q = 0; q < k; ++q) {
       const int64_t m = ((l - q) % 3 + 3) % 3;

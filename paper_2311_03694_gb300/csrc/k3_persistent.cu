@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k3p_kernel(const KPArgs p) {
   int64_t l0[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) l0[b] = b < p.batch ? st.taken[b] : 0;
-  const double inv_dt = 1.0 / st.dt;
+  const double inv_dt = st.inv_dt;
   // the owned rows' history stays in shared memory for the whole launch
   for (int t = threadIdx.x; t < NB * (int)(i1 - i0) * 6; t += KP_THREADS) {
     const int b = t / ((int)(i1 - i0) * 6), rem = t % ((int)(i1 - i0) * 6), ri = rem / 6, q = rem % 6;

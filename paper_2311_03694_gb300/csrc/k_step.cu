@@ -46,7 +46,8 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
   atomicMin(a.first_bad, b);
 }
 
-// Diagonal step spread over nblk CTAs per trajectory (STEP_MC_THREADS each).
+// Diagonal step spread over nblk CTAs per trajectory (STEP_MC_THREADS each,
+// a.ept elements per thread, strided by the block size).
 // Per-CTA energy/invariant partials are summed in CTA order by the last CTA
 // of the trajectory to arrive (arrival counter, no waiting), which also
 // advances the step count.  With k1 set, the K1 partials of the element are
@@ -64,12 +65,14 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
   const int64_t l = a.taken[b];
   const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
   double* h = a.hist + b * a.hist_stride;
-  const int64_t i = (int64_t)blockIdx.x * STEP_MC_THREADS + threadIdx.x;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  const bool sums = a.energy || a.invariant;  // energy and invariant asked for
   double e_part = 0.0, i_part = 0.0;
   int my_bad = 0;
-  if (i < n) {
+  for (int e = 0; e < a.ept; ++e) {
+    const int64_t i = ((int64_t)blockIdx.x * a.ept + e) * STEP_MC_THREADS + threadIdx.x;
+    if (i >= n) break;
     double nl;
     if (fuse) {
       // K1 finalize: partials of every CTA whose chunk range covers test index i, in CTA order
@@ -87,10 +90,21 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
     } else {
       nl = h[(3 + l % 3) * n + i];
     }
-    step_elem(a, h, n, l, k, i, nl, e_part, i_part, my_bad);
+    double ep, ip;
+    int eb;
+    step_elem(a, h, n, l, k, i, nl, ep, ip, eb, sums);
+    if (sums) {
+      e_part += ep;
+      i_part += ip;
+    }
+    my_bad |= eb;
   }
   if (my_bad) bad = 1;
-  block_sum2(e_part, i_part, sh);
+  if (sums) {
+    block_sum2(e_part, i_part, sh);
+  } else {
+    __syncthreads();  // `bad` complete before thread 0 reads it
+  }
   if (threadIdx.x == 0) {
     if (bad) report_nonfinite(a, b);
     double* r = a.red + ((int64_t)b * a.nblk + blockIdx.x) * 2;
@@ -241,7 +255,7 @@ __global__ void k_step_prep(const StepArgs a) {
     const int64_t m = ((l - q) % 3 + 3) % 3;
     const double uq = h[m * n + i];
     y -= c_alpha[k - 1][q] * (h[(3 + m) * n + i] + f);
-    t += c_beta[k - 1][q + 1] / a.dt * uq;
+    t += c_beta[k - 1][q + 1] * a.inv_dt * uq;
     z += c_alpha[k - 1][q] * uq;
   }
   if (!a.mass) y -= (a.mass_diag ? a.mass_diag[i] : 1.0) * t;
