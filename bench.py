@@ -727,7 +727,7 @@ def main():
                 batched["B%d_cpd_%s" % (B, storage)] = {
                     "ms_per_step": cms, "trajectory_steps_per_s": B * 1e3 / cms,
                     "alg_tflops": cflops / (cms * 1e-3) / 1e12,
-                    "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 32
+                    "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
                                else "k3g project/expand (register-tiled GEMMs)" if B >= 16 else "k3 project/expand")}
                 ctr.close()
                 crom.close()

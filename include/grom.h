@@ -223,7 +223,7 @@ grom_status grom_sync(grom_rom* rom);
 int64_t grom_rom_bytes(const grom_rom* rom);
 
 /* Choice of the contraction kernel.  AUTO picks the tensor-core kernel for
- * BF16 storage and batches above 8 trajectories (full form) or of 32 and more
+ * BF16 storage and batches above 8 trajectories (full form) or of 16 and more
  * (CP forms), else the streaming (full) or SIMT (CP) kernels. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass;

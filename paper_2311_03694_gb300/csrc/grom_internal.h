@@ -179,7 +179,7 @@ struct K3TPlan {
   int stages, tmem_cols;
   size_t smem;
 };
-constexpr int K3T_MIN_BATCH = 32;
+constexpr int K3T_MIN_BATCH = 16;
 K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count);
 size_t k3t_scratch_bytes(const K3TPlan& p);
 size_t k3t_factor_bytes(int64_t n, int64_t r, int form);

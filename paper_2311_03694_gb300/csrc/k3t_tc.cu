@@ -180,12 +180,13 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
   }
 }
 
-// States into BF16 hi/lo rows xh, xl (bp x np), zero for padding and inactive trajectories.
+// States into BF16 hi/lo rows xh, xl (bp x np), zero for padding and inactive
+// trajectories; grid (np / 256, bp).
 __global__ void k3t_prep(const K3Args a, int64_t n, int64_t np, int64_t bp, int batch, __nv_bfloat16* xh,
                          __nv_bfloat16* xl) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= bp * np) return;
-  const int64_t b = t / np, k = t - b * np;
+  const int64_t b = blockIdx.y, k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int64_t t = b * np + k;
   float v = 0.f;
   if (b < batch && k < n && (a.active == nullptr || a.active[b])) {
     const double* ub = a.taken ? a.hist + b * a.hist_stride + (a.taken[b] % 3) * n : a.u + b * a.u_stride;
@@ -234,11 +235,14 @@ __global__ void k3t_hadamard(const float* __restrict__ d1, int s1, int64_t m1, i
 }
 
 // c[b][i] = sum over splits of d2[split][i][b], in split order, in FP64.
+// Consecutive threads take consecutive b: the reads are coalesced, the
+// writes land 6 n doubles apart (a 32 x 32 shared-memory transpose for
+// coalesced writes was measured slower: a quarter of the threads).
 __global__ void k3t_finish(const float* __restrict__ d2, int s2, int64_t n, int64_t m2, int64_t bp, const K3Args a,
                            int batch) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)batch * n) return;
-  const int64_t i = t / batch, b = t - i * batch;  // consecutive threads: consecutive b
+  const int64_t i = t / batch, b = t - i * batch;
   if (a.active && !a.active[b]) return;
   double s = 0.0;
   for (int q = 0; q < s2; ++q) s += (double)d2[((int64_t)q * m2 + i) * bp + b];
@@ -398,8 +402,7 @@ cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensor
   __nv_bfloat16* zh = reinterpret_cast<__nv_bfloat16*>(d1 + (size_t)p.s1 * p.m1 * p.bp);
   __nv_bfloat16* zl = zh + p.bp * p.k2;
   float* d2 = reinterpret_cast<float*>(zl + p.bp * p.k2);
-  const int64_t prep = p.bp * p.np;
-  k3t_prep<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(a, p.n, p.np, p.bp, batch, xh, xl);
+  k3t_prep<<<dim3((unsigned)((p.np + 255) / 256), (unsigned)p.bp), 256, 0, s>>>(a, p.n, p.np, p.bp, batch, xh, xl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = k3t_gemm_launch(p, m_ft, xh, xl, p.m1, p.k1, p.s1, d1, err, s)) != cudaSuccess) return e;

@@ -89,7 +89,7 @@ def test_k3t_is_the_auto_choice_and_steps(form):
     a = synth.diag_stiffness(n)
     U0 = synth.initial_condition(n, 77, 0, batch)
     rom = grom.Rom(n, form, "bf16", factors=facs, stiffness=a, nu=1e-2, dt=1e-3, max_batch=batch)
-    tr = grom.Trajectories(rom, U0)  # auto: batch >= 32 selects K3T
+    tr = grom.Trajectories(rom, U0)  # auto: batch >= 16 selects K3T
     tr.step(steps)
     code, _ = tr.status()
     assert code == 0
