@@ -974,6 +974,14 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   return cudaSuccess;
 }
 
+// grom_step runs a call of nsteps on the persistent stepper (so a captured
+// call must too, for the same bits).
+static bool persistent_ok(const grom_traj* t, int nsteps) {
+  const grom_rom* r = t->rom;
+  return r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
+         !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8 && !use_k2p(r, t->batch);
+}
+
 grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {
   if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step: null trajectory");
   if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step: nsteps < 0");
@@ -992,8 +1000,7 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   // full G-ROM with the skew-packed tensor and a few trajectories: all steps
   // in one persistent launch (falls back to the graphs below when the launch
   // cannot be placed)
-  if (r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
-      !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8 && !use_k2p(r, t->batch)) {
+  if (persistent_ok(t, nsteps)) {
     StepArgs a = step_args(t, energy, invariant);
     K1Args k = k1_args(r);
     k.hist = t->hist;
@@ -1105,6 +1112,19 @@ static bool pinned_or_device(const void* p, bool* host) {
   return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice;
 }
 
+// The address the device uses for p (pinned host memory is mapped into the
+// device's address space), or null.
+static double* device_alias(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice) return const_cast<double*>(static_cast<const double*>(p));
+  if (at.type == cudaMemoryTypeHost) return static_cast<double*>(at.devicePointer);
+  return nullptr;
+}
+
 grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, double* u_out) {
   if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step_host: null trajectory");
   grom_rom* r = t->rom;
@@ -1129,16 +1149,53 @@ grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, dou
         GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
         GROM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
       }
-      cudaGraph_t g = nullptr;
-      GROM_CUDA_TRY(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaMemcpyAsync(t->io, u_in, bytes, cudaMemcpyDefault, t->gstream);
-      if (e == cudaSuccess) e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, true, t->gstream);
-      if (e == cudaSuccess) e = launch_steps(t, nsteps, nullptr, nullptr, t->gstream);
-      if (e == cudaSuccess) e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, false, t->gstream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(u_out, t->io, bytes, cudaMemcpyDefault, t->gstream);
-      cudaError_t e2 = cudaStreamEndCapture(t->gstream, &g);
-      if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&t->io_graph, g, 0);
-      if (g) cudaGraphDestroy(g);
+      // The state moves straight between the caller's buffers and the
+      // history ring (pinned host memory through its device mapping, no
+      // copy nodes); the steps are the persistent stepper where it applies
+      // (one cooperative launch), else the per-step kernels.
+      double* din = device_alias(u_in);
+      double* dout = device_alias(u_out);
+      cudaError_t e = cudaSuccess, e2 = cudaSuccess;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        const bool persist = attempt == 0 && persistent_ok(t, nsteps);
+        if (attempt == 1 && !persistent_ok(t, nsteps)) break;  // the first attempt was already the plain one
+        cudaGraph_t g = nullptr;
+        GROM_CUDA_TRY(cudaStreamBeginCapture(t->gstream, cudaStreamCaptureModeThreadLocal));
+        e = cudaSuccess;
+        if (din) {
+          e = state_io_launch(t->hist, t->taken, n, t->batch, din, true, t->gstream);
+        } else {
+          e = cudaMemcpyAsync(t->io, u_in, bytes, cudaMemcpyDefault, t->gstream);
+          if (e == cudaSuccess) e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, true, t->gstream);
+        }
+        if (e == cudaSuccess) {
+          if (persist) {
+            StepArgs a = step_args(t, nullptr, nullptr);
+            K1Args k = k1_args(r);
+            k.hist = t->hist;
+            k.taken = t->taken;
+            k.hist_stride = 6 * (int64_t)r->n;
+            e = k1pp_launch(r->k1, r->storage, k, a, t->batch, nsteps, r->k1pp_scratch, t->gstream);
+          } else {
+            e = launch_steps(t, nsteps, nullptr, nullptr, t->gstream);
+          }
+        }
+        if (e == cudaSuccess) {
+          if (dout) {
+            e = state_io_launch(t->hist, t->taken, n, t->batch, dout, false, t->gstream);
+          } else {
+            e = state_io_launch(t->hist, t->taken, n, t->batch, t->io, false, t->gstream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(u_out, t->io, bytes, cudaMemcpyDefault, t->gstream);
+          }
+        }
+        e2 = cudaStreamEndCapture(t->gstream, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&t->io_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess && e2 == cudaSuccess) break;
+        cudaGetLastError();
+        t->io_graph = nullptr;
+        if (!persist) break;  // the persistent launch could not be captured: retry with the per-step kernels
+      }
       if (e != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
         t->io_graph = nullptr;
