@@ -153,12 +153,14 @@ def workload(n, rank, seed, device):
 
 def svd_of_workload(C, ranks, torch):
     """Truncated SVD of the tensor's matricization over the advecting index
-    (the SVD-ROM's offline step, Sec. 4.4.2), on the device in FP64: the
-    eigenpairs of M M^T give U and sigma, and V = M^T U / sigma.  Returns
-    {rank: (U, sigma, V)} with V laid out n x rank x n (V[i][r][k])."""
+    (the SVD-ROM's offline step, Sec. 4.4.2) in FP64: M M^T on the device, its
+    eigenpairs on the host (n x n), U and sigma from them and V = M^T U / sigma
+    on the device.  Returns {rank: (U, sigma, V)} with V laid out n x rank x n
+    (V[i][r][k])."""
     n = C.shape[0]
     M = C.permute(1, 0, 2).reshape(n, n * n)
-    lam, vec = torch.linalg.eigh(M @ M.T)
+    lam_h, vec_h = np.linalg.eigh((M @ M.T).cpu().numpy())
+    lam, vec = torch.from_numpy(lam_h).to(C.device), torch.from_numpy(vec_h).to(C.device)
     order = torch.argsort(lam, descending=True)
     out = {}
     for r in ranks:

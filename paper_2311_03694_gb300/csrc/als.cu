@@ -112,8 +112,11 @@ __global__ void k_als_norm(const double* __restrict__ src, int64_t total, double
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// G = F^T F for F (n x r, row-major FP64), 16 x 16 output tiles.
+// G = F^T F for F (n x r, row-major FP64), 16 x 16 output tiles; G is
+// symmetric, so only the tiles on and above the diagonal are computed (FP64
+// runs at about two operations per clock per SM here) and mirrored.
 __global__ void k_gram(const double* __restrict__ F, int64_t n, int64_t r, double* __restrict__ G) {
+  if (blockIdx.x < blockIdx.y) return;  // whole block, before any barrier
   __shared__ double a[16][17], b[16][17];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t row = (int64_t)blockIdx.y * 16 + ty, col = (int64_t)blockIdx.x * 16 + tx;
@@ -127,7 +130,10 @@ __global__ void k_gram(const double* __restrict__ F, int64_t n, int64_t r, doubl
     for (int q = 0; q < 16; ++q) s = fma(a[q][ty], b[q][tx], s);
     __syncthreads();
   }
-  if (row < r && col < r) G[row * r + col] = s;
+  if (row < r && col < r) {
+    G[row * r + col] = s;
+    G[col * r + row] = s;
+  }
 }
 
 // ------------------------------------------------ SPD solves on the device
