@@ -334,7 +334,9 @@ __global__ void k2p_prep_kernel(const K2PDev p, float* uf, __nv_bfloat16* uh, __
 }
 
 // c[b][k] = direct partials of row k - mirrored-entry windows covering k,
-// summed in a fixed order in FP64.
+// each group summed in a fixed order in FP32 (the partials are FP32 sums
+// already; FP64 adds run at about two per clock per SM on this part), the
+// two totals subtracted in FP64.
 __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, double* hist, const int64_t* taken,
                                   int64_t hist_stride, const int32_t* active, int batch) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,8 +344,8 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
   const int64_t k = t / batch, b = t - k * batch;  // consecutive threads: consecutive b
   if (active && !active[b]) return;
   const int ct = (int)(b / p.btile), bl = (int)(b - (int64_t)ct * p.btile);
-  double s = 0.0;
-  for (int pb = 0; pb < p.pblks; ++pb) s += (double)p.cdp[((int64_t)pb * p.n + k) * p.bp + b];
+  float sd = 0.f, sm = 0.f;
+  for (int pb = 0; pb < p.pblks; ++pb) sd += p.cdp[((int64_t)pb * p.n + k) * p.bp + b];
   // window row w of tile (range r, block pb) holds the mirrored entries of
   // k = (r m + 1 + 128 pb + w) mod n
   for (int pb = 0; pb < p.pblks; ++pb) {
@@ -352,7 +354,7 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
       int64_t w = x - (int64_t)r * p.m;
       if (w < 0) w += p.n;
       const float* e = p.ep + ((int64_t)(r * p.pblks + pb) * p.col_tiles + ct) * p.wrows * p.btile + bl;
-      for (; w < p.wrows; w += p.n) s -= (double)e[w * p.btile];
+      for (; w < p.wrows; w += p.n) sm += e[w * p.btile];
     };
     if (p.n <= p.wrows) {
       for (int r = 0; r < p.ranges; ++r) add(r);
@@ -369,7 +371,7 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
     }
   }
   double* dst = taken ? hist + b * hist_stride + (3 + taken[b] % 3) * p.n : c + b * c_stride;
-  dst[k] = s;
+  dst[k] = (double)sd - (double)sm;
 }
 
 // ------------------------------------------------------------------- host

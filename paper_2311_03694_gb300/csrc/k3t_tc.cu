@@ -198,11 +198,11 @@ __global__ void k3t_prep(const K3Args a, int64_t n, int64_t np, int64_t bp, int 
 }
 
 // Z[b][j] (BF16 hi/lo, bp x kz) from the projection partials d1 (s1 x m1 x
-// bp, rows P | Q | S of rp each): general Z[b][j] = P_j Q_j, skew
-// Z[b][j] = P_j Q_j and Z[b][rp + j] = P_j S_j; 32 x 32 tiles through shared
+// bp, rows P | Q | S of rp each): Z[b][j] = P_j Q_j for j < rp and, in the
+// skew form (kz = 2 rp), Z[b][rp + j] = P_j S_j; 32 x 32 tiles through shared
 // memory (coalesced reads along b, writes along j).
 __global__ void k3t_hadamard(const float* __restrict__ d1, int s1, int64_t m1, int64_t rp, int64_t bp, int64_t kz,
-                             int skew, __nv_bfloat16* zh, __nv_bfloat16* zl) {
+                             __nv_bfloat16* zh, __nv_bfloat16* zl) {
   __shared__ float tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t j0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
@@ -221,7 +221,6 @@ __global__ void k3t_hadamard(const float* __restrict__ d1, int s1, int64_t m1, i
     }
     tile[jj][tx] = z;
   }
-  (void)skew;
   __syncthreads();
   for (int bb = ty; bb < 32; bb += 8) {
     const int64_t b = b0 + bb, j = j0 + tx;
@@ -407,7 +406,7 @@ cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensor
   if (e != cudaSuccess) return e;
   if ((e = k3t_gemm_launch(p, m_ft, xh, xl, p.m1, p.k1, p.s1, d1, err, s)) != cudaSuccess) return e;
   dim3 hg((unsigned)((p.bp + 31) / 32), (unsigned)((p.k2 + 31) / 32));
-  k3t_hadamard<<<hg, 256, 0, s>>>(d1, p.s1, p.m1, p.rp, p.bp, p.k2, p.nz == 2 ? 1 : 0, zh, zl);
+  k3t_hadamard<<<hg, 256, 0, s>>>(d1, p.s1, p.m1, p.rp, p.bp, p.k2, zh, zl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = k3t_gemm_launch(p, m_ae, zh, zl, p.m2, p.k2, p.s2, d2, err, s)) != cudaSuccess) return e;
   const int64_t fin = (int64_t)batch * p.n;
