@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -99,6 +100,9 @@ struct K2Args {
   int64_t f_stride;
   int tiled;  // 1: the tensor map covers the tile-major copy (k2_build_tiles)
 };
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null when
+// the driver does not provide it); looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn();
 K2Plan k2_plan(int64_t n, int batch, int sm_count);
 size_t k2_scratch_bytes(const K2Plan& p);
 bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np);

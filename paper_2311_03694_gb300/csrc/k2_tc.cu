@@ -359,7 +359,7 @@ __global__ void k2_reduce_kernel(const K2Dev p, double* c, int64_t c_stride, dou
 }
 
 // ------------------------------------------------------------------- host
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* f = nullptr;
@@ -405,7 +405,7 @@ cudaError_t k2_build_tiles(const void* rows, int64_t n, void* tiles, cudaStream_
 }
 
 bool k2_make_tmap_tiled(CUtensorMap* m, const void* tiles, int64_t n) {
-  auto fn = encode_fn();
+  auto fn = tmap_encode_fn();
   if (!fn) return false;
   const int64_t np = padded_n(n), i_tiles = (n + 255) / 256;
   cuuint64_t dims[2] = {64, (cuuint64_t)(i_tiles * n * (np / 64) * 256)};
@@ -419,7 +419,7 @@ bool k2_make_tmap_tiled(CUtensorMap* m, const void* tiles, int64_t n) {
 }
 
 bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np) {
-  auto fn = encode_fn();
+  auto fn = tmap_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)(n * np), (cuuint64_t)n};
   cuuint64_t strides[1] = {(cuuint64_t)(n * np * 2)};

@@ -375,21 +375,9 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
 }
 
 // ------------------------------------------------------------------- host
-static PFN_cuTensorMapEncodeTiled_v12000 k2p_encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
-  return fn;
-}
-
 // The stored rows as a 3-D tensor (p, j, i); boxes of 64 positions x 64 j.
 bool k2p_make_tmap(CUtensorMap* m, const void* packed, int64_t n, int64_t lp) {
-  auto fn = k2p_encode_fn();
+  auto fn = tmap_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)lp, (cuuint64_t)n, (cuuint64_t)n};
   cuuint64_t strides[2] = {(cuuint64_t)(lp * 2), (cuuint64_t)(n * lp * 2)};
@@ -402,7 +390,7 @@ bool k2p_make_tmap(CUtensorMap* m, const void* packed, int64_t n, int64_t lp) {
 }
 
 static bool k2p_make_tmap_u(CUtensorMap* m, const void* u, int64_t np, int64_t bp, int btile) {
-  auto fn = k2p_encode_fn();
+  auto fn = tmap_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)bp};
   cuuint64_t strides[1] = {(cuuint64_t)(np * 2)};

@@ -276,21 +276,9 @@ __global__ void k3t_build(const __nv_bfloat16* __restrict__ fa, const __nv_bfloa
 }
 
 // ------------------------------------------------------------------- host
-static PFN_cuTensorMapEncodeTiled_v12000 k3t_encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
-  return fn;
-}
-
 // rows x cols BF16, row-major, boxes of box_rows x 64.
 static bool k3t_tmap(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int box_rows) {
-  auto fn = k3t_encode_fn();
+  auto fn = tmap_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
