@@ -226,8 +226,9 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * BF16 storage and batches above 8 trajectories (full form) or of 16 and more
  * (CP forms), else the streaming (full) or SIMT (CP) kernels. */
 #define GROM_KERNEL_AUTO 0
-#define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass;
-                                CP forms: the SIMT kernels (K3, K3g)                        */
+#define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass, one
+                                launch per step (no persistent stepper); CP forms: the SIMT
+                                kernels (K3, K3g)                                            */
 #define GROM_KERNEL_TENSOR 2 /* BF16 storage only.  Dense layout, K2: tcgen05 GEMM over the
                                 Khatri-Rao product of the states (Sec. 2.2, eq. Cu with the
                                 mode-1 matricisation).  Skew-packed layout, K2P: the factored

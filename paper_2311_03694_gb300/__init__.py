@@ -279,7 +279,8 @@ class Rom:
         _check(load().grom_selftest_timeout(self._h, int(limit_ns)))
 
     def set_kernel(self, kernel):
-        """Override the dense-contraction kernel: "auto", "stream" (K1) or "tensor" (K2)."""
+        """Override the contraction kernel: "auto", "stream" (the SIMT streaming or CP
+        kernels, one launch per step) or "tensor" (the tcgen05 kernels: K2, K2P, K3T)."""
         _check(load().grom_set_kernel(self._h, {"auto": 0, "stream": 1, "tensor": 2}[kernel]))
 
     def profile(self, enable=True):

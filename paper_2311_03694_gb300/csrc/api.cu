@@ -975,11 +975,16 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
 }
 
 // grom_step runs a call of nsteps on the persistent stepper (so a captured
-// call must too, for the same bits).
+// call must too, for the same bits): the skew-packed full form with a few
+// trajectories, unless the caller asked for the per-step kernels
+// (GROM_KERNEL_STREAM).  One launch per call of any length: the finalize of
+// the transposed term runs between grid barriers instead of in a second
+// launch.
 static bool persistent_ok(const grom_traj* t, int nsteps) {
   const grom_rom* r = t->rom;
   return r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
-         !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 8 && !use_k2p(r, t->batch);
+         !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 1 &&
+         r->kernel_choice != GROM_KERNEL_STREAM && !use_k2p(r, t->batch);
 }
 
 grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {

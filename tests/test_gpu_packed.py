@@ -261,8 +261,8 @@ def test_step_host_paths_agree(layout):
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32x2", 1e-12), ("f32", 1e-6), ("bf16", 1e-4)])
 @pytest.mark.parametrize("batch", [1, 3])
 def test_persistent_stepper_matches_single_steps(storage, tol, batch):
-    # 40 steps in one persistent launch vs 40 single-step calls (the
-    # finalize sums run in different orders: agreement to rounding)
+    # 40 steps in one persistent launch vs 40 single steps on the per-step
+    # kernels (the finalize sums run in different orders: agreement to rounding)
     n = 96
     seed = synth.seed_for(0) + 8100
     C = synth.skew_normal_tensor(n, seed)
@@ -270,9 +270,16 @@ def test_persistent_stepper_matches_single_steps(storage, tol, batch):
     rom = _rom(C, storage, max_batch=batch, nu=1e-2, dt=1e-3)
     t1 = grom.Trajectories(rom, U0)
     t1.step(40)
+    rom.set_kernel("stream")  # the streaming kernel and a separate finalize/step launch
     t2 = grom.Trajectories(rom, U0)
     for _ in range(40):
         t2.step(1)
+    rom.set_kernel("auto")
+    t3 = grom.Trajectories(rom, U0)
+    for _ in range(40):
+        t3.step(1)  # single-step calls on the persistent stepper: the bits of one long launch
+    np.testing.assert_array_equal(t3.get_state(), t1.get_state())
+    t3.close()
     H1, H2 = t1.get_state(), t2.get_state()
     for b in range(batch):
         assert _rel(H1[b][:n], H2[b][:n]) <= tol, (storage, b)
