@@ -203,6 +203,9 @@ class Rom:
     pair C_ijk = -C_kji stored; the tensor, or each V slice, must be skew).
     augmented: the operator includes the zeroth mode (full: tensor n x (n+1)
     x (n+1); cp: fb and fc with n+1 rows); see grom_desc.augmented.
+    tile_copy: dense BF16 full form with max_batch > 8 keeps a tile-major copy
+    of the tensor for the tensor-core kernel (False: row layout only, less
+    memory); see grom_desc.no_tile_copy.
     """
 
     def __init__(self, n, form="full", storage="f64", tensor=None, factors=None, stiffness=None, mass=None,
