@@ -240,6 +240,59 @@ int64_t grom_rom_bytes(const grom_rom* rom);
                                 tcgen05 GEMMs (Sec. 3.1, eq. tc_ap; Sec. 3.3)              */
 grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
 
+/* ------------------------------------------------------------ autotuning
+ * The launch shapes of the batched tensor-core kernels come from fixed rules
+ * (their plans): K2 splits the advecting index j across CTAs, K2P covers m
+ * test indices per tile, K3T splits the K range of each of its two GEMMs;
+ * and AUTO picks between the tensor-core and the SIMT kernels by batch size.
+ * The autotuner times the alternatives on the device and keeps the fastest
+ * for the ROM, per batch bucket: batches with the same ceil(batch / 16) have
+ * identical plans apart from the batch itself, so one entry serves them all.
+ * Entries change only which valid configuration runs (the results differ by
+ * FP32 summation order, within each kernel's bound); the persistent steppers
+ * (few trajectories, whole step in one launch) ignore them, and a kernel
+ * forced by grom_set_kernel overrides an entry's `kernel`. */
+typedef struct grom_tuning {
+  int32_t batch;   /* trajectories tuned for; the entry serves ceil(batch / 16)       */
+  int32_t kernel;  /* GROM_KERNEL_STREAM or GROM_KERNEL_TENSOR (in grom_set_tuning,
+                      GROM_KERNEL_AUTO removes the bucket's entry)                      */
+  int32_t tile_m;  /* K2P: test indices per tile, 8..32; 0 = the plan's rule           */
+  int32_t split_a; /* K2: CTAs sharing one output tile (split of j), 1..n;
+                      K3T: splits of the projection GEMM; 0 = the rule                  */
+  int32_t split_b; /* K3T: splits of the expansion GEMM; 0 = the rule                  */
+  int32_t timed;   /* grom_autotune: configurations timed                              */
+  float ms;        /* grom_autotune: median device ms per evaluation of this entry      */
+  float ms_rule;   /* grom_autotune: the same for the rules' configuration             */
+} grom_tuning;
+
+/* The configurations grom_autotune times for `batch` trajectories of a ROM
+ * with these parameters (host arithmetic only, no device needed): the rules'
+ * own first, then every alternative the plans admit whose scratch fits what
+ * grom_create allocates for max_batch.  Writes up to `cap` entries to `out`
+ * (NULL with cap 0 to count) and returns how many there are, or -1 for
+ * invalid arguments.  sm_count: the device's multiprocessor count. */
+int32_t grom_tune_space(int32_t form, int32_t storage, int32_t layout, int32_t n, int32_t rank, int32_t max_batch,
+                        int32_t batch, int32_t sm_count, grom_tuning* out, int32_t cap);
+
+/* Times every configuration of grom_tune_space for `batch` trajectories on
+ * the ROM's stream: synthetic states, two untimed evaluations, then three
+ * groups of `reps` (0: 10) back-to-back evaluations between CUDA events; a
+ * configuration's time is the median of its groups.  Installs the fastest for
+ * the bucket if it beats the rules' by more than 2 %, else the rules' (so the
+ * entry records the decision), and returns the installed entry in *out
+ * (nullable).  Synchronises the stream; not allowed while it is being
+ * captured (INVALID_ARG).  A device-side wait that timed out returns TIMEOUT
+ * and leaves the bucket untuned. */
+grom_status grom_autotune(grom_rom* rom, int32_t batch, int32_t reps, grom_tuning* out);
+
+/* Installs an entry, e.g. one saved from grom_autotune in an earlier run;
+ * INVALID_ARG unless it is one of grom_tune_space's for this ROM (the timing
+ * fields are ignored).  kernel = GROM_KERNEL_AUTO removes the bucket's entry. */
+grom_status grom_set_tuning(grom_rom* rom, const grom_tuning* entry);
+
+/* The entry serving `batch` (kernel = GROM_KERNEL_AUTO: none, the rules apply). */
+grom_status grom_get_tuning(const grom_rom* rom, int32_t batch, grom_tuning* out);
+
 /* ------------------------------------------------------------ serving
  * A server keeps several ROMs resident and steps trajectory requests as they
  * arrive, with continuous batching: each ROM owns a pool of max_slots

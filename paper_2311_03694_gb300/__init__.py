@@ -38,6 +38,28 @@ class _Stats(ctypes.Structure):
                 ("peak_bytes", ctypes.c_int64), ("peak_active", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("kernel", ctypes.c_int32), ("tile_m", ctypes.c_int32),
+                ("split_a", ctypes.c_int32), ("split_b", ctypes.c_int32), ("timed", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("ms_rule", ctypes.c_float)]
+
+
+KERNELS = {"auto": 0, "stream": 1, "tensor": 2}
+_KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+
+
+def _tuning_dict(t):
+    return {"batch": t.batch, "kernel": _KERNEL_NAMES.get(t.kernel, t.kernel), "tile_m": t.tile_m,
+            "split_a": t.split_a, "split_b": t.split_b, "timed": t.timed, "ms": t.ms, "ms_rule": t.ms_rule}
+
+
+def _tuning_struct(d):
+    t = _Tuning()
+    t.batch, t.kernel = int(d["batch"]), KERNELS[d["kernel"]]
+    t.tile_m, t.split_a, t.split_b = int(d.get("tile_m", 0)), int(d.get("split_a", 0)), int(d.get("split_b", 0))
+    return t
+
+
 class GromError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s: %s" % (ERRORS.get(code, code), msg))
@@ -77,6 +99,10 @@ EXPORTS = {
     "grom_rom_bytes": ([ctypes.c_void_p], ctypes.c_int64),
     "grom_step_host": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "grom_set_kernel": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
+    "grom_tune_space": ([ctypes.c_int32] * 8 + [ctypes.POINTER(_Tuning), ctypes.c_int32], ctypes.c_int32),
+    "grom_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Tuning)], ctypes.c_int32),
+    "grom_set_tuning": ([ctypes.c_void_p, ctypes.POINTER(_Tuning)], ctypes.c_int32),
+    "grom_get_tuning": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_Tuning)], ctypes.c_int32),
     "grom_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "grom_profile_read": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                           ctypes.c_int32),
@@ -155,6 +181,20 @@ def _stream_handle(stream):
 
 def max_n(form, storage):
     return load().grom_max_n(FORMS[form], STORAGE[storage])
+
+
+def tune_space(form, storage, n, batch, max_batch=None, rank=0, layout="dense", sm_count=152):
+    """The configurations the autotuner times for `batch` trajectories of such a
+    ROM (grom_tune_space; host arithmetic only): the rules' first."""
+    lib = load()
+    args = (FORMS[form], STORAGE[storage], LAYOUTS[layout], int(n), int(rank),
+            int(max_batch if max_batch is not None else batch), int(batch), int(sm_count))
+    count = lib.grom_tune_space(*args, None, 0)
+    if count < 0:
+        raise GromError(1, "grom_tune_space: invalid arguments")
+    buf = (_Tuning * max(count, 1))()
+    lib.grom_tune_space(*args, buf, count)
+    return [_tuning_dict(buf[i]) for i in range(count)]
 
 
 def nonlinear_full_noalloc(n, storage, tensor, u, c, stream=None):
@@ -284,7 +324,24 @@ class Rom:
     def set_kernel(self, kernel):
         """Override the contraction kernel: "auto", "stream" (the SIMT streaming or CP
         kernels, one launch per step) or "tensor" (the tcgen05 kernels: K2, K2P, K3T)."""
-        _check(load().grom_set_kernel(self._h, {"auto": 0, "stream": 1, "tensor": 2}[kernel]))
+        _check(load().grom_set_kernel(self._h, KERNELS[kernel]))
+
+    def autotune(self, batch, reps=0):
+        """Time the kernel choices and tile shapes for `batch` trajectories and
+        keep the fastest for its batch bucket (grom_autotune); returns the entry
+        installed, a dict that set_tuning accepts in a later run."""
+        t = _Tuning()
+        _check(load().grom_autotune(self._h, int(batch), int(reps), ctypes.byref(t)))
+        return _tuning_dict(t)
+
+    def set_tuning(self, entry):
+        """Install an entry (a dict from autotune or tune_space); kernel "auto" removes it."""
+        _check(load().grom_set_tuning(self._h, ctypes.byref(_tuning_struct(entry))))
+
+    def get_tuning(self, batch):
+        t = _Tuning()
+        _check(load().grom_get_tuning(self._h, int(batch), ctypes.byref(t)))
+        return _tuning_dict(t)
 
     def profile(self, enable=True):
         _check(load().grom_profile_enable(self._h, 1 if enable else 0))

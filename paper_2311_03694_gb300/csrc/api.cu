@@ -248,20 +248,34 @@ static bool prof_pair(grom_rom* r, cudaEvent_t* e0, cudaEvent_t* e1) {
   return true;
 }
 
-static bool use_k2(const grom_rom* r, int batch) {
-  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE) return false;
+// ------------------------------------------------------------ autotuning
+// The installed entry serving a batch (its bucket ceil(batch / 16)), if any.
+static const grom_tuning* tuned(const grom_rom* r, int batch) {
+  const size_t b = (size_t)((batch + 15) / 16) - 1;
+  return b < r->tuning.size() && r->tuning[b].kernel != GROM_KERNEL_AUTO ? &r->tuning[b] : nullptr;
+}
+
+// AUTO's choice of the tensor-core kernel: the tuned entry's, else the rule
+// (full form: batches above 8; CP forms: K3T_MIN_BATCH and more).  The
+// persistent steppers ask for the rule alone (use_tuning false).
+static bool tensor_choice(const grom_rom* r, int batch, bool use_tuning) {
   if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
   if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
-  return batch > 8;
+  if (use_tuning)
+    if (const grom_tuning* t = tuned(r, batch)) return t->kernel == GROM_KERNEL_TENSOR;
+  return r->form == GROM_FORM_FULL ? batch > 8 : batch >= K3T_MIN_BATCH;
+}
+
+static bool use_k2(const grom_rom* r, int batch, bool use_tuning = true) {
+  if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_DENSE) return false;
+  return tensor_choice(r, batch, use_tuning);
 }
 
 // K2P: the factored tensor-core kernel of the skew-packed layout
-static bool use_k2p(const grom_rom* r, int batch) {
+static bool use_k2p(const grom_rom* r, int batch, bool use_tuning = true) {
   if (r->form != GROM_FORM_FULL || r->storage != GROM_BF16 || !r->k2_ok || r->layout != GROM_LAYOUT_SKEW_PACKED)
     return false;
-  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
-  if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
-  return batch > 8;
+  return tensor_choice(r, batch, use_tuning);
 }
 
 static bool is_cp(const grom_rom* r) { return r->form == GROM_FORM_CP || r->form == GROM_FORM_CP_SKEW; }
@@ -271,11 +285,132 @@ static bool use_k3g(const grom_rom* r, int batch) {
 }
 
 // K3T: the batched CP form on the tensor cores (BF16 factors)
-static bool use_k3t(const grom_rom* r, int batch) {
+static bool use_k3t(const grom_rom* r, int batch, bool use_tuning = true) {
   if (!is_cp(r) || !r->k3t_factors) return false;
-  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
-  if (r->kernel_choice == GROM_KERNEL_STREAM) return false;
-  return batch >= K3T_MIN_BATCH;
+  return tensor_choice(r, batch, use_tuning);
+}
+
+// The plans with the tuned entry's shape for the batch's bucket.
+static K2Plan k2_plan_of(const grom_rom* r, int batch) {
+  const grom_tuning* t = tuned(r, batch);
+  return k2_plan(r->n, batch, r->sm_count, t ? t->split_a : 0);
+}
+static K2PPlan k2p_plan_of(const grom_rom* r, int batch) {
+  const grom_tuning* t = tuned(r, batch);
+  return k2p_plan(r->n, r->k1.lp, batch, r->sm_count, t ? t->tile_m : 0);
+}
+static K3TPlan k3t_plan_of(const grom_rom* r, int batch) {
+  const grom_tuning* t = tuned(r, batch);
+  return k3t_plan(r->n, r->rank, r->form, batch, r->sm_count, t ? t->split_a : 0, t ? t->split_b : 0);
+}
+
+// What the tune space depends on: a ROM's parameters and the scratch it holds.
+struct TuneShape {
+  int form = 0, storage = 0, layout = 0, max_batch = 1, sm_count = 1;
+  int64_t n = 0, rank = 0, lp = 0;
+  bool tensor = false;  // a tensor-core kernel exists
+  size_t k2_scratch = 0, k3t_scratch = 0;
+};
+
+static TuneShape shape_of(const grom_rom* r) {
+  TuneShape s;
+  s.form = r->form;
+  s.storage = r->storage;
+  s.layout = r->layout;
+  s.max_batch = r->max_batch;
+  s.sm_count = r->sm_count;
+  s.n = r->n;
+  s.rank = r->rank;
+  s.lp = r->k1.lp;
+  s.tensor = (r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok) || (is_cp(r) && r->k3t_factors);
+  s.k2_scratch = r->k2_scratch_bytes;
+  s.k3t_scratch = r->k3t_scratch_bytes;
+  return s;
+}
+
+static bool shape_is_cp(const TuneShape& s) { return s.form == GROM_FORM_CP || s.form == GROM_FORM_CP_SKEW; }
+
+// Whether an entry is one of the tune space's (timing fields ignored).
+static bool tuning_ok(const TuneShape& s, const grom_tuning& t) {
+  if (t.batch < 1 || t.batch > s.max_batch) return false;
+  if (t.kernel == GROM_KERNEL_STREAM) return t.tile_m == 0 && t.split_a == 0 && t.split_b == 0;
+  if (t.kernel != GROM_KERNEL_TENSOR || !s.tensor) return false;
+  if (s.form == GROM_FORM_FULL && s.layout == GROM_LAYOUT_DENSE) {
+    if (t.tile_m != 0 || t.split_b != 0 || t.split_a < 0 || t.split_a > s.n) return false;
+    return k2_scratch_bytes(k2_plan(s.n, t.batch, s.sm_count, t.split_a)) <= s.k2_scratch;
+  }
+  if (s.form == GROM_FORM_FULL) {
+    if (t.split_a != 0 || t.split_b != 0) return false;
+    if (t.tile_m != 0 && !k2p_tile_m_ok(t.batch, t.tile_m)) return false;
+    return k2p_scratch_bytes(k2p_plan(s.n, s.lp, t.batch, s.sm_count, t.tile_m)) <= s.k2_scratch;
+  }
+  const K3TPlan p = k3t_plan(s.n, s.rank, s.form, t.batch, s.sm_count, t.split_a, t.split_b);
+  if (t.tile_m != 0 || t.split_a < 0 || t.split_a > p.s1_max || t.split_b < 0 || t.split_b > p.s2_max) return false;
+  return k3t_scratch_bytes(p) <= s.k3t_scratch;
+}
+
+// Split counts to try around the rule's: halvings and doublings of it, and
+// every power of two, within [1, hi].
+static std::vector<int> split_candidates(int rule, int hi) {
+  std::vector<int> v;
+  for (int x = rule; x >= 1; x /= 2) v.push_back(x);
+  for (int x = 2 * rule; x <= hi && x <= 4 * rule; x *= 2) v.push_back(x);
+  for (int x = 1; x <= hi; x *= 2) v.push_back(x);
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+  std::vector<int> out;
+  for (int x : v)
+    if (x >= 1 && x <= hi) out.push_back(x);
+  return out;
+}
+
+// The rules' configuration first, then the alternatives: the other kernel
+// family, and every admissible tile shape of the tensor-core kernel that
+// differs from the rule's.
+static void tune_space(const TuneShape& s, int batch, std::vector<grom_tuning>& out) {
+  out.clear();
+  grom_tuning base{};
+  base.batch = batch;
+  const bool rule_tensor = s.tensor && (s.form == GROM_FORM_FULL ? batch > 8 : batch >= K3T_MIN_BATCH);
+  grom_tuning e = base;
+  e.kernel = rule_tensor ? GROM_KERNEL_TENSOR : GROM_KERNEL_STREAM;
+  out.push_back(e);
+  if (!s.tensor) return;
+  e = base;
+  e.kernel = rule_tensor ? GROM_KERNEL_STREAM : GROM_KERNEL_TENSOR;
+  out.push_back(e);  // the other family with its rule shape
+  auto add = [&](grom_tuning c) {
+    c.batch = batch;
+    c.kernel = GROM_KERNEL_TENSOR;
+    if (tuning_ok(s, c)) out.push_back(c);
+  };
+  if (s.form == GROM_FORM_FULL && s.layout == GROM_LAYOUT_DENSE) {
+    const int rule = k2_plan(s.n, batch, s.sm_count).splits;
+    for (int x : split_candidates(rule, (int)std::min<int64_t>(s.n, 4 * (int64_t)s.sm_count)))
+      if (x != rule) {
+        grom_tuning c{};
+        c.split_a = x;
+        add(c);
+      }
+  } else if (s.form == GROM_FORM_FULL) {
+    const int rule = k2p_plan(s.n, s.lp, batch, s.sm_count).m;
+    for (int m = 8; m <= 32; ++m)
+      if (m != rule) {
+        grom_tuning c{};
+        c.tile_m = m;
+        add(c);
+      }
+  } else if (shape_is_cp(s)) {
+    const K3TPlan p = k3t_plan(s.n, s.rank, s.form, batch, s.sm_count);
+    for (int a : split_candidates(p.s1, p.s1_max))
+      for (int b : split_candidates(p.s2, p.s2_max))
+        if (a != p.s1 || b != p.s2) {
+          grom_tuning c{};
+          c.split_a = a;
+          c.split_b = b;
+          add(c);
+        }
+  }
 }
 
 static K1Args k1_args(grom_rom* r) {
@@ -418,12 +553,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       r->k2_ok = k2p_make_tmap(&r->k2_tmap, r->op, n, r->k1.lp);
       if (r->k2_ok) {
         // scratch for the largest plan over the batch sizes this ROM accepts
-        size_t need = 0;
-        for (int b = 16;; b = b < 128 ? b + 16 : b + 128) {
-          const int bb = b < r->max_batch ? b : r->max_batch;
-          need = std::max(need, k2p_scratch_bytes(k2p_plan(n, r->k1.lp, bb, r->sm_count)));
-          if (bb >= r->max_batch) break;
-        }
+        const size_t need = k2p_scratch_need(n, r->k1.lp, r->max_batch, r->sm_count);
         r->k2_scratch_bytes = need;
         if ((st = dmalloc(&r->k2_scratch, need, &r->total_bytes))) return bail(st);
       }
@@ -432,12 +562,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       r->k2_ok = k2_make_tmap(&r->k2_tmap, r->op, n, r->np);
       if (r->k2_ok) {
         // scratch for the largest plan over the batch sizes this ROM accepts
-        size_t need = 0;
-        for (int b = 16;; b = b < 256 ? b + 16 : b * 2) {
-          const int bb = b < r->max_batch ? b : r->max_batch;
-          need = std::max(need, k2_scratch_bytes(k2_plan(n, bb, r->sm_count)));
-          if (bb >= r->max_batch) break;
-        }
+        const size_t need = k2_scratch_need(n, r->max_batch, r->sm_count);
         r->k2_scratch_bytes = need;
         if ((st = dmalloc(&r->k2_scratch, need, &r->total_bytes))) return bail(st);
       }
@@ -525,13 +650,8 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
                             ae, r->stream) != cudaSuccess ||
           !k3t_make_tmaps(&r->k3t_tmap_ft, &r->k3t_tmap_ae, ft, ae, n, r->rank, r->form))
         return bail(cuda_fail(cudaGetLastError(), "grom_create: tensor-core factor copies"));
-      size_t need = 0;
-      for (int b = 16;; b = b < 128 ? b + 16 : b + 128) {
-        const int bb = b < r->max_batch ? b : r->max_batch;
-        need = std::max(need, k3t_scratch_bytes(k3t_plan(n, r->rank, r->form, bb, r->sm_count)));
-        if (bb >= r->max_batch) break;
-      }
-      if ((st = dmalloc(&r->k3t_scratch, need, &r->total_bytes))) return bail(st);
+      r->k3t_scratch_bytes = k3t_scratch_need(n, r->rank, r->form, r->max_batch, r->sm_count);
+      if ((st = dmalloc(&r->k3t_scratch, r->k3t_scratch_bytes, &r->total_bytes))) return bail(st);
     }
     // persistent stepper (its grid-barrier word starts at zero)
     const size_t kp = k3p_scratch_bytes(n, rp, r->storage, r->sm_count);
@@ -725,7 +845,7 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
     a.tiled = r->k2_tiles != nullptr;
-    e = k2_launch(k2_plan(r->n, batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, r->stream);
+    e = k2_launch(k2_plan_of(r, batch), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, r->stream);
   } else if (use_k2p(r, batch)) {
     K2Args a{};
     a.u = u;
@@ -736,7 +856,7 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     a.scratch = r->k2_scratch;
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return fail(GROM_ERR_CUDA, "event creation failed");
-    e = k2p_launch(k2p_plan(r->n, r->k1.lp, batch, r->sm_count), &r->k2_tmap, a, r->stream);
+    e = k2p_launch(k2p_plan_of(r, batch), &r->k2_tmap, a, r->stream);
   } else if (!is_cp(r)) {
     K1Args a = k1_args(r);
     a.u = u;
@@ -755,7 +875,7 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     cudaEvent_t e0, e1;
     if (!prof_pair(r, &e0, &e1)) return fail(GROM_ERR_CUDA, "event creation failed");
     if (e0) prof_record(e0, r->stream);
-    e = use_k3t(r, batch) ? k3t_launch(k3t_plan(r->n, r->rank, r->form, batch, r->sm_count), &r->k3t_tmap_ft,
+    e = use_k3t(r, batch) ? k3t_launch(k3t_plan_of(r, batch), &r->k3t_tmap_ft,
                                        &r->k3t_tmap_ae, a, batch, r->k3t_scratch, r->err, r->stream)
         : use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
                             : k3_launch(r->k3, r->storage, a, batch, r->stream);
@@ -848,7 +968,7 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
     a.tiled = r->k2_tiles != nullptr;
-    return k2_launch(k2_plan(r->n, t->batch, r->sm_count), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, strm);
+    return k2_launch(k2_plan_of(r, t->batch), a.tiled ? &r->k2_tmap_tiled : &r->k2_tmap, a, strm);
   }
   if (use_k2p(r, t->batch)) {
     K2Args a{};
@@ -860,7 +980,7 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
     a.scratch = r->k2_scratch;
     a.err = r->err;
     if (!prof_pair(r, &a.ev0, &a.ev1)) return cudaErrorMemoryAllocation;
-    return k2p_launch(k2p_plan(r->n, r->k1.lp, t->batch, r->sm_count), &r->k2_tmap, a, strm);
+    return k2p_launch(k2p_plan_of(r, t->batch), &r->k2_tmap, a, strm);
   }
   if (!is_cp(r)) {
     K1Args a = k1_args(r);
@@ -884,7 +1004,7 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
   if (e0) prof_record(e0, strm);
   cudaError_t e = use_k3t(r, t->batch)
-                      ? k3t_launch(k3t_plan(r->n, r->rank, r->form, t->batch, r->sm_count), &r->k3t_tmap_ft,
+                      ? k3t_launch(k3t_plan_of(r, t->batch), &r->k3t_tmap_ft,
                                    &r->k3t_tmap_ae, a, t->batch, r->k3t_scratch, r->err, strm)
                   : use_k3g(r, t->batch)
                       ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
@@ -984,7 +1104,7 @@ static bool persistent_ok(const grom_traj* t, int nsteps) {
   const grom_rom* r = t->rom;
   return r->form == GROM_FORM_FULL && r->layout == GROM_LAYOUT_SKEW_PACKED && r->diagonal && r->k1pp_scratch &&
          !t->active && t->batch <= 4 && t->batch <= r->k1.nb_max && nsteps >= 1 &&
-         r->kernel_choice != GROM_KERNEL_STREAM && !use_k2p(r, t->batch);
+         r->kernel_choice != GROM_KERNEL_STREAM && !use_k2p(r, t->batch, false);
 }
 
 grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {
@@ -994,7 +1114,7 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_step: tensor rows missing");
   // CP forms with a few trajectories: all steps in one persistent launch
   if (r->diagonal && is_cp(r) && r->k3p_scratch && !t->active && !r->prof &&
-      t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 && !use_k3t(r, t->batch) &&
+      t->batch <= k3p_max_batch(r->storage) && nsteps >= 4 && !use_k3t(r, t->batch, false) &&
       k3p_fits(r->n, r->k3.rb, r->storage, t->batch, r->sm_count)) {
     StepArgs a = step_args(t, energy, invariant);
     cudaError_t e = k3p_launch(r->op, r->op + r->panel_bytes, r->op + 2 * r->panel_bytes, r->form, r->n, r->k3.rb,
@@ -1246,6 +1366,147 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   }
   r->kernel_choice = kernel;
   ++r->version;
+  return GROM_OK;
+}
+
+int32_t grom_tune_space(int32_t form, int32_t storage, int32_t layout, int32_t n, int32_t rank, int32_t max_batch,
+                        int32_t batch, int32_t sm_count, grom_tuning* out, int32_t cap) {
+  const bool cp = form == GROM_FORM_CP || form == GROM_FORM_CP_SKEW;
+  if (n < 1 || max_batch < 1 || batch < 1 || batch > max_batch || sm_count < 1 || cap < 0 || (cap > 0 && !out) ||
+      storage_elem_bytes(storage) == 0 || form < GROM_FORM_FULL || form > GROM_FORM_SVD ||
+      (layout != GROM_LAYOUT_DENSE && layout != GROM_LAYOUT_SKEW_PACKED) || ((cp || form == GROM_FORM_SVD) && rank < 1))
+    return -1;
+  TuneShape s;
+  s.form = form;
+  s.storage = storage;
+  s.layout = layout;
+  s.max_batch = max_batch;
+  s.sm_count = sm_count;
+  s.n = n;
+  s.rank = rank;
+  if (form == GROM_FORM_FULL && storage == GROM_BF16) {
+    const bool packed = layout == GROM_LAYOUT_SKEW_PACKED;
+    s.tensor = true;
+    s.lp = k1_plan(n, storage, sm_count, packed ? 1 : 0).lp;
+    s.k2_scratch = packed ? k2p_scratch_need(n, s.lp, max_batch, sm_count) : k2_scratch_need(n, max_batch, sm_count);
+  } else if (cp && storage == GROM_BF16) {
+    s.tensor = true;
+    s.k3t_scratch = k3t_scratch_need(n, rank, form, max_batch, sm_count);
+  }
+  std::vector<grom_tuning> v;
+  tune_space(s, batch, v);
+  for (size_t i = 0; i < v.size() && (int64_t)i < cap; ++i) out[i] = v[i];
+  return (int32_t)v.size();
+}
+
+grom_status grom_autotune(grom_rom* r, int32_t batch, int32_t reps, grom_tuning* out) {
+  if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: null rom");
+  if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: batch out of range");
+  if (reps < 0 || reps > 10000) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: reps out of range");
+  if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: tensor rows missing");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  GROM_CUDA_TRY(cudaStreamIsCapturing(r->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: the stream is being captured");
+  grom_status st = grom_sync(r);  // earlier work's errors are reported as they are
+  if (st) return st;
+  if (reps == 0) reps = 10;
+  const TuneShape shape = shape_of(r);
+  std::vector<grom_tuning> cand;
+  tune_space(shape, batch, cand);
+  if (shape.tensor && (st = build_k2_tiles(r))) return st;
+
+  const int64_t n = r->n, cnt = (int64_t)batch * n;
+  std::vector<double> hu((size_t)cnt);
+  for (int64_t b = 0; b < batch; ++b)
+    for (int64_t i = 0; i < n; ++i) hu[(size_t)(b * n + i)] = std::cos(0.37 * (double)(i + 1) + 1.3 * (double)b) / (double)(i + 1);
+  const size_t bucket = (size_t)((batch + 15) / 16) - 1;
+  if (r->tuning.size() <= bucket) r->tuning.resize(bucket + 1, grom_tuning{});
+  const grom_tuning saved = r->tuning[bucket];
+  const int saved_choice = r->kernel_choice;
+  const bool saved_prof = r->prof;
+  double *du = nullptr, *dc = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  auto finish = [&](grom_status code) {
+    cudaStreamSynchronize(r->stream);
+    r->kernel_choice = saved_choice;
+    r->prof = saved_prof;
+    if (code != GROM_OK) r->tuning[bucket] = saved;
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (du) cudaFree(du);
+    if (dc) cudaFree(dc);
+    ++r->version;  // captured graphs hold the plans
+    return code;
+  };
+  if ((st = dmalloc(&du, (size_t)cnt * sizeof(double), nullptr)) ||
+      (st = dmalloc(&dc, (size_t)cnt * sizeof(double), nullptr)))
+    return finish(st);
+  if (cudaMemcpy(du, hu.data(), (size_t)cnt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+    return finish(cuda_fail(cudaGetLastError(), "grom_autotune"));
+  r->kernel_choice = GROM_KERNEL_AUTO;  // the entry under test picks the kernel
+  r->prof = false;
+  for (grom_tuning& c : cand) {
+    r->tuning[bucket] = c;
+    for (int w = 0; w < 2; ++w)
+      if ((st = grom_nonlinear(r, batch, du, dc))) return finish(st);
+    float g[3];
+    for (int q = 0; q < 3; ++q) {
+      if (cudaEventRecord(ev[0], r->stream) != cudaSuccess) return finish(cuda_fail(cudaGetLastError(), "grom_autotune"));
+      for (int k = 0; k < reps; ++k)
+        if ((st = grom_nonlinear(r, batch, du, dc))) return finish(st);
+      float ms = 0.f;
+      if (cudaEventRecord(ev[1], r->stream) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess)
+        return finish(cuda_fail(cudaGetLastError(), "grom_autotune"));
+      g[q] = ms / (float)reps;
+    }
+    std::sort(g, g + 3);
+    c.ms = g[1];
+  }
+  if ((st = grom_sync(r))) return finish(st);
+  size_t best = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (cand[i].ms < cand[best].ms) best = i;
+  grom_tuning chosen = cand[best].ms < 0.98f * cand[0].ms ? cand[best] : cand[0];
+  chosen.timed = (int32_t)cand.size();
+  chosen.ms_rule = cand[0].ms;
+  r->tuning[bucket] = chosen;
+  if (out) *out = chosen;
+  return finish(GROM_OK);
+}
+
+grom_status grom_set_tuning(grom_rom* r, const grom_tuning* t) {
+  if (!r || !t) return fail(GROM_ERR_INVALID_ARG, "grom_set_tuning: null argument");
+  if (t->batch < 1 || t->batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_set_tuning: batch out of range");
+  const size_t bucket = (size_t)((t->batch + 15) / 16) - 1;
+  if (t->kernel == GROM_KERNEL_AUTO) {
+    if (bucket < r->tuning.size()) r->tuning[bucket] = grom_tuning{};
+    ++r->version;
+    return GROM_OK;
+  }
+  if (!tuning_ok(shape_of(r), *t))
+    return fail(GROM_ERR_INVALID_ARG, "grom_set_tuning: the ROM's plans do not admit this configuration");
+  if (t->kernel == GROM_KERNEL_TENSOR) {
+    grom_status st = build_k2_tiles(r);
+    if (st) return st;
+  }
+  if (r->tuning.size() <= bucket) r->tuning.resize(bucket + 1, grom_tuning{});
+  r->tuning[bucket] = *t;
+  ++r->version;
+  return GROM_OK;
+}
+
+grom_status grom_get_tuning(const grom_rom* r, int32_t batch, grom_tuning* out) {
+  if (!r || !out) return fail(GROM_ERR_INVALID_ARG, "grom_get_tuning: null argument");
+  if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_get_tuning: batch out of range");
+  const grom_tuning* t = tuned(r, batch);
+  if (t) {
+    *out = *t;
+  } else {
+    *out = grom_tuning{};
+    out->batch = batch;
+  }
   return GROM_OK;
 }
 

@@ -103,7 +103,8 @@ struct K2Args {
 // cuTensorMapEncodeTiled through the runtime's driver entry point (null when
 // the driver does not provide it); looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn();
-K2Plan k2_plan(int64_t n, int batch, int sm_count);
+// splits_force > 0 replaces the rule's split of the advecting index (capped at n).
+K2Plan k2_plan(int64_t n, int batch, int sm_count, int splits_force = 0);
 size_t k2_scratch_bytes(const K2Plan& p);
 bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np);
 // Tile-major BF16 copy of the stored tensor for K2 (every 256 x 64 tile of
@@ -130,7 +131,12 @@ struct K2PPlan {
   int64_t bp;      // padded batch
   size_t smem;
 };
-K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count);
+// m_force replaces the rule's tile height when k2p_tile_m_ok admits it.
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force = 0);
+bool k2p_tile_m_ok(int batch, int m);
+// Scratch of the largest plan over every batch a ROM with max_batch accepts.
+size_t k2_scratch_need(int64_t n, int max_batch, int sm_count);
+size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count);
 size_t k2p_scratch_bytes(const K2PPlan& p);
 bool k2p_make_tmap(CUtensorMap* m, const void* packed, int64_t n, int64_t lp);
 // Same arguments as K2 (fp/fq and tiled unused).
@@ -180,12 +186,15 @@ struct K3TPlan {
   int btile, ctiles;     // trajectories per column tile (<= 128), column tiles
   int64_t bp;
   int s1, s2;            // K splits of the two GEMMs
+  int s1_max, s2_max;    // their largest admissible values
   int stages, tmem_cols;
   size_t smem;
 };
 constexpr int K3T_MIN_BATCH = 16;
-K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count);
+// s1_force, s2_force in [1, s1_max] / [1, s2_max] replace the rule's splits.
+K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1_force = 0, int s2_force = 0);
 size_t k3t_scratch_bytes(const K3TPlan& p);
+size_t k3t_scratch_need(int64_t n, int64_t r, int form, int max_batch, int sm_count);
 size_t k3t_factor_bytes(int64_t n, int64_t r, int form);
 cudaError_t k3t_build_factors(const void* fa, const void* fb, const void* fc, int64_t n, int64_t rb, int64_t r,
                               int form, void* ft, void* ae, cudaStream_t s);
@@ -351,6 +360,8 @@ struct grom_rom {
   CUtensorMap k3t_tmap_ft, k3t_tmap_ae;
   void* k3p_scratch = nullptr;       // persistent CP stepper: partials, h, barrier
   size_t k2_scratch_bytes = 0;
+  size_t k3t_scratch_bytes = 0;
+  std::vector<grom_tuning> tuning;   // per batch bucket ceil(batch / 16); kernel 0: untuned
   bool prof = false;                 // kernel timing enabled
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs
   size_t prof_used = 0;              // pairs recorded since enable

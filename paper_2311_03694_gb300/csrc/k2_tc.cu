@@ -35,6 +35,8 @@
 // rank component) instead of u_bj u_bk, Cout = X_(1) (P kr Q).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "grom_internal.h"
 #include "tc.cuh"
 
@@ -431,7 +433,7 @@ bool k2_make_tmap(CUtensorMap* m, const void* tensor, int64_t n, int64_t np) {
   return r == CUDA_SUCCESS;
 }
 
-K2Plan k2_plan(int64_t n, int batch, int sm_count) {
+K2Plan k2_plan(int64_t n, int batch, int sm_count, int splits_force) {
   K2Plan p{};
   p.n = n;
   p.np = padded_n(n);
@@ -443,6 +445,7 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
   const int tiles = p.col_tiles * p.i_tiles;
   int splits = sm_count / tiles;
   if (splits < 1) splits = 1;
+  if (splits_force > 0) splits = splits_force;
   if (splits > n) splits = (int)n;
   p.splits = splits;
   const int b_bytes = 2 * btile * 128;  // hi and lo KR tiles
@@ -464,6 +467,13 @@ K2Plan k2_plan(int64_t n, int batch, int sm_count) {
 // split-K partials.
 size_t k2_scratch_bytes(const K2Plan& p) {
   return 4 * (2 * (size_t)p.bp * p.np + (size_t)p.splits * p.n * p.bp);
+}
+
+size_t k2_scratch_need(int64_t n, int max_batch, int sm_count) {
+  size_t need = 0;
+  for (int b = 16; b - 16 < max_batch; b += 16)
+    need = std::max(need, k2_scratch_bytes(k2_plan(n, b < max_batch ? b : max_batch, sm_count)));
+  return need;
 }
 
 cudaError_t k2_launch(const K2Plan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {

@@ -38,6 +38,8 @@
 // the window rows that cover k, in a fixed order (deterministic), in FP64.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "grom_internal.h"
 #include "tc.cuh"
 
@@ -404,32 +406,46 @@ static bool k2p_make_tmap_u(CUtensorMap* m, const void* u, int64_t np, int64_t b
 
 static size_t k2p_window_bytes(int wrows, int wpitch) { return ((size_t)wrows * wpitch * 4 + 15) / 16 * 16; }
 
-K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
+// Pipeline stages that fit beside the mirrored-entry window of an m-row tile.
+static int k2p_stages_for(int m, int wpitch, int stage) {
+  const size_t fixed = 1024 + k2p_window_bytes(m + 127, wpitch) + 4 * 128 * 4 + (size_t)(2 * 8 + 5) * 8 + 16;
+  const int st = (int)(((size_t)K2P_SMEM_MAX - fixed) / (size_t)stage);
+  return st > 8 ? 8 : st;
+}
+
+static int k2p_btile(int batch) {
+  const int btile = (batch + 15) / 16 * 16;
+  return btile > 128 ? 128 : btile;
+}
+
+// The tile heights the plan considers: m in [8, 32] that keep the deepest
+// pipeline the shared memory allows at m = 8 (the window grows with m).
+bool k2p_tile_m_ok(int batch, int m) {
+  if (m < 8 || m > 32) return false;
+  const int btile = k2p_btile(batch);
+  const int stage = K2P_A_BYTES + 2 * btile * 128;
+  const int s8 = k2p_stages_for(8, btile + 1, stage);
+  return k2p_stages_for(m, btile + 1, stage) >= (s8 < 3 ? s8 : 3);
+}
+
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force) {
   K2PPlan p{};
   p.n = n;
   p.np = padded_n(n);
   p.lp = lp;
-  int btile = (batch + 15) / 16 * 16;
-  if (btile > 128) btile = 128;
+  const int btile = k2p_btile(batch);
   p.btile = btile;
   p.col_tiles = (batch + btile - 1) / btile;
   p.bp = (int64_t)p.col_tiles * btile;
   p.pblks = (int)((lp + 127) / 128);
   p.wpitch = btile + 1;  // odd pitch: the 32 lanes of a warp hit 32 banks
   const int stage = K2P_A_BYTES + 2 * btile * 128;
-  auto stages_for = [&](int m) {
-    const size_t fixed = 1024 + k2p_window_bytes(m + 127, p.wpitch) + 4 * 128 * 4 + (size_t)(2 * 8 + 5) * 8 + 16;
-    int st = (int)(((size_t)K2P_SMEM_MAX - fixed) / (size_t)stage);
-    return st > 8 ? 8 : st;
-  };
-  // test indices per tile: the largest m in [8, 32] whose tile count fills
-  // whole waves of SMs best, among those that keep the deepest pipeline the
-  // shared memory allows at m = 8 (the window grows with m)
-  const int st_max = stages_for(8) < 3 ? stages_for(8) : 3;
+  // test indices per tile: among the heights k2p_tile_m_ok admits, the
+  // largest whose tile count fills whole waves of SMs best
   double best = -1.0;
   int bm = 8;
   for (int m = 32; m >= 8; --m) {
-    if (stages_for(m) < st_max) continue;
+    if (!k2p_tile_m_ok(batch, m)) continue;
     const int64_t tiles = (n + m - 1) / m * p.pblks * p.col_tiles;
     const int64_t waves = (tiles + sm_count - 1) / sm_count;
     const double eff = (double)tiles / (double)(waves * sm_count);
@@ -438,11 +454,12 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
       bm = m;
     }
   }
+  if (m_force > 0 && k2p_tile_m_ok(batch, m_force)) bm = m_force;
   p.m = bm;
   p.ranges = (int)((n + bm - 1) / bm);
   p.tiles = p.ranges * p.pblks * p.col_tiles;
   p.wrows = bm + 127;
-  int st = stages_for(bm);
+  int st = k2p_stages_for(bm, p.wpitch, stage);
   if (st < 2) st = 2;
   p.stages = st;
   p.smem = 1024 + (size_t)st * stage + k2p_window_bytes(p.wrows, p.wpitch) + 4 * 128 * 4 + (size_t)(2 * st + 5) * 8 + 16;
@@ -457,6 +474,13 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count) {
 size_t k2p_scratch_bytes(const K2PPlan& p) {
   const size_t st = (size_t)p.bp * p.np;
   return st * (4 + 2 + 2) + 4 * ((size_t)p.pblks * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
+}
+
+size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count) {
+  size_t need = 0;
+  for (int b = 16; b - 16 < max_batch; b += 16)
+    need = std::max(need, k2p_scratch_bytes(k2p_plan(n, lp, b < max_batch ? b : max_batch, sm_count)));
+  return need;
 }
 
 cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {

@@ -27,6 +27,8 @@
 // back.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "grom_internal.h"
 #include "tc.cuh"
 
@@ -290,14 +292,20 @@ static bool k3t_tmap(CUtensorMap* m, const void* base, int64_t cols, int64_t row
   return r == CUDA_SUCCESS;
 }
 
-static int k3t_splits(int64_t tiles, int64_t kblocks, int sm_count) {
+// Largest split of a K range of kblocks 64-wide blocks: at least 4 K steps per split.
+static int k3t_split_max(int64_t kblocks) { return (int)(kblocks / 4 > 1 ? kblocks / 4 : 1); }
+
+// Splits of one GEMM: enough CTAs to cover the SMs, within k3t_split_max;
+// `force` in [1, k3t_split_max] replaces the rule.
+static int k3t_splits(int64_t tiles, int64_t kblocks, int sm_count, int force) {
+  const int kmax = k3t_split_max(kblocks);
+  if (force >= 1 && force <= kmax) return force;
   int s = (int)(sm_count / (tiles > 0 ? tiles : 1));
-  const int kmax = (int)(kblocks / 4 > 1 ? kblocks / 4 : 1);  // at least 4 K steps per split
   if (s > kmax) s = kmax;
   return s < 1 ? 1 : s;
 }
 
-K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count) {
+K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1_force, int s2_force) {
   K3TPlan p{};
   p.n = n;
   p.np = padded_n(n);
@@ -316,8 +324,10 @@ K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count) {
   p.ctiles = (batch + btile - 1) / btile;
   p.bp = (int64_t)p.ctiles * btile;
   const int64_t mt1 = (p.m1 + 127) / 128, mt2 = (p.m2 + 127) / 128;
-  p.s1 = k3t_splits(mt1 * p.ctiles, p.k1 / 64, sm_count);
-  p.s2 = k3t_splits(mt2 * p.ctiles, p.k2 / 64, sm_count);
+  p.s1 = k3t_splits(mt1 * p.ctiles, p.k1 / 64, sm_count, s1_force);
+  p.s2 = k3t_splits(mt2 * p.ctiles, p.k2 / 64, sm_count, s2_force);
+  p.s1_max = k3t_split_max(p.k1 / 64);
+  p.s2_max = k3t_split_max(p.k2 / 64);
   const int stage = K3T_A_BYTES + 2 * btile * 128;
   int st = (int)((K3T_SMEM_MAX - 1024 - 256) / stage);
   if (st > 6) st = 6;
@@ -333,6 +343,13 @@ K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count) {
 size_t k3t_scratch_bytes(const K3TPlan& p) {
   return 2 * (size_t)p.bp * p.np * 2 + 4 * (size_t)p.s1 * p.m1 * p.bp + 2 * (size_t)p.bp * p.k2 * 2 +
          4 * (size_t)p.s2 * p.m2 * p.bp;
+}
+
+size_t k3t_scratch_need(int64_t n, int64_t r, int form, int max_batch, int sm_count) {
+  size_t need = 0;
+  for (int b = 16; b - 16 < max_batch; b += 16)
+    need = std::max(need, k3t_scratch_bytes(k3t_plan(n, r, form, b < max_batch ? b : max_batch, sm_count)));
+  return need;
 }
 
 size_t k3t_factor_bytes(int64_t n, int64_t r, int form) {
