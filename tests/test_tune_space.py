@@ -137,3 +137,38 @@ def test_binding_structs_match_the_header(cls, struct, tmp_path):
     got = _c_layout(struct, names, tmp_path)
     assert got[0] == ctypes.sizeof(cls)
     assert got[1:] == [getattr(cls, f).offset for f in names]
+
+
+class _FakeRom:
+    """Stands in for a Rom in the cache logic: autotune returns a fixed entry
+    per batch, set_tuning records what is installed."""
+
+    form, storage, layout, n, rank, max_batch = "full", "bf16", "skew_packed", 512, 0, 1024
+
+    def __init__(self, tile_m=0):
+        self.tile_m = tile_m
+        self.installed = []
+
+    def autotune(self, batch, reps=0):
+        return {"batch": batch, "kernel": "tensor", "tile_m": self.tile_m, "split_a": 0, "split_b": 0, "timed": 3,
+                "ms": 1.0, "ms_rule": 1.0}
+
+    def set_tuning(self, e):
+        self.installed.append(e)
+
+
+def test_tuning_cache_merges_per_bucket_and_reapplies(tmp_path):
+    from paper_2311_03694_gb300 import tune
+
+    path = str(tmp_path / "cache.json")
+    tune.tune(_FakeRom(20), [16, 64], SM, path=path)
+    # a later run for a batch of the same bucket as 64 replaces that entry
+    tune.tune(_FakeRom(24), [60, 256], SM, path=path)
+    rom = _FakeRom()
+    assert tune.apply(rom, SM, path) == 3
+    assert [(e["batch"], e["tile_m"]) for e in rom.installed] == [(16, 20), (60, 24), (256, 24)]
+    # another device (SM count) or ROM shape has its own key
+    assert tune.apply(_FakeRom(), SM - 4, path) == 0
+    other = _FakeRom()
+    other.n = 256
+    assert tune.apply(other, SM, path) == 0
