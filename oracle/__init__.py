@@ -15,6 +15,7 @@ passage each one follows:
 * ``cp_reconstruct``      Kruskal operator                    Sec. 2.3, eq. cpd
 * ``rom_step``            BDFk/EXTk step with cached Cholesky Sec. 2.2, eq. nse_d1
 * ``cr_als``, ``cr_als_skew``, ``cost_reduction``              Sec. 4, eq. compress_ratio; Sec. 3.1
+* ``amdahl_speedup``      1 / ((1 - f) + f / reduction)         Sec. 4.1.2-4.1.4 (theoretical speedup)
 
 Index convention: C[i, j, k] with i the test index, j the advecting index
 and k the advected index.
@@ -83,6 +84,8 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = [i64, i64]
             fn.restype = dbl
+        lib.oracle_amdahl_speedup.argtypes = [dbl, dbl]
+        lib.oracle_amdahl_speedup.restype = dbl
         _lib = lib
     return _lib
 
@@ -403,3 +406,7 @@ def cr_svd(n, r):
 
 def cost_reduction(n, r):
     return _load().oracle_cost_reduction(n, r)
+
+
+def amdahl_speedup(frac, reduction):
+    return _load().oracle_amdahl_speedup(float(frac), float(reduction))

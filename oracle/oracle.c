@@ -413,5 +413,9 @@ int oracle_rom_step(const oracle_rom* m, double* hist, int64_t nsteps, double* e
 double oracle_cr_als(int64_t n, int64_t r) { return (double)n * (double)n / (3.0 * (double)r); }
 double oracle_cr_als_skew(int64_t n, int64_t r) { return 2.0 * (double)n * (double)n / (3.0 * (double)r); }
 double oracle_cost_reduction(int64_t n, int64_t r) { return (double)n * (double)n / (3.0 * (double)r); }
+/* Whole-solve speedup when a fraction `frac` of the time is the contraction
+ * and its cost falls by `reduction`, the rest unchanged (Amdahl's law; the
+ * "theoretical speedup" of Sec. 4.1.2-4.1.4). */
+double oracle_amdahl_speedup(double frac, double reduction) { return 1.0 / ((1.0 - frac) + frac / reduction); }
 /* Compression ratio of the SVD-ROM: N^3 / (N^2 R) (Sec. 4.4.2). */
 double oracle_cr_svd(int64_t n, int64_t r) { return (double)n / (double)r; }
