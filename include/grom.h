@@ -224,7 +224,9 @@ int64_t grom_rom_bytes(const grom_rom* rom);
 
 /* Choice of the contraction kernel.  AUTO picks the tensor-core kernel for
  * BF16 storage and batches above 8 trajectories (full form) or of 16 and more
- * (CP forms), else the streaming (full) or SIMT (CP) kernels. */
+ * (CP forms), else the streaming (full) or SIMT (CP) kernels; an autotuning
+ * entry for the batch's bucket (grom_autotune, grom_set_tuning) replaces that
+ * rule. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass, one
                                 launch per step (no persistent stepper); CP forms: the SIMT
