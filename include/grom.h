@@ -341,7 +341,9 @@ grom_status grom_server_create(int64_t hbm_budget_bytes, int32_t quantum_steps, 
                                grom_server** out);
 /* Makes `rom` resident with a pool of max_slots slots (max_slots <= the ROM's
  * max_batch).  Charged: the ROM's bytes plus the pool; GROM_ERR_BUDGET if it
- * does not fit.  The ROM must outlive the server. */
+ * does not fit.  The ROM must outlive the server.  The pool is stepped as one
+ * batch of max_slots trajectories, so a tuning entry for that batch
+ * (grom_autotune(rom, max_slots, ...) before serving) applies to it. */
 grom_status grom_server_add_rom(grom_server* s, grom_rom* rom, int32_t max_slots, int32_t* model);
 /* Simulation mode only: a model of n modes occupying rom_bytes whose batched
  * step takes step_seconds. */
