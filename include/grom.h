@@ -90,9 +90,10 @@ typedef int32_t grom_status;
  * The caller's tensor must be skew to rounding.  While uploading, the library
  * forms the probe sum_ijk x_i y_j x_k C_ijk for two seeded +-1 vector pairs
  * (zero for a skew tensor, about ||sym(C)||_F otherwise) and rejects the
- * tensor with GROM_ERR_INVALID_ARG if a probe exceeds 1e-9 ||C||_F.  The
- * tensor-core batched kernel needs the dense layout; packed ROMs evaluate
- * every batch with the streaming kernel. */
+ * tensor with GROM_ERR_INVALID_ARG if a probe exceeds 1e-9 ||C||_F.  With
+ * BF16 storage, batches of the packed tensor go to the factored tensor-core
+ * kernel K2P (see GROM_KERNEL_TENSOR); with the other storage types, every
+ * batch goes to the streaming kernel. */
 #define GROM_LAYOUT_DENSE 0
 #define GROM_LAYOUT_SKEW_PACKED 1
 
