@@ -359,8 +359,9 @@ grom_status grom_serve(grom_server* s, const grom_request* reqs, int32_t count, 
 grom_status grom_server_destroy(grom_server* s);
 
 /* Kernel timing: while enabled, the library records CUDA events on the ROM's
- * stream around every launch of its main contraction kernel (K1 streaming
- * kernel for the full form, the CP projection+expansion for CP forms).
+ * stream around every launch of its main contraction kernel (full form: the
+ * streaming kernel K1/K1P, or K2/K2P for batches on the tensor cores; CP
+ * forms: the projection and expansion kernels together).
  * grom_profile_read synchronises and returns the summed device time in ms and
  * the number of timed launches since the last enable. */
 grom_status grom_profile_enable(grom_rom* rom, int32_t enable);
