@@ -205,6 +205,44 @@ def test_inviscid_energy_drift_is_third_order_with_exact_history():
     assert np.all(np.abs(_order(started) - 2.0) < 0.2), started
 
 
+def test_scalar_cp_model_closed_form_and_blow_up():
+    # n = 1, rank 1: c = a b c u^2, so du/dt = -k u^2 with k = abc, solved by
+    # u(t) = u0 / (1 + k u0 t).  For k u0 > 0 the state decays, and the stepper
+    # with its BDF1/BDF2 startup converges to it at order 2.  For k u0 < 0 the
+    # solution blows up at t* = -1/(k u0), which the unstructured CP form can
+    # do (Sec. 4.1: plain CP-ROMs at low rank diverge, skew ones do not).
+    u0, T = 1.0, 1.0
+    one = np.ones((1, 1))
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        rom = oracle.Rom("cp", 1, np.zeros(1), 0.0, dt, factors=(2.0 * one, one, one))
+        h = rom.initial_history(np.array([u0]))
+        rom.step(h, int(round(T / dt)))
+        errs.append(abs(h[0] - u0 / (1.0 + 2.0 * u0 * T)))
+    assert np.all(np.abs(_order(errs) - 2.0) < 0.2), errs
+    rom = oracle.Rom("cp", 1, np.zeros(1), 0.0, 1e-3, factors=(-one, one, one))
+    h = rom.initial_history(np.array([u0]))
+    rom.step(h, 900)  # t = 0.9 < t* = 1: still the closed form
+    assert abs(h[0] - u0 / (1.0 - u0 * 0.9)) < 1e-3 * 10.0
+    with np.errstate(all="ignore"):
+        rom.step(h, 600)  # past t*
+    assert not np.isfinite(h[0]) or abs(h[0]) > 1e6
+
+
+def test_skew_cp_model_stays_bounded():
+    # the skew CP structure conserves u^T u / 2 at nu = 0 (u^T c(u) = 0), so
+    # even a large initial state only drifts by the scheme's error
+    n, r = 4, 2
+    U, V, W = (synth.normal(synth.seed_for(0) + 21, 40 + q, 0, n * r).reshape(n, r) for q in range(3))
+    u0 = 3.0 * synth.initial_condition(n, synth.seed_for(0) + 21)[0]
+    rom = oracle.Rom("cp_skew", n, np.zeros(n), 0.0, 1e-3, factors=(U, V, W))
+    h = rom.initial_history(u0)
+    e, inv = rom.step(h, 2000, want_energy=True, want_invariant=True)
+    e0 = 0.5 * u0 @ u0
+    assert np.all(np.isfinite(h)) and np.max(np.abs(e - e0)) <= 1e-4 * e0
+    assert np.max(np.abs(inv)) <= 1e-12 * np.max(e)
+
+
 def test_energy_and_invariant_outputs():
     n, dt = 8, 1e-3
     C = synth.skew_normal_tensor(n, synth.seed_for(0))
