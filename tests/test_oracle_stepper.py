@@ -210,7 +210,7 @@ def test_scalar_cp_model_closed_form_and_blow_up():
     # u(t) = u0 / (1 + k u0 t).  For k u0 > 0 the state decays, and the stepper
     # with its BDF1/BDF2 startup converges to it at order 2.  For k u0 < 0 the
     # solution blows up at t* = -1/(k u0), which the unstructured CP form can
-    # do (Sec. 4.1: plain CP-ROMs at low rank diverge, skew ones do not).
+    # do (Sec. 4.3: plain CPD-ROMs at low rank diverge, skew ones do not).
     u0, T = 1.0, 1.0
     one = np.ones((1, 1))
     errs = []
