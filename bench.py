@@ -72,6 +72,8 @@ def parse_args():
     p.add_argument("--als-ridge", type=float, default=1e-5, help="relative ridge of the ALS normal equations")
     p.add_argument("--layout", default="skew_packed", choices=["skew_packed", "dense"],
                    help="stored layout of the headline tensor")
+    p.add_argument("--autotune", action="store_true",
+                   help="batched section: also autotune each BF16 batched ROM (grom_autotune) and re-time it")
     return p.parse_args()
 
 
@@ -201,6 +203,26 @@ def kernel_traffic(kernel_key):
 
 
 # ------------------------------------------------------------------ timing
+def time_steps(torch, tr, steps, stream):
+    """ms per step of `steps` steps of an existing trajectory batch (one
+    untimed step first, so captured graphs are rebuilt outside the region)."""
+    tr.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def autotuned(torch, rom, tr, batch, steps, stream):
+    """Autotune the ROM for the batch, then re-time the same trajectories."""
+    t = rom.autotune(batch)
+    ms = time_steps(torch, tr, steps, stream)
+    return {"entry": t, "ms_per_step": ms, "trajectory_steps_per_s": batch * 1e3 / ms}
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -675,6 +697,8 @@ def main():
                 torch.cuda.synchronize()
                 errs = [rel(cf[b].cpu().numpy(), oracle.nonlinear_full(Ch, U0[b])) for b in range(min(3, B))]
                 entry["eval_rel_err_vs_fp64_oracle_max3"] = max(errs)
+            if args.autotune:
+                entry["autotuned"] = autotuned(torch, brom, btr, B, bsteps, stream)
             code_b, _ = btr.status()
             entry["status"] = grom.ERRORS.get(code_b, "OK") if code_b else "OK"
             batched["B%d" % B] = entry
@@ -709,6 +733,8 @@ def main():
                 torch.cuda.synchronize()
                 errs = [rel(cf[b].cpu().numpy(), oracle.nonlinear_full(Ch, U0[b])) for b in range(min(3, B))]
                 pentry["eval_rel_err_vs_fp64_oracle_max3"] = max(errs)
+            if args.autotune:
+                pentry["autotuned"] = autotuned(torch, prom, ptr, B, bsteps, stream)
             code_p, _ = ptr.status()
             pentry["status"] = grom.ERRORS.get(code_p, "OK") if code_p else "OK"
             batched["B%d_packed" % B] = pentry
@@ -731,6 +757,8 @@ def main():
                     "alg_tflops": cflops / (cms * 1e-3) / 1e12,
                     "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
                                else "k3g project/expand (register-tiled GEMMs)" if B >= 16 else "k3 project/expand")}
+                if args.autotune and storage == "bf16":
+                    batched["B%d_cpd_%s" % (B, storage)]["autotuned"] = autotuned(torch, crom, ctr, B, bsteps, stream)
                 ctr.close()
                 crom.close()
 
