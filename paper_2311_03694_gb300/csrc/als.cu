@@ -664,6 +664,7 @@ grom_status grom_als_create(int32_t n, const double* tensor, void* stream, grom_
 
 grom_status grom_als_fit(grom_als* s, int32_t rank, int32_t method, int32_t iters, double lambda, int32_t subiters,
                          double ridge, double* fa, double* fb, double* fc, double* residual) {
+  TraceRange trace("grom_als_fit");
   if (!s || !fa || !fb || rank < 1 || iters < 0 || !(ridge >= 0.0))
     return fail(GROM_ERR_INVALID_ARG, "grom_als_fit: bad argument");
   if (method != GROM_ALS_PLAIN && method != GROM_ALS_SKEW) return fail(GROM_ERR_INVALID_ARG, "grom_als_fit: bad method");

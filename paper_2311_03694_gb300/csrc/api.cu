@@ -464,6 +464,7 @@ int32_t grom_max_n(int32_t form, int32_t storage) {
 }
 
 grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
+  TraceRange trace("grom_create");
   if (!d || !out) return fail(GROM_ERR_INVALID_ARG, "grom_create: null argument");
   *out = nullptr;
   if (d->reserved) return fail(GROM_ERR_INVALID_ARG, "grom_create: reserved fields must be zero");
@@ -830,6 +831,7 @@ grom_status grom_selftest_timeout(grom_rom* r, int64_t limit_ns) {
 int64_t grom_rom_bytes(const grom_rom* r) { return r ? (int64_t)r->total_bytes : 0; }
 
 grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* c) {
+  TraceRange trace("grom_nonlinear");
   if (!r || !u || !c) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: null argument");
   if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: batch out of range");
   if (!full_ready(r)) return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear: tensor rows missing");
@@ -886,6 +888,7 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
 }
 
 grom_status grom_traj_create(grom_rom* r, int32_t batch, const double* u0, grom_traj** out) {
+  TraceRange trace("grom_traj_create");
   if (!r || !u0 || !out) return fail(GROM_ERR_INVALID_ARG, "grom_traj_create: null argument");
   *out = nullptr;
   if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_traj_create: batch out of range");
@@ -1108,6 +1111,7 @@ static bool persistent_ok(const grom_traj* t, int nsteps) {
 }
 
 grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* invariant) {
+  TraceRange trace("grom_step");
   if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step: null trajectory");
   if (nsteps < 0) return fail(GROM_ERR_INVALID_ARG, "grom_step: nsteps < 0");
   grom_rom* r = t->rom;
@@ -1251,6 +1255,7 @@ static double* device_alias(const void* p) {
 }
 
 grom_status grom_step_host(grom_traj* t, int32_t nsteps, const double* u_in, double* u_out) {
+  TraceRange trace("grom_step_host");
   if (!t) return fail(GROM_ERR_INVALID_ARG, "grom_step_host: null trajectory");
   grom_rom* r = t->rom;
   const int64_t n = r->n;
@@ -1400,6 +1405,7 @@ int32_t grom_tune_space(int32_t form, int32_t storage, int32_t layout, int32_t n
 }
 
 grom_status grom_autotune(grom_rom* r, int32_t batch, int32_t reps, grom_tuning* out) {
+  TraceRange trace("grom_autotune");
   if (!r) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: null rom");
   if (batch < 1 || batch > r->max_batch) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: batch out of range");
   if (reps < 0 || reps > 10000) return fail(GROM_ERR_INVALID_ARG, "grom_autotune: reps out of range");

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
@@ -60,6 +62,15 @@ inline int storage_elem_bytes(int storage) {
 #include "k1_types.h"
 
 namespace grom {
+
+// NVTX range over a library call, shown by Nsight tools on the host timeline
+// next to the kernels it launches; a no-op when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // m = 0: the G-ROM (middle extent n, weights u); m > 0: middle extent m with
 // separate weights (the SVD-ROM)

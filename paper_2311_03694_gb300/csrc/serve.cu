@@ -171,6 +171,7 @@ grom_status grom_server_add_rom(grom_server* s, grom_rom* rom, int32_t max_slots
 
 grom_status grom_serve(grom_server* s, const grom_request* reqs, int32_t count, grom_result* results,
                        grom_serve_stats* stats) {
+  TraceRange trace("grom_serve");
   if (!s || (count > 0 && (!reqs || !results))) return fail(GROM_ERR_INVALID_ARG, "grom_serve: null argument");
   const int M = (int)s->models.size();
   for (int32_t q = 0; q < count; ++q) {
