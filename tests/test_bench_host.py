@@ -71,3 +71,22 @@ def test_peaks_measured_and_fallback(tmp_path, monkeypatch):
 def test_replica_throughput_counts_every_replica():
     assert bench.replica_throughput(0.5, 1) == pytest.approx(2000.0)
     assert bench.replica_throughput(0.5, 8) == pytest.approx(16000.0)
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the oracle arm of the bench on the host cores, at a small N
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--n", "64",
+                        "--steps", "3", "--warmup", "3"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] and d["dtype"] == "f64"
