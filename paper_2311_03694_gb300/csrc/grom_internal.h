@@ -112,7 +112,7 @@ struct K2Args {
   int tiled;  // 1: the tensor map covers the tile-major copy (k2_build_tiles)
 };
 // cuTensorMapEncodeTiled through the runtime's driver entry point (null when
-// the driver does not provide it); looked up once.
+// the CUDA driver does not provide it); looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn();
 // splits_force > 0 replaces the rule's split of the advecting index (capped at n).
 K2Plan k2_plan(int64_t n, int batch, int sm_count, int splits_force = 0);
