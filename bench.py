@@ -9,12 +9,15 @@ dt = 1e-3, initial state u_i ~ N(0,1)/i.
 
 One bench step is one BDF3/EXT3 step (advection term, extrapolation, cached
 reduced solve, energy/invariant, history rotation) of one trajectory of the
-headline model: the full G-ROM with the tensor stored in BF16 in the
-skew-packed layout (one entry of each pair C_ijk = -C_kji; the same model
-as the dense tensor), FP32 accumulation and FP64 state update.  The same step
-is also timed for the other storage types, for the dense layout and for the
-CPD-ROM (skew CP factors, rank N) and reported under "variants"; each result
-carries its error against the FP64 oracle.
+headline model: the full G-ROM at FP64 tolerance.  Its tensor is stored as
+F32X2 (hi = rn32(C), lo = rn32(C - hi): a 48-bit significand in 8 bytes) in
+the skew-packed layout (one entry of each pair C_ijk = -C_kji; the same model
+as the dense tensor), contracted in double-single FP32 arithmetic (error-free
+products and sums) with an FP64 state update; its per-evaluation error
+against the FP64 oracle is bounded by 1e-12 and printed in the line.  The
+same step is also timed for the other storage types (BF16, FP32, FP64), for
+the dense layout and for the CPD-ROM (skew CP factors, rank N) and reported
+under "variants"; each result carries its error against the FP64 oracle.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -40,7 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ROM steps/s at N=1024 (full vs CPD, FP64 vs BF16), HBM/TC roofline %, p99 latency"
 UNIT = "steps/s"
 NU, DT = 1e-2, 1e-3
-HEADLINE = ("full", "bf16")  # + the layout chosen by --layout (skew-packed by default)
+HEADLINE_FORM = "full"  # storage and layout: --storage (F32X2) and --layout (skew-packed)
 VARIANTS = [("full", "bf16", "skew_packed"), ("full", "f32", "skew_packed"), ("full", "f32x2", "skew_packed"),
             ("full", "f64", "skew_packed"), ("full", "bf16", "dense"), ("full", "f32", "dense"),
             ("full", "f32x2", "dense"), ("full", "f64", "dense"), ("cp_skew", "bf16", "dense"),
@@ -72,6 +75,8 @@ def parse_args():
     p.add_argument("--als-ridge", type=float, default=1e-5, help="relative ridge of the ALS normal equations")
     p.add_argument("--layout", default="skew_packed", choices=["skew_packed", "dense"],
                    help="stored layout of the headline tensor")
+    p.add_argument("--storage", default="f32x2", choices=["f32x2", "f64", "f32", "bf16"],
+                   help="storage of the headline tensor (f32x2: FP64 tolerance on the FP32 pipe)")
     p.add_argument("--autotune", action="store_true",
                    help="batched section: also autotune each BF16 batched ROM (grom_autotune) and re-time it")
     return p.parse_args()
@@ -270,6 +275,15 @@ def max_over_ranks(ms, device="cuda"):
     return float(t.item())
 
 
+def replica_initial_state(n, seed, rank_id):
+    """The trajectory that replica `rank_id` steps (1 x n FP64): the seeded
+    initial condition with trajectory index rank_id, so that every rank
+    advances its own independent problem of the same workload."""
+    import synth
+
+    return synth.initial_condition(n, seed, traj=rank_id)
+
+
 def replica_throughput(ms, world):
     """Steps per second of all replicas together, each stepping one trajectory."""
     return world * 1e3 / ms
@@ -411,7 +425,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(n, rank, args.layout),
+        "config": {"workload": _workload(n, rank),
+                   "storage": "FP64 dense tensor, FP64 loops on the host cores (the oracle, OpenMP over the "
+                              "test index)", "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT,
+                   "layout": "dense"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -436,13 +453,27 @@ def _row_len(n, layout):
     return _packed_len(n) if layout == "skew_packed" else (n + 63) // 64 * 64
 
 
-def _config(n, rank, layout):
-    how = ("in the skew-packed layout (one entry of each pair C_ijk = -C_kji)" if layout == "skew_packed"
-           else "in the dense layout")
-    return {"workload": "N=%d full G-ROM BDF3/EXT3, BF16 tensor storage %s, FP32 accumulation, FP64 state; "
-                        "CP-structured skew tensor (R=%d) + 1e-3 skew residual; one trajectory per GPU" % (n, how, rank),
+STORAGE_NAME = {"f32x2": "F32X2", "f64": "F64", "f32": "F32", "bf16": "BF16"}
+ARITH = {"f32x2": "F32X2 tensor (FP32 hi/lo pair, 48-bit significand), double-single FP32 contraction "
+                  "(error-free products and sums), FP64 state; FP64 tolerance (1e-12 per evaluation)",
+         "f64": "FP64 tensor, FP64 contraction and state",
+         "f32": "FP32 tensor, FP32 accumulation, FP64 state",
+         "bf16": "BF16 tensor, FP32 accumulation, FP64 state"}
+
+
+def _workload(n, rank):
+    """The model every arm steps (the same text for the GPU and the reference arm)."""
+    return ("N=%d full G-ROM, one BDF3/EXT3 step of one trajectory per GPU; CP-structured skew tensor (R=%d) "
+            "+ 1e-3 skew residual, A = diag((i/N)^2), B = I" % (n, rank))
+
+
+def _config(n, rank, layout, storage):
+    how = ("skew-packed layout (one entry of each pair C_ijk = -C_kji)" if layout == "skew_packed"
+           else "dense layout")
+    return {"workload": _workload(n, rank), "storage": "%s; %s" % (ARITH[storage], how),
             "n": n, "cp_rank": rank, "batch_per_gpu": 1, "nu": NU, "dt": DT, "layout": layout,
-            "l2": "inputs larger than L2 (stored tensor %.2f GB per step)" % (n * n * _row_len(n, layout) * 2 / 1e9)}
+            "l2": "inputs larger than L2 (stored tensor %.2f GB per step)" % (
+                n * n * _row_len(n, layout) * STORAGE_BYTES[storage] / 1e9)}
 
 
 # -------------------------------------------------------------------- main
@@ -470,7 +501,7 @@ def main():
     R = args.rank or n
     seed = synth.seed_for(2)
     C, factors, a = workload(n, R, seed, "cuda")
-    u0 = synth.initial_condition(n, seed, traj=rank_id)  # one trajectory per replica
+    u0 = replica_initial_state(n, seed, rank_id)  # one trajectory per replica
     hbm_peak, tc_peak, tc_sustained, peak_kind = peaks()
 
     def make_rom(form, storage, layout="dense"):
@@ -479,7 +510,7 @@ def main():
         return grom.Rom(n, form, storage, factors=factors, stiffness=a, nu=NU, dt=DT)
 
     # ---------------------------------------------------- headline, timed
-    rom = make_rom(*HEADLINE, args.layout)
+    rom = make_rom(HEADLINE_FORM, args.storage, args.layout)
     tr = grom.Trajectories(rom, u0)
     stream = torch.cuda.current_stream()
     tr.step(args.warmup)
@@ -520,22 +551,24 @@ def main():
 
     # roofline of the dominant kernel.  Its algorithmic bytes are the stored
     # tensor per step, N * N rows of round_up(N/2, 64) (skew-packed) or
-    # round_up(N, 64) (dense) BF16 values, times the steps one launch runs:
+    # round_up(N, 64) (dense) values of the storage type (8 bytes for F32X2
+    # and FP64, 4 for FP32, 2 for BF16), times the steps one launch runs:
     # the persistent stepper runs all K steps (streaming, finalize and step)
     # in one launch, the graph path one streaming launch per step.
     k1_avg_ms = k1_ms / max(1, k1_launches)
     steps_per_launch = args.steps // max(1, k1_launches)
-    step_bytes = float(n) * n * _row_len(n, args.layout) * STORAGE_BYTES[HEADLINE[1]]
+    step_bytes = float(n) * n * _row_len(n, args.layout) * STORAGE_BYTES[args.storage]
     alg_bytes = step_bytes * steps_per_launch
     achieved = alg_bytes / (k1_avg_ms * 1e-3) / 1e9
     persistent = steps_per_launch > 1
     kname = "k1pp" if persistent else ("k1_packed" if args.layout == "skew_packed" else "k1_stream")
-    traffic = kernel_traffic("%s_bf16_n%d" % (kname, n))
+    traffic = kernel_traffic("%s_%s_n%d" % (kname, args.storage, n))
+    stname = STORAGE_NAME[args.storage]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic * steps_per_launch if traffic else None,
-                "kernel": ("k1pp_kernel<BF16> (persistent stepper: streaming, finalize and BDF3/EXT3 step of "
-                           "%d steps in one launch)" % steps_per_launch) if persistent
-                else "%s_kernel<BF16> (finalize excluded)" % kname, "peak_kind": peak_kind,
+                "kernel": ("k1pp_kernel<%s> (persistent stepper: streaming, finalize and BDF3/EXT3 step of "
+                           "%d steps in one launch)" % (stname, steps_per_launch)) if persistent
+                else "%s_kernel<%s> (finalize excluded)" % (kname, stname), "peak_kind": peak_kind,
                 "kernel_ms": k1_avg_ms, "kernel_launches": k1_launches, "steps_per_launch": steps_per_launch,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "timing": "CUDA events around each launch in a second timed run of the same %d steps "
@@ -557,6 +590,7 @@ def main():
     e2e = {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
            "api": "grom_step_host(traj, 1, u_in=pinned host, u_out=pinned host)"}
     tr.close()
+    headline = {"storage": args.storage, "layout": args.layout, "tolerance": TOL[args.storage]}
     # launches in the headline timed region: one persistent launch, or per
     # step the streaming kernel and the fused finalize + step kernel
     timed_launches = 1 if persistent else 2 * args.steps
@@ -573,6 +607,13 @@ def main():
         c_full = oracle.nonlinear_full(Ch, u0[0])
         t_ref = time.perf_counter() - t_ref
         c_cp = oracle.nonlinear_cp_skew(*factors, u0[0])
+        ud = torch.from_numpy(u0.copy()).cuda()
+        cd = torch.empty_like(ud)
+        rom.nonlinear(ud, cd)
+        torch.cuda.synchronize()
+        headline["eval_rel_err_vs_fp64_oracle"] = rel(cd.cpu().numpy()[0], c_full)
+        headline["eval_max_abs_err_over_max_abs"] = float(np.max(np.abs(cd.cpu().numpy()[0] - c_full)) /
+                                                          np.max(np.abs(c_full)))
 
     # ------------------------------------------------------------ variants
     wanted = VARIANTS if args.variants == "all" else (
@@ -803,16 +844,36 @@ def main():
         cpu_baseline = {"value": k / tk, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                         "sample": "%d BDF3/EXT3 steps (after 1 untimed) of the N=%d FP64 full G-ROM on the "
                                   "host cores, OpenMP over the test index" % (k, n)}
-        # trajectory error of each full-form storage type and layout after 1 + k steps
+        # trajectory error after 1 + k steps: the headline, each full-form
+        # storage type and layout, and each CPD variant against the oracle's
+        # CPD-ROM (same factors, same steps)
+        tkey = "traj_rel_err_after_%d_steps" % (1 + k)
+        ht = grom.Trajectories(rom, u0)
+        ht.step(1 + k)
+        headline[tkey] = rel(ht.get_state()[0][:n], h[:n])
+        ht.close()
         for key in [k for k in variants if k.startswith("full_")]:
             storage = key.split("_")[1]
             vrom = make_rom("full", storage, variants[key]["layout"])
             vt = grom.Trajectories(vrom, u0)
             vt.step(1 + k)
             hv = vt.get_state()[0]
-            variants[key]["traj_rel_err_after_%d_steps" % (1 + k)] = rel(hv[:n], h[:n])
+            variants[key][tkey] = rel(hv[:n], h[:n])
             vt.close()
             vrom.close()
+        cpd_keys = [k for k in variants if k.startswith("cpd_")]
+        if cpd_keys:
+            cp_ref = oracle.Rom("cp_skew", n, a, NU, DT, factors=factors)
+            hc = cp_ref.initial_history(u0[0])
+            cp_ref.step(hc, 1 + k)
+            for key in cpd_keys:
+                vrom = make_rom("cp_skew", key.split("_")[1])
+                vt = grom.Trajectories(vrom, u0)
+                vt.step(1 + k)
+                variants[key][tkey] = rel(vt.get_state()[0][:n], hc[:n])
+                variants[key][tkey + "_cpd_vs_full_model_gap"] = rel(hc[:n], h[:n])
+                vt.close()
+                vrom.close()
         errors["oracle_full_eval_seconds"] = t_ref
 
     # ------------------------------------------------------ serving mix
@@ -825,8 +886,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": _config(n, R, args.layout),
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": _config(n, R, args.layout, args.storage),
+        "headline": headline,
         "roofline": roofline,
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
@@ -840,6 +902,7 @@ def main():
     }
     if errors:
         line["oracle"] = errors
+    rom.close()
     if rank_id == 0:
         out = json.dumps(line)
         print(out)
