@@ -333,9 +333,36 @@ def serving_section(args, grom, synth, torch, a_of):
            "steps_per_s": stats["trajectory_steps"] / stats["seconds"],
            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
            "peak_active": int(stats["peak_active"]), "peak_gb": stats["peak_bytes"] / 1e9}
+    # where the time goes: per resident ROM, the requests' demand and the
+    # pool's measured step time with all slots busy (one quantum on random
+    # states of the workload), i.e. the GPU time the demand needs at full pools
+    per_rom = {}
+    for q, (rom, (n_q, R_q, st_q)) in enumerate(zip(roms, keys)):
+        mask = models == q
+        demand = int(horizons[mask].sum())
+        tr = grom.Trajectories(rom, synth.initial_condition(n_q, seed, 50000, args.serve_slots))
+        tr.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(streams[q])
+        tr.step(16)
+        e1.record(streams[q])
+        torch.cuda.synchronize()
+        pool_ms = e0.elapsed_time(e1) / 16
+        tr.close()
+        per_rom["N%d_R%s_%s" % (n_q, "N" if R_q == n_q else "N/2", st_q)] = {
+            "requests": int(mask.sum()), "demand_trajectory_steps": demand,
+            "pool_ms_per_step_all_slots": pool_ms,
+            "pool_trajectory_steps_per_s": args.serve_slots * 1e3 / pool_ms,
+            "gpu_s_at_full_pools": demand / args.serve_slots * pool_ms * 1e-3}
+    res["per_rom"] = per_rom
+    res["per_rom_note"] = ("demand_trajectory_steps / slots x the pool's step time with every slot busy: the GPU "
+                           "seconds each ROM's requests need if its pool ran alone and full; pools on different "
+                           "streams overlap")
     # plain per-request FP64 full G-ROM: single-trajectory step time per N
     step_ms = {}
     finals_full = {}
+    sample_s = {}
     order = np.argsort(horizons)
     sample = list(order[:8])
     for n in ns:
@@ -356,8 +383,11 @@ def serving_section(args, grom, synth, torch, a_of):
         for q in sample:
             if ns[nidx[q]] == n:
                 t1 = grom.Trajectories(full_rom, u0s[q][None, :])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
                 t1.step(int(horizons[q]))
                 finals_full[q] = t1.get_state()[0][:n]
+                sample_s[q] = time.perf_counter() - t0
                 t1.close()
         full_rom.close()
         torch.cuda.empty_cache()
@@ -369,10 +399,19 @@ def serving_section(args, grom, synth, torch, a_of):
         end = start + horizons[q] * step_ms[ns[nidx[q]]] * 1e-3
         blat[q] = end - times[q]
     res["baseline_fp64_full_per_request"] = {
+        "kind": "modelled",
         "steps_per_s": float(horizons.sum() / (end - times.min())),
         "p50_latency_s": float(np.percentile(blat, 50)), "p99_latency_s": float(np.percentile(blat, 99)),
         "step_ms_by_n": {str(k): v for k, v in step_ms.items()},
-        "how": "measured single-trajectory FP64 full step time per N; requests served one at a time in arrival order"}
+        "how": "modelled: a FIFO queue of the requests served one at a time in arrival order, each step costing "
+               "the measured single-trajectory FP64 full step time of its N",
+        "measured_sample": {
+            "requests": len(sample_s), "trajectory_steps": int(sum(horizons[q] for q in sample_s)),
+            "seconds": float(sum(sample_s.values())),
+            "steps_per_s": float(sum(horizons[q] for q in sample_s) / max(sum(sample_s.values()), 1e-9)),
+            "modelled_seconds": float(sum(horizons[q] * step_ms[ns[nidx[q]]] * 1e-3 for q in sample_s)),
+            "how": "the %d shortest-horizon requests stepped one at a time through grom_step on the FP64 full "
+                   "G-ROM (wall clock per request, including the final-state read-back)" % len(sample_s)}}
     errs = {}
     for q, ref in finals_full.items():
         n, R, storage = keys[models[q]]
@@ -781,9 +820,13 @@ def main():
             batched["B%d_packed" % B] = pentry
             ptr.close()
             prom.close()
-            # the CPD-ROM (skew CP factors, rank N) on the same batch
-            for storage in ("bf16", "f64"):
+            # the CPD-ROM (skew CP factors, rank N) on the same batch: BF16
+            # factors on the tensor cores, FP64 factors in double-single FP32
+            # arithmetic (K3D, FP64 tolerance) and, for reference, in FP64
+            # arithmetic (K3g, GROM_KERNEL_STREAM)
+            for storage, kernel in (("bf16", "auto"), ("f64", "auto"), ("f64", "stream")):
                 crom = grom.Rom(n, "cp_skew", storage, factors=factors, stiffness=a, nu=NU, dt=DT, max_batch=B)
+                crom.set_kernel(kernel)
                 ctr = grom.Trajectories(crom, U0)
                 ctr.step(2)
                 torch.cuda.synchronize()
@@ -793,13 +836,26 @@ def main():
                 torch.cuda.synchronize()
                 cms = e0b.elapsed_time(e1b) / bsteps
                 cflops = 2.0 * 5 * n * R * B  # p, q, s projections and two expansions
-                batched["B%d_cpd_%s" % (B, storage)] = {
+                key = "B%d_cpd_%s%s" % (B, storage, "_fp64_gemm" if kernel == "stream" else "")
+                entry = {
                     "ms_per_step": cms, "trajectory_steps_per_s": B * 1e3 / cms,
                     "alg_tflops": cflops / (cms * 1e-3) / 1e12,
                     "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
-                               else "k3g project/expand (register-tiled GEMMs)" if B >= 16 else "k3 project/expand")}
+                               else "k3d project/expand (double-single FP32 GEMMs, FP64 tolerance)"
+                               if storage == "f64" and kernel == "auto" and B >= 16
+                               else "k3g project/expand (register-tiled FP64 GEMMs)" if B >= 16
+                               else "k3 project/expand")}
+                if rank_id == 0:
+                    uf = torch.from_numpy(U0.copy()).cuda()
+                    cf = torch.empty_like(uf)
+                    crom.nonlinear(uf, cf)
+                    torch.cuda.synchronize()
+                    errs = [rel(cf[b].cpu().numpy(), oracle.nonlinear_cp_skew(*factors, U0[b])) for b in range(min(3, B))]
+                    entry["eval_rel_err_vs_fp64_oracle_max3"] = max(errs)
+                    entry["tolerance"] = TOL[storage]
                 if args.autotune and storage == "bf16":
-                    batched["B%d_cpd_%s" % (B, storage)]["autotuned"] = autotuned(torch, crom, ctr, B, bsteps, stream)
+                    entry["autotuned"] = autotuned(torch, crom, ctr, B, bsteps, stream)
+                batched[key] = entry
                 ctr.close()
                 crom.close()
 
@@ -852,7 +908,7 @@ def main():
         ht.step(1 + k)
         headline[tkey] = rel(ht.get_state()[0][:n], h[:n])
         ht.close()
-        for key in [k for k in variants if k.startswith("full_")]:
+        for key in [k for k in variants if k.startswith("full_") and "augmented" not in k]:
             storage = key.split("_")[1]
             vrom = make_rom("full", storage, variants[key]["layout"])
             vt = grom.Trajectories(vrom, u0)

@@ -227,11 +227,15 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * BF16 storage and batches above 8 trajectories (full form) or of 16 and more
  * (CP forms), else the streaming (full) or SIMT (CP) kernels; an autotuning
  * entry for the batch's bucket (grom_autotune, grom_set_tuning) replaces that
- * rule. */
+ * rule.  FP64 CP ROMs step batches of 16 and more with K3D: the projections
+ * and the expansion as double-single FP32 GEMMs (every operand a hi/lo FP32
+ * pair, error-free products and sums) on hi/lo copies of the factors made at
+ * create, at FP64 tolerance (per-evaluation error ~1e-13 against FP64) and
+ * several times the FP64 GEMMs' speed on this part's FP32 pipe. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass, one
                                 launch per step (no persistent stepper); CP forms: the SIMT
-                                kernels (K3, K3g)                                            */
+                                kernels (K3, K3g; FP64 factors in FP64 arithmetic, no K3D)    */
 #define GROM_KERNEL_TENSOR 2 /* BF16 storage only.  Dense layout, K2: tcgen05 GEMM over the
                                 Khatri-Rao product of the states (Sec. 2.2, eq. Cu with the
                                 mode-1 matricisation).  Skew-packed layout, K2P: the factored
@@ -391,11 +395,25 @@ grom_status grom_profile_read(grom_rom* rom, double* total_ms, int64_t* launches
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  All calls share the one
  * array and it keeps the last call's partial sums, so calls that overlap on
- * the GPU (other streams, other host threads) race: serialise them.  A
- * device-side wait that times out leaves c unspecified; it is not reported
- * (the call does not synchronise). */
+ * the GPU (other streams, other host threads) race: serialise them.
+ * `stream` (cudaStream_t, NULL = the legacy default stream) must belong to
+ * the current device (GROM_ERR_INVALID_ARG otherwise), since the scratch
+ * address is the current device's.  The call does not synchronise: a
+ * device-side wait that times out leaves c unspecified and is reported by
+ * grom_nonlinear_full_noalloc_status.
+ *
+ * The library cannot check the extent of caller pointers: tensor must hold
+ * n*n rows of the stored layout, u and c n doubles, all on the current
+ * device; anything shorter makes the kernel read or write out of bounds. */
 grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, const void* tensor, const double* u,
                                         double* c, void* stream);
+
+/* Outcome of the last grom_nonlinear_full_noalloc call on the current device:
+ * reads its device error word on `stream` (the stream of that call) and
+ * synchronises the stream.  GROM_OK, or GROM_ERR_TIMEOUT when a device wait
+ * of that call gave up (its c is unspecified); the next call clears the
+ * word.  Allocates nothing. */
+grom_status grom_nonlinear_full_noalloc_status(void* stream);
 
 /* Self-test of failure detection: enqueues on the ROM's stream a kernel that
  * waits on a device barrier nothing ever signals, through the same bounded

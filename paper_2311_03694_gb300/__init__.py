@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build_mod
 
 GROM_OK = 0
+GROM_ERR_INVALID_ARG = 1
 ERRORS = {
     1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "TIMEOUT", 6: "BUDGET", 7: "UNSUPPORTED",
 }
@@ -108,6 +109,7 @@ EXPORTS = {
                           ctypes.c_int32),
     "grom_nonlinear_full_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "grom_nonlinear_full_noalloc_status": ([ctypes.c_void_p], ctypes.c_int32),
     "grom_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
                            ctypes.c_int32),
     "grom_server_add_rom": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
@@ -197,14 +199,47 @@ def tune_space(form, storage, n, batch, max_batch=None, rank=0, layout="dense", 
     return [_tuning_dict(buf[i]) for i in range(count)]
 
 
+def stored_row_bytes(n, storage):
+    """Bytes of one stored row (i, j) of the dense layout: round_up(n, 64)
+    elements of the storage type (F32X2: a hi and a lo plane of floats)."""
+    return (int(n) + 63) // 64 * 64 * STORAGE_BYTES[storage]
+
+
 def nonlinear_full_noalloc(n, storage, tensor, u, c, stream=None):
     """grom_nonlinear_full_noalloc: c = C(u)u for one trajectory without any
     library allocation.  tensor is a device tensor already in the stored
     layout (see include/grom.h and stored_layout()); u, c are float64 device
-    tensors of n entries."""
-    _check(load().grom_nonlinear_full_noalloc(int(n), STORAGE[storage], tensor.data_ptr(), _ptr(u), _ptr(c),
+    tensors of n entries.  The C entry point cannot see the extent of the
+    caller's buffers, so they are checked here: every operand on the current
+    device, tensor holding n*n stored rows, u and c n entries each."""
+    import torch
+
+    n = int(n)
+    if storage not in STORAGE:
+        raise GromError(GROM_ERR_INVALID_ARG, "unknown storage %r" % (storage,))
+    dev = torch.cuda.current_device()
+    for name, x in (("tensor", tensor), ("u", u), ("c", c)):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.device.index != dev:
+            raise GromError(GROM_ERR_INVALID_ARG, "%s must be a tensor on cuda:%d" % (name, dev))
+    if not tensor.is_contiguous():
+        raise GromError(GROM_ERR_INVALID_ARG, "tensor must be contiguous")
+    need = n * n * stored_row_bytes(max(n, 1), storage)
+    if tensor.numel() * tensor.element_size() < need:
+        raise GromError(GROM_ERR_INVALID_ARG, "tensor holds %d bytes, the stored layout of n=%d %s needs %d"
+                        % (tensor.numel() * tensor.element_size(), n, storage, need))
+    for name, x in (("u", u), ("c", c)):
+        if x.numel() != n:
+            raise GromError(GROM_ERR_INVALID_ARG, "%s has %d entries, n = %d" % (name, x.numel(), n))
+    _check(load().grom_nonlinear_full_noalloc(n, STORAGE[storage], tensor.data_ptr(), _ptr(u), _ptr(c),
                                               ctypes.c_void_p(_stream_handle(stream))))
     return c
+
+
+def nonlinear_full_noalloc_status(stream=None):
+    """grom_nonlinear_full_noalloc_status: raises GromError (GROM_ERR_TIMEOUT)
+    when a device wait of the last allocation-free call on this device gave
+    up; synchronises the stream."""
+    _check(load().grom_nonlinear_full_noalloc_status(ctypes.c_void_p(_stream_handle(stream))))
 
 
 def stored_layout(C, storage):
@@ -222,7 +257,13 @@ def stored_layout(C, storage):
     elif storage == "f32":
         out = P.to(torch.float32)
     elif storage == "bf16":
-        out = P.to(torch.bfloat16)
+        # one round-to-nearest-even from FP64 to the 8-bit significand (the
+        # library's rounding; a cast through FP32 would round twice): round
+        # the FP64 bit pattern at bit 45, after which the FP32 and BF16
+        # conversions are exact
+        bits = P.view(torch.int64)
+        bits = (bits + ((1 << 44) - 1) + ((bits >> 45) & 1)) & ~((1 << 45) - 1)
+        out = bits.view(torch.float64).to(torch.float32).to(torch.bfloat16)
     elif storage == "f32x2":
         hi = P.to(torch.float32)
         lo = (P - hi.to(torch.float64)).to(torch.float32)

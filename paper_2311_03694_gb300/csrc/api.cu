@@ -216,7 +216,7 @@ static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
-                  r->k3t_factors, r->k3t_scratch,
+                  r->k3t_factors, r->k3t_scratch, r->k3d_factors, r->k3d_scratch,
                   r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch,
                   r->k2_tiles};
   for (void* p : ptrs)
@@ -282,6 +282,12 @@ static bool is_cp(const grom_rom* r) { return r->form == GROM_FORM_CP || r->form
 
 static bool use_k3g(const grom_rom* r, int batch) {
   return is_cp(r) && batch >= K3G_MIN_BATCH && r->k3g_scratch;
+}
+
+// K3D: FP64 CP batches at FP64 tolerance in double-single FP32 arithmetic;
+// GROM_KERNEL_STREAM keeps the FP64 GEMMs of K3g
+static bool use_k3d(const grom_rom* r, int batch) {
+  return is_cp(r) && r->k3d_factors && batch >= K3G_MIN_BATCH && r->kernel_choice != GROM_KERNEL_STREAM;
 }
 
 // K3T: the batched CP form on the tensor cores (BF16 factors)
@@ -640,6 +646,15 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
                                           k3g_scratch_bytes(n, rp, r->max_batch, r->storage, r->sm_count),
                                           r->stream) != cudaSuccess)
       return bail(cuda_fail(cudaGetLastError(), "grom_create"));
+    if (r->storage == GROM_F64 && r->max_batch >= K3G_MIN_BATCH) {
+      // hi/lo FP32 copies of the factors for the double-single GEMMs (K3D)
+      if ((st = dmalloc(&r->k3d_factors, k3d_factor_bytes(n, rp), &r->total_bytes))) return bail(st);
+      const size_t kd = k3d_scratch_bytes(n, rp, r->max_batch, r->sm_count);
+      if ((st = dmalloc(&r->k3d_scratch, kd, &r->total_bytes))) return bail(st);
+      if (cudaMemsetAsync(r->k3d_scratch, 0, kd, r->stream) != cudaSuccess ||
+          k3d_build_factors(r->op, r->panel_bytes, n, rp, r->k3d_factors, r->stream) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "grom_create: double-single factor copies"));
+    }
     if (r->storage == GROM_BF16) {
       // the factors again, laid out for the tensor-core GEMMs (K3T), and the
       // scratch of the largest plan over the batch sizes this ROM accepts
@@ -879,6 +894,8 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     if (e0) prof_record(e0, r->stream);
     e = use_k3t(r, batch) ? k3t_launch(k3t_plan_of(r, batch), &r->k3t_tmap_ft,
                                        &r->k3t_tmap_ae, a, batch, r->k3t_scratch, r->err, r->stream)
+        : use_k3d(r, batch) ? k3d_launch(r->k3, a, r->k3d_factors, batch, r->max_batch, r->k3d_scratch, r->sm_count,
+                                         r->stream)
         : use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
                             : k3_launch(r->k3, r->storage, a, batch, r->stream);
     if (e1) prof_record(e1, r->stream);
@@ -1009,6 +1026,8 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   cudaError_t e = use_k3t(r, t->batch)
                       ? k3t_launch(k3t_plan_of(r, t->batch), &r->k3t_tmap_ft,
                                    &r->k3t_tmap_ae, a, t->batch, r->k3t_scratch, r->err, strm)
+                  : use_k3d(r, t->batch)
+                      ? k3d_launch(r->k3, a, r->k3d_factors, t->batch, r->max_batch, r->k3d_scratch, r->sm_count, strm)
                   : use_k3g(r, t->batch)
                       ? k3g_launch(r->k3, r->storage, a, t->batch, r->max_batch, r->k3g_scratch, r->sm_count, strm)
                       : k3_launch(r->k3, r->storage, a, t->batch, strm);

@@ -188,6 +188,15 @@ size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int 
 cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
                        int sm_count, cudaStream_t s);
 constexpr int K3G_MIN_BATCH = 16;
+// Batched CP form of FP64 ROMs at FP64 tolerance in double-single FP32
+// arithmetic (K3D, same batch sizes as K3g): hi/lo copies of the factors
+// made at create, then per step a state split and two GEMMs.
+size_t k3d_factor_bytes(int64_t n, int64_t rp);
+size_t k3d_scratch_bytes(int64_t n, int64_t rp, int max_batch, int sm_count);
+cudaError_t k3d_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, int64_t rp, void* out,
+                              cudaStream_t s);
+cudaError_t k3d_launch(const K3Plan& p, const K3Args& a, const void* factors, int batch, int max_batch,
+                       void* scratch, int sm_count, cudaStream_t s);
 // Batched CP form on the tensor cores (BF16 factors): projections and
 // expansion as two tcgen05 GEMMs over copies of the factors laid out for them.
 struct K3TPlan {
@@ -366,6 +375,8 @@ struct grom_rom {
   CUtensorMap k2_tmap_tiled;         // its TMA descriptor
   void* k2_scratch = nullptr;        // K2 state copy + split-K partials
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
+  void* k3d_factors = nullptr;       // batched FP64 CP in double-single arithmetic: hi/lo factor planes
+  void* k3d_scratch = nullptr;       // its states, products and split partials
   void* k3t_factors = nullptr;       // batched CP on tensor cores: FT | AE (BF16)
   void* k3t_scratch = nullptr;
   CUtensorMap k3t_tmap_ft, k3t_tmap_ae;

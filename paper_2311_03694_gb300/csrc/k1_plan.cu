@@ -81,7 +81,8 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed, int64_t m) {
     p.qm = pow2_ceil((P + K1_CONSUMERS - 1) / K1_CONSUMERS);
     rpr = P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
   }
-  const int64_t rmax = 8 / p.qm;  // rows a consumer thread holds in registers per chunk
+  const int64_t rmax = k1_rmax(p.qm, storage == GROM_F32X2 ? 2 : 1);  // rows a consumer thread holds per chunk
+  p.rpr = rpr;
   p.rpc = K1_STAGE_BYTES / p.row_bytes;
   if (p.rpc > rmax * rpr) p.rpc = rmax * rpr;
   if (p.rpc < 1) p.rpc = 1;

@@ -51,6 +51,16 @@ extern "C" grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, c
   int dev = 0;
   GROM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(GROM_ERR_UNSUPPORTED, "grom_nonlinear_full_noalloc: device index");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (s != nullptr) {
+    // the scratch address below belongs to the current device; a stream of
+    // another device would run the kernel against that device's memory
+    int sdev = -1;
+    GROM_CUDA_TRY(cudaStreamGetDevice(s, &sdev));
+    if (sdev != dev)
+      return fail(GROM_ERR_INVALID_ARG, "grom_nonlinear_full_noalloc: the stream belongs to device " +
+                                            std::to_string(sdev) + ", the current device is " + std::to_string(dev));
+  }
   DeviceSlot slot;
   {
     // Once per device, with that device current: resolve the device address
@@ -73,7 +83,6 @@ extern "C" grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, c
   if (need > kNoAllocScratchDoubles)
     return fail(GROM_ERR_UNSUPPORTED, "grom_nonlinear_full_noalloc: needs " + std::to_string(need * 8) +
                                           " bytes of scratch, more than the fixed 1 MiB");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // The timeout flag sits after the partials and must start at zero; every
   // partial the finalize step reads is written earlier in the same call.
   int* err = reinterpret_cast<int*>(slot.scratch + kNoAllocScratchDoubles);
@@ -88,5 +97,26 @@ extern "C" grom_status grom_nonlinear_full_noalloc(int32_t n, int32_t storage, c
   a.err = err;
   cudaError_t e = k1_launch(plan, storage, a, 1, s);
   if (e != cudaSuccess) return cuda_fail(e, "grom_nonlinear_full_noalloc launch");
+  return GROM_OK;
+}
+
+extern "C" grom_status grom_nonlinear_full_noalloc_status(void* stream) {
+  int dev = 0;
+  GROM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(GROM_ERR_UNSUPPORTED, "grom_nonlinear_full_noalloc_status: device index");
+  DeviceSlot slot;
+  {
+    std::lock_guard<std::mutex> lock(g_slots_mu);
+    slot = g_slots[dev];
+  }
+  if (!slot.ready) return GROM_OK;  // no call has run on this device
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int flag = 0;
+  const int* err = reinterpret_cast<const int*>(slot.scratch + kNoAllocScratchDoubles);
+  GROM_CUDA_TRY(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GROM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flag & DEV_ERR_TIMEOUT)
+    return fail(GROM_ERR_TIMEOUT, "grom_nonlinear_full_noalloc: a device wait of the last call timed out; c is unspecified");
+  if (flag) return fail(GROM_ERR_CUDA, "grom_nonlinear_full_noalloc: device error flags " + std::to_string(flag));
   return GROM_OK;
 }

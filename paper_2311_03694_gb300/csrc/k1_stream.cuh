@@ -20,6 +20,7 @@
 // (deterministic, no atomics).
 #pragma once
 
+#include "ds_arith.cuh"
 #include "grom_internal.h"
 #include "ptx.cuh"
 
@@ -84,20 +85,22 @@ struct Acc<GROM_BF16> {
   __device__ void zero() { v = 0.f; }
 };
 
-// Error-free accumulation of hi*u (double-single arithmetic on the FP32 pipe):
-// p + e = hi*uh exactly (FMA residual), t ~ hi*ul + lo*uh (lo*ul is below
-// 2^-48 relative and dropped), (S, s) += p + (e + t) with Knuth's TwoSum on
-// the leading part.  Intrinsics with explicit rounding keep the compiler from
-// contracting or reassociating the transformation.
-__device__ __forceinline__ void ds_fma(float hi, float lo, float uh, float ul, float& S, float& s) {
-  const float p = __fmul_rn(hi, uh);
-  const float e = __fmaf_rn(hi, uh, -p);
-  const float t = __fmaf_rn(hi, ul, __fmul_rn(lo, uh));
-  const float S1 = __fadd_rn(S, p);
-  const float bb = __fsub_rn(S1, S);
-  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(S1, bb)), __fsub_rn(p, bb));
-  S = S1;
-  s = __fadd_rn(s, __fadd_rn(err, __fadd_rn(e, t)));
+// Error-free accumulation of C*u for F32X2 storage: ds_mac (ds_arith.cuh) of
+// the stored (hi, lo) pair and the state's (uh, ul) pair into the
+// accumulator (S, s), which ds_renorm renormalises before every streamed
+// chunk (every 4 rows per accumulator at N = 1024).  Per-evaluation error at
+// N = 256 in a CPU emulation of the arithmetic: 3.7e-14, against 1.1e-13 for
+// Knuth's full TwoSum per term without renormalisation.
+template <int ST, int QM, int EPV, int NB, typename A>
+__device__ __forceinline__ void ds_renorm_all(A (&acc)[QM][EPV][NB]) {
+  if constexpr (ST == GROM_F32X2) {
+#pragma unroll
+    for (int q = 0; q < QM; ++q)
+#pragma unroll
+      for (int e = 0; e < EPV; ++e)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) ds_renorm(acc[q][e][b].S, acc[q][e][b].s);
+  }
 }
 
 // Loads one vector per trajectory of the pass into shared memory in the
@@ -278,13 +281,17 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
     // caps the rows per chunk accordingly).  It copies them to registers and
     // releases the stage at once, so the ring refills while it computes.
     // Offsets inside a stage are 32-bit; chunks advance without divisions.
-    constexpr int RMAX = 8 / QM;
     constexpr int PLANES = (ST == GROM_F32X2) ? 2 : 1;
+    constexpr int RMAX = k1_rmax(QM, PLANES);
     const int rowb = (int)row_bytes;
     const int t_off = (int)(ro * row_bytes + pos0 * 16);  // this thread's first vector in a stage
     const int t_step = (int)(rpr * row_bytes);             // next row of this thread
     const int plane_off = (int)(np * 4);                    // F32X2: lo plane
     const bool full_pos = act && (pos0 + (int64_t)(QM - 1) * K1_CONSUMERS < P);
+    // rows of a full chunk held by this thread (other chunks: the last of a test index)
+    int nrow_full = act ? ((int)pl.rpc - (int)ro + (int)rpr - 1) / (int)rpr : 0;
+    if (nrow_full > RMAX) nrow_full = RMAX;
+    if (nrow_full < 0) nrow_full = 0;
     (void)rowb;
     int64_t ci = c0 / pl.cpi, cj = c0 - ci * pl.cpi;
     int s = 0;
@@ -309,9 +316,12 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
       }
       const uint8_t* st = stages + s * K1_STAGE_BYTES + t_off;
       // rows of this chunk held by this thread
-      int nrow = act ? (rows - (int)ro + (int)rpr - 1) / (int)rpr : 0;
-      if (nrow > RMAX) nrow = RMAX;
-      if (nrow < 0) nrow = 0;
+      int nrow = nrow_full;
+      if (rows != (int)pl.rpc) {
+        nrow = act ? (rows - (int)ro + (int)rpr - 1) / (int)rpr : 0;
+        if (nrow > RMAX) nrow = RMAX;
+        if (nrow < 0) nrow = 0;
+      }
       uint4 vec[RMAX][QM][PLANES];
       if (full_pos && nrow == RMAX) {
 #pragma unroll
@@ -339,6 +349,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
       // zero vectors of rows beyond nrow contribute nothing; u_j of such rows
       // is read at a clamped, valid index
       const int jt = j0 + (int)ro;
+      ds_renorm_all<ST>(acc);
 #pragma unroll
       for (int t = 0; t < RMAX; ++t) {
         if (t >= nrow) break;
@@ -370,10 +381,10 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
             const uint4 l = vec[t][q][PLANES - 1];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              ds_fma(__uint_as_float(h.x), __uint_as_float(l.x), uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
-              ds_fma(__uint_as_float(h.y), __uint_as_float(l.y), uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
-              ds_fma(__uint_as_float(h.z), __uint_as_float(l.z), uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
-              ds_fma(__uint_as_float(h.w), __uint_as_float(l.w), uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
+              ds_mac(__uint_as_float(h.x), __uint_as_float(l.x), uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
+              ds_mac(__uint_as_float(h.y), __uint_as_float(l.y), uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
+              ds_mac(__uint_as_float(h.z), __uint_as_float(l.z), uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
+              ds_mac(__uint_as_float(h.w), __uint_as_float(l.w), uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
             }
           }
         } else if constexpr (ST == GROM_F32) {

@@ -13,6 +13,10 @@ constexpr int K1_THREADS = K1_CONSUMERS + 32;     // + one producer warp
 constexpr int K1_STAGES = 6;
 constexpr int K1_STAGE_BYTES = 32768;
 constexpr int K1_MAX_ROW_BYTES = K1_STAGE_BYTES;
+// Rows of a chunk one consumer thread holds in registers: 8 16-byte vectors
+// over its QM positions and the storage's planes (F32X2: hi and lo).  The
+// plan caps the rows per chunk at this many per thread row step.
+__host__ __device__ constexpr int k1_rmax(int qm, int planes) { return 8 / (qm * planes); }
 
 struct K1Plan {
   int64_t n, np;
@@ -23,6 +27,7 @@ struct K1Plan {
   int has_mid;         // 1: the middle weights come from K1Args::mid
   int64_t row_bytes;   // stored elements per row (np, or lp when packed) * element bytes
   int64_t rpc;         // rows per chunk (all in one test index i)
+  int64_t rpr;         // rows between a consumer thread's consecutive rows of a chunk
   int64_t cpi;         // chunks per test index
   int64_t T;           // total chunks = n * cpi
   int grid;            // persistent CTAs

@@ -138,13 +138,17 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     const int64_t uplane = (int64_t)NB * np;
     const int64_t first_i = c0 / pl.cpi, last_i = (c1 - 1) / pl.cpi;
     const int64_t nseg = last_i - first_i + 1;
-    constexpr int RMAX = 8 / QM;
+    constexpr int RMAX = k1_rmax(QM, (ST == GROM_F32X2) ? 2 : 1);
     constexpr int PLANES = (ST == GROM_F32X2) ? 2 : 1;
     const int t_off = (int)(ro * row_bytes + pos0 * 16);
     const int t_step = (int)(R * row_bytes);
     const int q_step = W * 16;
     const int plane_off = (int)(lp * 4);
     const bool full_pos = act && (pos0 + (QM - 1) * W < P);
+    // rows of a full chunk held by this thread (other chunks: the last of a test index)
+    int nrow_full = act ? ((int)pl.rpc - ro + R - 1) >> lgR : 0;
+    if (nrow_full > RMAX) nrow_full = RMAX;
+    if (nrow_full < 0) nrow_full = 0;
     const int64_t i_lo = (int64_t)g * n / G, i_hi = ((int64_t)g + 1) * n / G;  // owned test indices
     int s = 0;
     uint32_t ph = 0;
@@ -261,9 +265,12 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
           break;
         }
         const uint8_t* stg = stages + s * K1_STAGE_BYTES + t_off;
-        int nrow = act ? (rows - ro + R - 1) / R : 0;
-        if (nrow > RMAX) nrow = RMAX;
-        if (nrow < 0) nrow = 0;
+        int nrow = nrow_full;
+        if (rows != (int)pl.rpc) {
+          nrow = act ? (rows - ro + R - 1) >> lgR : 0;
+          if (nrow > RMAX) nrow = RMAX;
+          if (nrow < 0) nrow = 0;
+        }
         uint4 vec[RMAX][QM][PLANES];
         if (full_pos && nrow == RMAX) {
 #pragma unroll
@@ -289,6 +296,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
         if (lane == 0) ptx::mbar_arrive(&empty[s]);
         if (++s == K1_STAGES) { s = 0; ph ^= 1u; }
         const int jt = j0 + ro;
+        ds_renorm_all<ST>(acc);
 #pragma unroll
         for (int t = 0; t < RMAX; ++t) {
           if (t >= nrow) break;
@@ -320,10 +328,10 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
               const uint4 lv = vec[t][q][PLANES - 1];
 #pragma unroll
               for (int b = 0; b < NB; ++b) {
-                ds_fma(__uint_as_float(hv.x), __uint_as_float(lv.x), uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
-                ds_fma(__uint_as_float(hv.y), __uint_as_float(lv.y), uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
-                ds_fma(__uint_as_float(hv.z), __uint_as_float(lv.z), uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
-                ds_fma(__uint_as_float(hv.w), __uint_as_float(lv.w), uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
+                ds_mac(__uint_as_float(hv.x), __uint_as_float(lv.x), uh[b], ul[b], acc[q][0][b].S, acc[q][0][b].s);
+                ds_mac(__uint_as_float(hv.y), __uint_as_float(lv.y), uh[b], ul[b], acc[q][1][b].S, acc[q][1][b].s);
+                ds_mac(__uint_as_float(hv.z), __uint_as_float(lv.z), uh[b], ul[b], acc[q][2][b].S, acc[q][2][b].s);
+                ds_mac(__uint_as_float(hv.w), __uint_as_float(lv.w), uh[b], ul[b], acc[q][3][b].S, acc[q][3][b].s);
               }
             }
           } else if constexpr (ST == GROM_F32) {

@@ -43,6 +43,11 @@ static void check_k1(int sm) {
           CHECK(p.grid >= 1 && p.grid <= sm, "K1 grid %d", p.grid);
           CHECK(p.nb_max >= 1 && p.nb_max <= 8 && (p.nb_max & (p.nb_max - 1)) == 0, "K1 nb_max %d", p.nb_max);
           CHECK(p.rpc >= 1 && p.cpi * p.rpc >= p.m, "K1 rows per chunk n %ld", (long)n);
+          // every row of a chunk lands in some consumer thread's registers
+          const int planes = st == GROM_F32X2 ? 2 : 1;
+          CHECK(k1_rmax(p.qm, planes) >= 1 && (p.rpc + p.rpr - 1) / p.rpr <= k1_rmax(p.qm, planes),
+                "K1 rows per thread st %d packed %d n %ld", st, packed, (long)n);
+          CHECK(!packed || p.rpr == p.rg, "K1 packed row step n %ld", (long)n);
           CHECK(p.row_bytes <= K1_MAX_ROW_BYTES && p.row_bytes % 16 == 0, "K1 row bytes %ld", (long)p.row_bytes);
           CHECK((int64_t)p.grid * (p.maxseg - 1) * p.cpi >= p.T - p.grid * p.cpi, "K1 segments n %ld", (long)n);
         }

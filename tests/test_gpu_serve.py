@@ -1,5 +1,9 @@
-"""grom_serve on the GPU: continuous batching of mixed-model requests; each
-result equals the same request stepped alone, within the parity tolerance."""
+"""grom_serve on the GPU: continuous batching of mixed-model requests.  Each
+result is bitwise the same as the same request served alone by a server with
+the same pools (every quantum steps a pool as one batch of all its slots, so
+the kernels' plan and summation order do not depend on the other requests),
+and equals the request stepped on its own (batch 1, another kernel plan)
+within the parity tolerance."""
 import numpy as np
 import pytest
 
@@ -55,6 +59,15 @@ def test_mixed_requests_match_alone(models):
     assert out["stats"]["peak_active"] > 1
     names = ["full_bf16", "cp_f64", "full_f64", "packed_bf16"]
     tol = {"full_bf16": 1e-5, "cp_f64": 1e-11, "full_f64": 1e-12, "packed_bf16": 1e-5}
+    alone_srv = grom.Server(150 * 2 ** 30, quantum=8)
+    alone_ids = [alone_srv.add_rom(roms["full_bf16"], 12), alone_srv.add_rom(roms["cp_f64"], 20),
+                 alone_srv.add_rom(roms["full_f64"], 4), alone_srv.add_rom(roms["packed_bf16"], 12)]
+    for q in range(0, count, 3):
+        one = alone_srv.serve([alone_ids[which[q]]], [horizons[q]], [0.0], [u0s[q]], want_final=True)
+        assert one["status"][0] == 0
+        np.testing.assert_array_equal(one["final"][0], out["final"][q], err_msg="request %d (%s)" % (
+            q, names[which[q]]))
+    alone_srv.close()
     for q in range(0, count, 3):
         rom = roms[names[which[q]]]
         tr = grom.Trajectories(rom, u0s[q][None, :])
