@@ -668,6 +668,9 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
         return bail(cuda_fail(cudaGetLastError(), "grom_create: tensor-core factor copies"));
       r->k3t_scratch_bytes = k3t_scratch_need(n, r->rank, r->form, r->max_batch, r->sm_count);
       if ((st = dmalloc(&r->k3t_scratch, r->k3t_scratch_bytes, &r->total_bytes))) return bail(st);
+      // the projection tiles' arrival counters start at zero
+      if (cudaMemsetAsync(r->k3t_scratch, 0, k3t_counter_bytes(p0), r->stream) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "grom_create"));
     }
     // persistent stepper (its grid-barrier word starts at zero)
     const size_t kp = k3p_scratch_bytes(n, rp, r->storage, r->sm_count);
@@ -1083,9 +1086,21 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   StepArgs a = step_args(t, energy, invariant);
   const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch) && !use_k2p(r, t->batch);
   const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch) && !use_k3t(r, t->batch);
+  const bool fused_k3t = r->diagonal && use_k3t(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
-    if (fused_k3) {
+    if (fused_k3t) {
+      // the state prep once per call; later steps reuse the rows the step kernel writes
+      K3Args k = k3_args(r);
+      k.hist = t->hist;
+      k.taken = t->taken;
+      k.hist_stride = 6 * (int64_t)r->n;
+      k.active = t->active;
+      cudaEvent_t e0, e1;
+      if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
+      e = k3t_launch_step(k3t_plan_of(r, t->batch), &r->k3t_tmap_ft, &r->k3t_tmap_ae, k, t->batch, r->k3t_scratch,
+                          r->err, s == 0, a, s, e0, e1, strm);
+    } else if (fused_k3) {
       K3Args k = k3_args(r);
       k.hist = t->hist;
       k.taken = t->taken;

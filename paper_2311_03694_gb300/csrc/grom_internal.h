@@ -203,14 +203,27 @@ struct K3TPlan {
   int64_t n, np, r, rp;  // rank padded to 64
   int nseg, nz;          // projection segments (2 general, 3 skew), expansion blocks (1, 2)
   int64_t m1, k1, m2, k2;
-  int btile, ctiles;     // trajectories per column tile (<= 128), column tiles
+  int btile, ctiles;     // trajectories per column tile (<= 64 skew, <= 128 general), column tiles
   int64_t bp;
+  int jtiles;            // 128-wide rank tiles of the projection kernel
   int s1, s2;            // K splits of the two GEMMs
   int s1_max, s2_max;    // their largest admissible values
-  int stages, tmem_cols;
+  int stages_p, tmem_p;  // projection kernel: pipeline stages, tensor-memory columns
+  size_t smem_p;
+  int stages, tmem_cols; // expansion kernel
   size_t smem;
 };
 constexpr int K3T_MIN_BATCH = 16;
+constexpr int K3T_MAX_CTILES = 1024;  // column tiles (batch / btile) the counter region covers
+// The expansion's trajectory-major split partials, summed by the step kernel
+// (which also writes the next state's BF16 hi/lo rows for the projections).
+struct K3TStepFuse {
+  const float* d2;  // s2 x bp x n
+  int s2;
+  int64_t bp, np;
+  void* xh;         // bp x np BF16 (hi), then xl (lo)
+  void* xl;
+};
 // s1_force, s2_force in [1, s1_max] / [1, s2_max] replace the rule's splits.
 K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1_force = 0, int s2_force = 0);
 size_t k3t_scratch_bytes(const K3TPlan& p);
@@ -218,10 +231,18 @@ size_t k3t_scratch_need(int64_t n, int64_t r, int form, int max_batch, int sm_co
 size_t k3t_factor_bytes(int64_t n, int64_t r, int form);
 cudaError_t k3t_build_factors(const void* fa, const void* fb, const void* fc, int64_t n, int64_t rb, int64_t r,
                               int form, void* ft, void* ae, cudaStream_t s);
+size_t k3t_counter_bytes(const K3TPlan& p);
 bool k3t_make_tmaps(CUtensorMap* m_ft, CUtensorMap* m_ae, const void* ft, const void* ae, int64_t n, int64_t r,
                     int form);
 cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a, int batch,
                        void* scratch, int* err, cudaStream_t s);
+// One diagonal BDF step of the batch with the K3T evaluation: the state prep
+// (when `prep`; the step kernel keeps the BF16 state rows current after
+// that), the projection and expansion kernels (between ev0 and ev1 when
+// set), then the step kernel summing the expansion's splits.
+cudaError_t k3t_launch_step(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a,
+                            int batch, void* scratch, int* err, bool prep, const StepArgs& st, int step_index,
+                            cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s);
 // Persistent cooperative CPD-ROM stepper for a few trajectories.
 size_t k3p_scratch_bytes(int64_t n, int64_t rp, int storage, int sm_count);
 int k3p_max_batch(int storage);
@@ -288,6 +309,10 @@ inline int step_pk_blocks(int64_t n) { return (int)((n + 31) / 32); }
 // kernel (the advection term is written to the history ring first).
 cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
                                 int nbk, cudaStream_t s);
+// The same step for the whole batch with n^l summed from K3T's expansion
+// partials (written to the history ring) and the new state also written as
+// BF16 hi/lo rows for the next projections.
+cudaError_t step_diag_mc_k3t_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s);
 cudaError_t step_diag_packed_launch(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a, int b0,
                                     int nb, int nbk, cudaStream_t s);
 // Persistent skew-packed stepper (k1p_persist.cuh): nsteps diagonal steps of

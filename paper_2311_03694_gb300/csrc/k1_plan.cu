@@ -82,7 +82,6 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed, int64_t m) {
     rpr = P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
   }
   const int64_t rmax = k1_rmax(p.qm, storage == GROM_F32X2 ? 2 : 1);  // rows a consumer thread holds per chunk
-  p.rpr = rpr;
   p.rpc = K1_STAGE_BYTES / p.row_bytes;
   if (p.rpc > rmax * rpr) p.rpc = rmax * rpr;
   if (p.rpc < 1) p.rpc = 1;
@@ -103,6 +102,12 @@ K1Plan k1_plan(int64_t n, int storage, int sm_count, int packed, int64_t m) {
   p.smem = (size_t)(K1_SMEM_BASE + nb * per_traj);
   p.lw = p.maxseg - 1 + p.lp;
   return p;
+}
+
+int64_t k1_row_step(const K1Plan& p, int storage) {
+  if (p.packed) return p.rg;
+  const int64_t P = p.lp / epv(storage);
+  return P >= K1_CONSUMERS ? 1 : K1_CONSUMERS / P;
 }
 
 size_t k1p_dg_bytes(const K1Plan& p, int storage) {

@@ -316,8 +316,16 @@ __global__ void __launch_bounds__(K1_THREADS, 1) k1_stream_kernel(const K1Plan p
       }
       const uint8_t* st = stages + s * K1_STAGE_BYTES + t_off;
       // rows of this chunk held by this thread
-      int nrow = nrow_full;
-      if (rows != (int)pl.rpc) {
+      int nrow;
+      if constexpr (ST == GROM_F32X2) {
+        // full chunks: the precomputed count
+        nrow = nrow_full;
+        if (rows != (int)pl.rpc) {
+          nrow = act ? (rows - (int)ro + (int)rpr - 1) / (int)rpr : 0;
+          if (nrow > RMAX) nrow = RMAX;
+          if (nrow < 0) nrow = 0;
+        }
+      } else {
         nrow = act ? (rows - (int)ro + (int)rpr - 1) / (int)rpr : 0;
         if (nrow > RMAX) nrow = RMAX;
         if (nrow < 0) nrow = 0;

@@ -27,7 +27,6 @@ struct K1Plan {
   int has_mid;         // 1: the middle weights come from K1Args::mid
   int64_t row_bytes;   // stored elements per row (np, or lp when packed) * element bytes
   int64_t rpc;         // rows per chunk (all in one test index i)
-  int64_t rpr;         // rows between a consumer thread's consecutive rows of a chunk
   int64_t cpi;         // chunks per test index
   int64_t T;           // total chunks = n * cpi
   int grid;            // persistent CTAs
@@ -42,6 +41,11 @@ struct K1Plan {
   int64_t lp;          // stored elements per row: round_up(max(h, 1), 64)
   int64_t lw;          // transposed-term window per CTA: maxseg - 1 + lp
 };
+// Rows between a consumer thread's consecutive rows of a chunk: the row
+// groups of the packed layout, else the rows that share the consumer threads
+// (the kernels derive the same value; kept out of K1Plan, whose size is part
+// of every streaming kernel's parameters).
+int64_t k1_row_step(const K1Plan& p, int storage);
 // Scratch of the packed kernel: D u_i per (CTA, test-index segment, trajectory,
 // position) and the per-CTA transposed-term windows.
 size_t k1p_dg_bytes(const K1Plan& p, int storage);

@@ -355,10 +355,15 @@ __global__ void __launch_bounds__(256) k3d_expand(const DDims d, const K3Args a,
 }
 
 // K splits so that the grid covers about two waves of the GPU; each split
-// keeps at least 128 elements of the K range.
+// keeps at least 128 elements of the K range, or for short ranges one K
+// tile (up to 8 splits), so that small problems (a serving pool of a small
+// ROM: one output tile) still spread over several SMs.  (A 64-element floor
+// measured slower at N = 1024 with 16-64 trajectories: the last CTA's sum of
+// 16 splits costs more than the extra parallelism gains.)
 static int d_splits(int64_t tiles, int64_t K, int sm_count) {
   int64_t ks = (2 * sm_count + tiles - 1) / tiles;
-  const int64_t kmax = K / 128;
+  const int64_t kshort = K / D_BK < 8 ? K / D_BK : 8;
+  const int64_t kmax = K / 128 > kshort ? K / 128 : kshort;
   if (ks > kmax) ks = kmax;
   if (ks < 1) ks = 1;
   return (int)ks;

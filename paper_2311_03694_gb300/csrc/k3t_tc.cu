@@ -17,14 +17,23 @@
 //   * FP32 accumulation in tensor memory; the epilogue adds the hi and lo
 //     halves and stores FP32 rows (split-K partials when the output tiles
 //     alone cannot fill the GPU).
-// A Hadamard kernel sums the projection splits, forms Z and transposes it
-// into hi/lo rows; a finish kernel sums the expansion splits in a fixed
-// order in FP64 into the output or the advection slot of the history ring.
+// The projections run as one fused kernel (k3t_proj): a CTA owns 128 rank
+// indices j and one column tile of trajectories and issues the P, Q (and S)
+// MMAs of those j into separate tensor-memory accumulators that share the
+// state tile, so its epilogue forms Z = P o Q (and P o S) itself and writes
+// the hi/lo rows of the expansion's B operand (with split K, the last CTA of
+// a tile to arrive sums the splits' partials in split order).  The expansion
+// (k3t_gemm) writes its partials trajectory-major, and the step kernel sums
+// them in FP64 in split order while it steps (k_step_diag_mc, K3T mode),
+// writing the next state's BF16 hi/lo rows as it goes; a finish kernel does
+// the same sum for the plain evaluation (grom_nonlinear).  Per step: the
+// projection kernel, the expansion and the step; the state prep runs once
+// per call.
 //
-// CTA (6 warps): warp 0 issues the TMA loads (a 128 x 64 A box, two btile x
+// CTA (6 warps): warp 0 issues the TMA loads (128 x 64 A boxes, two btile x
 // 64 B boxes per K step), warp 1 owns the tensor memory and issues
-// tcgen05.mma (M = 128, N = 2 btile, K = 16), warps 2-5 read the accumulator
-// back.
+// tcgen05.mma (M = 128, N = 2 btile, K = 16), warps 2-5 read the
+// accumulators back.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -35,13 +44,24 @@
 namespace grom {
 
 constexpr int K3T_THREADS = 192;
+constexpr int K3T_PROJ_MAX_SPLITS = 8;  // K splits of the projection kernel (its last-CTA reduction holds them all)
 constexpr int K3T_A_BYTES = 128 * 64 * 2;  // 128 rows x 64 K
 constexpr int K3T_SMEM_MAX = 232448;
 
 struct K3TGemm {
   int64_t M, K, bp;  // A rows, contraction length (multiple of 64), padded batch
   int btile, mtiles, ctiles, splits, stages, tmem_cols;
-  float* out;        // splits x M x bp
+  float* out;        // splits x bp x M (trajectory-major)
+  int* err;
+};
+
+struct K3TProj {
+  int64_t rp, bp, kz, K;  // padded rank, padded batch, Z row length (nz rp), K = np
+  int nseg, btile, jtiles, ctiles, splits, stages, tmem_cols;
+  float* part;            // splits > 1: one block per (split, rank tile, column tile) of btile x 3 x 128 floats
+  unsigned int* cnt;      // jtiles x ctiles arrival counters, zero between launches
+  __nv_bfloat16* zh;      // bp x kz hi rows of Z
+  __nv_bfloat16* zl;      // lo rows
   int* err;
 };
 
@@ -143,34 +163,237 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
     tc::fence_after_sync();
     const int q = warp & 3;
     if (ok && T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0)) {
+      // lane = output row m, column = trajectory: for each column the 32
+      // lanes store 32 consecutive m of that trajectory's row
       const int64_t m = (int64_t)mt * 128 + 32 * q + lane;
       const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
-      float* dst = g.out + ((int64_t)split * g.M + m) * g.bp + (int64_t)ct * g.btile;
-      for (int c0 = 0; c0 < g.btile; c0 += 32) {
-        uint32_t v[32], w[32];
-        if (g.btile == 16) {
-          tc::tmem_ld_32x32b_x32(acc, v);  // hi 0..15 | lo 16..31
-#pragma unroll
-          for (int c = 0; c < 32; ++c) w[c] = v[(c + 16) & 31];
-        } else {
-          tc::tmem_ld_32x32b_x32(acc + (uint32_t)c0, v);
-          tc::tmem_ld_32x32b_x32(acc + (uint32_t)(g.btile + c0), w);
-        }
+      float* dst = g.out + ((int64_t)split * g.bp + (int64_t)ct * g.btile) * g.M + m;
+      for (int c0 = 0; c0 < g.btile; c0 += 16) {
+        uint32_t v[16], w[16];
+        tc::tmem_ld_32x32b_x16(acc + (uint32_t)c0, v);
+        tc::tmem_ld_32x32b_x16(acc + (uint32_t)(g.btile + c0), w);
         tc::tmem_ld_wait();
         if (m < g.M) {
-          const int nb = g.btile - c0 < 32 ? g.btile - c0 : 32;
-          if (nb == 32) {
 #pragma unroll
-            for (int c = 0; c < 32; c += 4)
-              *reinterpret_cast<float4*>(dst + c0 + c) = make_float4(
-                  __uint_as_float(v[c]) + __uint_as_float(w[c]), __uint_as_float(v[c + 1]) + __uint_as_float(w[c + 1]),
-                  __uint_as_float(v[c + 2]) + __uint_as_float(w[c + 2]),
-                  __uint_as_float(v[c + 3]) + __uint_as_float(w[c + 3]));
+          for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * g.M] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, (uint32_t)g.tmem_cols);
+  }
+}
+
+// Z[b][j] = P_j Q_j (and Z[b][rp + j] = P_j S_j) into BF16 hi/lo rows.
+__device__ __forceinline__ void k3t_store_z(const K3TProj& g, int64_t b, int64_t j, float p, float q, float s) {
+  const float z1 = p * q;
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(z1);
+  g.zh[b * g.kz + j] = h1;
+  g.zl[b * g.kz + j] = __float2bfloat16_rn(z1 - __bfloat162float(h1));
+  if (g.nseg == 3) {
+    const float z2 = p * s;
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(z2);
+    g.zh[b * g.kz + g.rp + j] = h2;
+    g.zl[b * g.kz + g.rp + j] = __float2bfloat16_rn(z2 - __bfloat162float(h2));
+  }
+}
+
+// The FP32 partial block of split z of tile (jt, ct): btile columns x 3
+// segments x 128 rank rows, so that inside a block every offset of a
+// column group is a constant.
+__device__ __forceinline__ float* k3t_part_block(const K3TProj& g, int z, int jt, int ct) {
+  return g.part + (((int64_t)z * g.jtiles + jt) * g.ctiles + ct) * ((int64_t)g.btile * 384);
+}
+
+// The last split CTA of a tile: Z of rank row jl (index j) for the tile's
+// columns from the splits' partials, summed in split order.  Four columns
+// at a time, every split's partials are loaded before they are summed, so
+// the L2 reads are in flight together.
+__device__ __forceinline__ void k3t_reduce_splits(const K3TProj& g, int jt, int ct, int jl, int64_t j) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < g.btile; c0 += 4) {
+    float w[K3T_PROJ_MAX_SPLITS][3][4];
+#pragma unroll
+    for (int z = 0; z < K3T_PROJ_MAX_SPLITS; ++z)
+      if (z < g.splits) {
+        const float* blk = k3t_part_block(g, z, jt, ct) + c0 * 384 + jl;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int seg = 0; seg < 3; ++seg) w[z][seg][c] = __ldcg(blk + (c * 3 + seg) * 128);
+      }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int z = 0; z < K3T_PROJ_MAX_SPLITS; ++z)
+        if (z < g.splits)
+#pragma unroll
+          for (int seg = 0; seg < 3; ++seg) v[seg] += w[z][seg][c];
+      k3t_store_z(g, (int64_t)ct * g.btile + c0 + c, j, v[0], v[1], v[2]);
+    }
+  }
+}
+
+// The projections and the Hadamard products of one tile: rank indices
+// j0 = 128 jt .. j0 + 127 and trajectories of column tile ct.  Per K step the
+// producer loads the nseg A boxes (rows seg rp + j0 of FT: V^T, W^T, U^T for
+// the skew form, B^T, C^T for the general one) and the hi/lo state boxes; the
+// MMA warp multiplies each A box with the shared state tile into its own
+// accumulator (tensor-memory columns seg 2 btile .. +2 btile: hi | lo).  Rows
+// of an A box past rp belong to the next segment or lie past the tensor
+// (zero-filled); their outputs are not stored.
+__global__ void __launch_bounds__(K3T_THREADS, 1)
+    k3t_proj(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_bh,
+             const __grid_constant__ CUtensorMap tmap_bl, const K3TProj g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int S = g.stages;
+  const int b_half = g.btile * 128;
+  const int stage_a = g.nseg * K3T_A_BYTES;
+  const int stage_b = 2 * b_half;
+  uint8_t* sa = smem;
+  uint8_t* sb = sa + (size_t)S * stage_a;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sb + (size_t)S * stage_b);
+  uint64_t* empty = full + S;
+  uint64_t* accum = empty + S;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* last_flag = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int split = blockIdx.x % g.splits;
+  const int rest = blockIdx.x / g.splits;
+  const int ct = rest % g.ctiles, jt = rest / g.ctiles;
+  const int64_t kblocks = g.K / 64;
+  const int64_t kb0 = (int64_t)split * kblocks / g.splits, kb1 = ((int64_t)split + 1) * kblocks / g.splits;
+  const int64_t T = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(accum, 1);
+    *abort_flag = 0;
+    *last_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_bh);
+    tc::prefetch_tmap(&tmap_bl);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, (uint32_t)g.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int64_t t = 0;
+      for (; t < T; ++t) {
+        const int s = (int)(t % S);
+        if (t >= S && !ptx::mbar_wait(&empty[s], (uint32_t)(((t / S) & 1) ^ 1), abort_flag)) {
+          k3t_abort(abort_flag, g.err);
+          break;
+        }
+        const int32_t x = (int32_t)((kb0 + t) * 64);
+        ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_a + stage_b));
+        for (int seg = 0; seg < g.nseg; ++seg)
+          tc::tma_load_2d(sa + (size_t)s * stage_a + seg * K3T_A_BYTES, &tmap_a, x,
+                          (int32_t)(seg * g.rp + (int64_t)jt * 128), &full[s]);
+        uint8_t* b = sb + (size_t)s * stage_b;
+        tc::tma_load_2d(b, &tmap_bh, x, ct * g.btile, &full[s]);
+        tc::tma_load_2d(b + b_half, &tmap_bl, x, ct * g.btile, &full[s]);
+      }
+      for (int64_t q = t > S ? t - S : 0; q < t; ++q)
+        if (!ptx::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), nullptr)) atomicOr(g.err, DEV_ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(128, 2 * g.btile);  // hi | lo
+      for (int64_t t = 0; t < T; ++t) {
+        const int s = (int)(t % S);
+        if (!ptx::mbar_wait(&full[s], (uint32_t)((t / S) & 1), abort_flag)) {
+          k3t_abort(abort_flag, g.err);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint64_t bd = tc::sw128_kmajor_desc(sb + (size_t)s * stage_b);  // 2 btile rows
+        for (int seg = 0; seg < g.nseg; ++seg) {
+          const uint64_t ad = tc::sw128_kmajor_desc(sa + (size_t)s * stage_a + seg * K3T_A_BYTES);
+          const uint32_t d = tmem + (uint32_t)(seg * 2 * g.btile);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tc::mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
+        }
+        tc::commit(&empty[s]);
+      }
+      tc::commit(accum);  // arrives once every issued MMA has completed
+    }
+  } else {
+    // ----------------------------------------------------- epilogue (warps 2-5)
+    const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(accum, 0, nullptr));
+    if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
+    tc::fence_after_sync();
+    const int q = warp & 3;
+    const bool run = ok && T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0);
+    const int64_t j = (int64_t)jt * 128 + 32 * q + lane;
+    const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
+    if (run) {
+      for (int c0 = 0; c0 < g.btile; c0 += 16) {
+        float pv[3][16];
+#pragma unroll
+        for (int seg = 0; seg < 3; ++seg) {
+          if (seg < g.nseg) {
+            uint32_t v[16], w[16];
+            tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + c0), v);
+            tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + g.btile + c0), w);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) pv[seg][c] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
           } else {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) dst[c0 + c] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
+            for (int c = 0; c < 16; ++c) pv[seg][c] = 0.f;
           }
         }
+        if (j < g.rp) {
+          const int64_t b0 = (int64_t)ct * g.btile + c0;
+          if (g.splits == 1) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) k3t_store_z(g, b0 + c, j, 0.f + pv[0][c], 0.f + pv[1][c], 0.f + pv[2][c]);
+          } else {
+            // this split's partials (all three segments; zero where the form has two)
+            float* blk = k3t_part_block(g, split, jt, ct) + c0 * 384 + 32 * q + lane;
+#pragma unroll
+            for (int seg = 0; seg < 3; ++seg)
+#pragma unroll
+              for (int c = 0; c < 16; ++c) blk[(c * 3 + seg) * 128] = pv[seg][c];
+          }
+        }
+      }
+    }
+    if (g.splits > 1) {
+      // the last split of the tile to arrive sums the partials in split order
+      const int tile = jt * g.ctiles + ct;
+      __threadfence();
+      ptx::named_sync(1, 128);
+      if (warp == 2 && lane == 0) *last_flag = atomicAdd(&g.cnt[tile], 1u) == (unsigned)(g.splits - 1);
+      ptx::named_sync(1, 128);
+      if (*last_flag) {
+        __threadfence();
+        if (j < g.rp && !*abort_flag) k3t_reduce_splits(g, jt, ct, 32 * q + lane, j);
+        if (warp == 2 && lane == 0) g.cnt[tile] = 0u;
       }
     }
   }
@@ -199,54 +422,16 @@ __global__ void k3t_prep(const K3Args a, int64_t n, int64_t np, int64_t bp, int 
   xl[t] = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// Z[b][j] (BF16 hi/lo, bp x kz) from the projection partials d1 (s1 x m1 x
-// bp, rows P | Q | S of rp each): Z[b][j] = P_j Q_j for j < rp and, in the
-// skew form (kz = 2 rp), Z[b][rp + j] = P_j S_j; 32 x 32 tiles through shared
-// memory (coalesced reads along b, writes along j).
-__global__ void k3t_hadamard(const float* __restrict__ d1, int s1, int64_t m1, int64_t rp, int64_t bp, int64_t kz,
-                             __nv_bfloat16* zh, __nv_bfloat16* zl) {
-  __shared__ float tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const int64_t j0 = (int64_t)blockIdx.y * 32, b0 = (int64_t)blockIdx.x * 32;
-  for (int jj = ty; jj < 32; jj += 8) {
-    const int64_t j = j0 + jj, b = b0 + tx;
-    float z = 0.f;
-    if (j < kz && b < bp) {
-      const int64_t jp = j < rp ? j : j - rp;            // column of P
-      const int64_t jo = j < rp ? rp + j : 2 * rp + jp;   // row of Q, or of S (skew, second half)
-      float p = 0.f, o = 0.f;
-      for (int s = 0; s < s1; ++s) {
-        p += d1[((int64_t)s * m1 + jp) * bp + b];
-        o += d1[((int64_t)s * m1 + jo) * bp + b];
-      }
-      z = p * o;
-    }
-    tile[jj][tx] = z;
-  }
-  __syncthreads();
-  for (int bb = ty; bb < 32; bb += 8) {
-    const int64_t b = b0 + bb, j = j0 + tx;
-    if (b < bp && j < kz) {
-      const float z = tile[tx][bb];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(z);
-      zh[b * kz + j] = hi;
-      zl[b * kz + j] = __float2bfloat16_rn(z - __bfloat162float(hi));
-    }
-  }
-}
-
-// c[b][i] = sum over splits of d2[split][i][b], in split order, in FP64.
-// Consecutive threads take consecutive b: the reads are coalesced, the
-// writes land 6 n doubles apart (a 32 x 32 shared-memory transpose for
-// coalesced writes was measured slower: a quarter of the threads).
-__global__ void k3t_finish(const float* __restrict__ d2, int s2, int64_t n, int64_t m2, int64_t bp, const K3Args a,
-                           int batch) {
+// c[b][i] = sum over splits of d2[split][b][i], in split order, in FP64
+// (the plain evaluation; stepping does this sum inside the step kernel).
+// Consecutive threads take consecutive i: reads and writes are coalesced.
+__global__ void k3t_finish(const float* __restrict__ d2, int s2, int64_t n, int64_t bp, const K3Args a, int batch) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)batch * n) return;
-  const int64_t i = t / batch, b = t - i * batch;
+  const int64_t b = t / n, i = t - b * n;
   if (a.active && !a.active[b]) return;
   double s = 0.0;
-  for (int q = 0; q < s2; ++q) s += (double)d2[((int64_t)q * m2 + i) * bp + b];
+  for (int q = 0; q < s2; ++q) s += (double)d2[((int64_t)q * bp + b) * n + i];
   double* dst = a.taken ? a.hist + b * a.hist_stride + (3 + a.taken[b] % 3) * n : a.c + b * a.c_stride;
   dst[i] = s;
 }
@@ -318,16 +503,30 @@ K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1
   p.k1 = p.np;
   p.m2 = n;
   p.k2 = p.nz * p.rp;
+  // the projection kernel keeps nseg accumulators of 2 btile columns (hi |
+  // lo) in tensor memory: 3 x 128 (skew) or 2 x 256 columns at most
+  const int bmax = skew ? 64 : 128;
   int btile = (batch + 15) / 16 * 16;
-  if (btile > 128) btile = 128;
+  if (btile > bmax) btile = bmax;
   p.btile = btile;
   p.ctiles = (batch + btile - 1) / btile;
   p.bp = (int64_t)p.ctiles * btile;
-  const int64_t mt1 = (p.m1 + 127) / 128, mt2 = (p.m2 + 127) / 128;
-  p.s1 = k3t_splits(mt1 * p.ctiles, p.k1 / 64, sm_count, s1_force);
+  p.jtiles = (int)((p.rp + 127) / 128);
+  const int64_t mt2 = (p.m2 + 127) / 128;
+  p.s1_max = std::min(k3t_split_max(p.k1 / 64), K3T_PROJ_MAX_SPLITS);
+  p.s1 = std::min(k3t_splits((int64_t)p.jtiles * p.ctiles, p.k1 / 64, sm_count, s1_force), p.s1_max);
   p.s2 = k3t_splits(mt2 * p.ctiles, p.k2 / 64, sm_count, s2_force);
-  p.s1_max = k3t_split_max(p.k1 / 64);
   p.s2_max = k3t_split_max(p.k2 / 64);
+  // projections: nseg A boxes and the hi/lo state boxes per stage
+  const int stage_p = p.nseg * K3T_A_BYTES + 2 * btile * 128;
+  int stp = (int)((K3T_SMEM_MAX - 1024 - 256) / stage_p);
+  if (stp > 6) stp = 6;
+  p.stages_p = stp;
+  p.smem_p = 1024 + (size_t)stp * stage_p + (size_t)(2 * stp + 1) * 8 + 16;
+  int cols_p = 32;
+  while (cols_p < p.nseg * 2 * btile) cols_p <<= 1;
+  p.tmem_p = cols_p;
+  // expansion: one A box and the hi/lo Z boxes per stage
   const int stage = K3T_A_BYTES + 2 * btile * 128;
   int st = (int)((K3T_SMEM_MAX - 1024 - 256) / stage);
   if (st > 6) st = 6;
@@ -339,9 +538,17 @@ K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1
   return p;
 }
 
-// xh | xl | d1 partials | zh | zl | d2 partials
+// Scratch: [arrival counters of the projection tiles, a fixed region per
+// (n, r) so that no batch size moves them] xh | xl | projection partials |
+// zh | zl | expansion partials.  The counters are zeroed at create and reset
+// by the last CTA of each tile.
+size_t k3t_counter_bytes(const K3TPlan& p) {
+  return ((size_t)p.jtiles * K3T_MAX_CTILES * sizeof(unsigned int) + 255) / 256 * 256;
+}
+
 size_t k3t_scratch_bytes(const K3TPlan& p) {
-  return 2 * (size_t)p.bp * p.np * 2 + 4 * (size_t)p.s1 * p.m1 * p.bp + 2 * (size_t)p.bp * p.k2 * 2 +
+  const size_t part = p.s1 > 1 ? 4 * (size_t)p.s1 * p.jtiles * p.bp * 384 : 0;
+  return k3t_counter_bytes(p) + 2 * (size_t)p.bp * p.np * 2 + part + 2 * (size_t)p.bp * p.k2 * 2 +
          4 * (size_t)p.s2 * p.m2 * p.bp;
 }
 
@@ -398,25 +605,92 @@ static cudaError_t k3t_gemm_launch(const K3TPlan& p, const CUtensorMap* ma, cons
   return cudaGetLastError();
 }
 
+// The pieces of the scratch for plan p.
+struct K3TBufs {
+  unsigned int* cnt;
+  __nv_bfloat16 *xh, *xl, *zh, *zl;
+  float *d1, *d2;
+};
+
+static K3TBufs k3t_bufs(const K3TPlan& p, void* scratch) {
+  K3TBufs q{};
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  q.cnt = reinterpret_cast<unsigned int*>(base);
+  q.xh = reinterpret_cast<__nv_bfloat16*>(base + k3t_counter_bytes(p));
+  q.xl = q.xh + p.bp * p.np;
+  q.d1 = reinterpret_cast<float*>(q.xl + p.bp * p.np);
+  q.zh = reinterpret_cast<__nv_bfloat16*>(q.d1 + (p.s1 > 1 ? (size_t)p.s1 * p.jtiles * p.bp * 384 : 0));
+  q.zl = q.zh + p.bp * p.k2;
+  q.d2 = reinterpret_cast<float*>(q.zl + p.bp * p.k2);
+  return q;
+}
+
+// States into the BF16 hi/lo rows of the projections' B operand.
+static cudaError_t k3t_prep_launch(const K3TPlan& p, const K3Args& a, int batch, const K3TBufs& q, cudaStream_t s) {
+  k3t_prep<<<dim3((unsigned)((p.np + 255) / 256), (unsigned)p.bp), 256, 0, s>>>(a, p.n, p.np, p.bp, batch, q.xh, q.xl);
+  return cudaGetLastError();
+}
+
+// Projections with the Hadamard products, then the expansion into the
+// trajectory-major partials d2.
+static cudaError_t k3t_gemms(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3TBufs& q,
+                             int* err, cudaStream_t s) {
+  if (p.ctiles > K3T_MAX_CTILES) return cudaErrorInvalidValue;
+  CUtensorMap mh, ml;
+  if (!k3t_tmap(&mh, q.xh, p.k1, p.bp, p.btile) || !k3t_tmap(&ml, q.xl, p.k1, p.bp, p.btile))
+    return cudaErrorInvalidValue;
+  K3TProj g{};
+  g.rp = p.rp;
+  g.bp = p.bp;
+  g.kz = p.k2;
+  g.K = p.k1;
+  g.nseg = p.nseg;
+  g.btile = p.btile;
+  g.jtiles = p.jtiles;
+  g.ctiles = p.ctiles;
+  g.splits = p.s1;
+  g.stages = p.stages_p;
+  g.tmem_cols = p.tmem_p;
+  g.part = q.d1;
+  g.cnt = q.cnt;
+  g.zh = q.zh;
+  g.zl = q.zl;
+  g.err = err;
+  cudaError_t e = cudaFuncSetAttribute(k3t_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem_p);
+  if (e != cudaSuccess) return e;
+  k3t_proj<<<(unsigned)(p.jtiles * p.ctiles * p.s1), K3T_THREADS, p.smem_p, s>>>(*m_ft, mh, ml, g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return k3t_gemm_launch(p, m_ae, q.zh, q.zl, p.m2, p.k2, p.s2, q.d2, err, s);
+}
+
 cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a, int batch,
                        void* scratch, int* err, cudaStream_t s) {
-  __nv_bfloat16* xh = reinterpret_cast<__nv_bfloat16*>(scratch);
-  __nv_bfloat16* xl = xh + p.bp * p.np;
-  float* d1 = reinterpret_cast<float*>(xl + p.bp * p.np);
-  __nv_bfloat16* zh = reinterpret_cast<__nv_bfloat16*>(d1 + (size_t)p.s1 * p.m1 * p.bp);
-  __nv_bfloat16* zl = zh + p.bp * p.k2;
-  float* d2 = reinterpret_cast<float*>(zl + p.bp * p.k2);
-  k3t_prep<<<dim3((unsigned)((p.np + 255) / 256), (unsigned)p.bp), 256, 0, s>>>(a, p.n, p.np, p.bp, batch, xh, xl);
-  cudaError_t e = cudaGetLastError();
+  const K3TBufs q = k3t_bufs(p, scratch);
+  cudaError_t e = k3t_prep_launch(p, a, batch, q, s);
+  if (e == cudaSuccess) e = k3t_gemms(p, m_ft, m_ae, q, err, s);
   if (e != cudaSuccess) return e;
-  if ((e = k3t_gemm_launch(p, m_ft, xh, xl, p.m1, p.k1, p.s1, d1, err, s)) != cudaSuccess) return e;
-  dim3 hg((unsigned)((p.bp + 31) / 32), (unsigned)((p.k2 + 31) / 32));
-  k3t_hadamard<<<hg, 256, 0, s>>>(d1, p.s1, p.m1, p.rp, p.bp, p.k2, zh, zl);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = k3t_gemm_launch(p, m_ae, zh, zl, p.m2, p.k2, p.s2, d2, err, s)) != cudaSuccess) return e;
   const int64_t fin = (int64_t)batch * p.n;
-  k3t_finish<<<(unsigned)((fin + 255) / 256), 256, 0, s>>>(d2, p.s2, p.n, p.m2, p.bp, a, batch);
+  k3t_finish<<<(unsigned)((fin + 255) / 256), 256, 0, s>>>(q.d2, p.s2, p.n, p.bp, a, batch);
   return cudaGetLastError();
+}
+
+cudaError_t k3t_launch_step(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a,
+                            int batch, void* scratch, int* err, bool prep, const StepArgs& st, int step_index,
+                            cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+  const K3TBufs q = k3t_bufs(p, scratch);
+  cudaError_t e = prep ? k3t_prep_launch(p, a, batch, q, s) : cudaSuccess;
+  if (e == cudaSuccess && ev0) e = prof_record(ev0, s);
+  if (e == cudaSuccess) e = k3t_gemms(p, m_ft, m_ae, q, err, s);
+  if (e == cudaSuccess && ev1) e = prof_record(ev1, s);
+  if (e != cudaSuccess) return e;
+  K3TStepFuse f{};
+  f.d2 = q.d2;
+  f.s2 = p.s2;
+  f.bp = p.bp;
+  f.np = p.np;
+  f.xh = q.xh;
+  f.xl = q.xl;
+  return step_diag_mc_k3t_launch(st, step_index, f, s);
 }
 
 }  // namespace grom

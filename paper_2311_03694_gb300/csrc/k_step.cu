@@ -8,6 +8,8 @@
 // and writes u^{l+1} over u^{l-2} (slot (l+1) mod 3).  It also returns the
 // energy 1/2 u^T B u of the new state, the invariant u^T n of the old state
 // and flags non-finite states.
+#include <cuda_bf16.h>
+
 #include "grom_internal.h"
 #include "ptx.cuh"
 #include "step_elem.cuh"
@@ -52,9 +54,14 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
 // of the trajectory to arrive (arrival counter, no waiting), which also
 // advances the step count.  With k1 set, the K1 partials of the element are
 // summed first (the streaming kernel's finalize, fused).
+// fuse: 0 n^l from the history ring; 1 the K1 partials (finalize fused);
+// 2 the K3T expansion partials, with the new state's BF16 hi/lo rows written
+// for the next projections (the values the state prep would write).
+// PLAIN: identity mass, no linear or forcing term, no energy or invariant.
+template <bool PLAIN>
 __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs a, const int step_index,
                                                                   const K1Plan pl, const K1Args k1a, const int fuse,
-                                                                  const int b0, const int nbk) {
+                                                                  const int b0, const int nbk, const K3TStepFuse kf) {
   __shared__ double sh[64];
   __shared__ int bad;
   __shared__ int last;
@@ -67,14 +74,20 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
   double* h = a.hist + b * a.hist_stride;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  const bool sums = a.energy || a.invariant;  // energy and invariant asked for
+  const bool sums = !PLAIN && (a.energy || a.invariant);  // energy and invariant asked for
   double e_part = 0.0, i_part = 0.0;
   int my_bad = 0;
   for (int e = 0; e < a.ept; ++e) {
     const int64_t i = ((int64_t)blockIdx.x * a.ept + e) * STEP_MC_THREADS + threadIdx.x;
     if (i >= n) break;
     double nl;
-    if (fuse) {
+    if (fuse == 2) {
+      // expansion splits in split order, FP64
+      double sum = 0.0;
+      for (int q = 0; q < kf.s2; ++q) sum += (double)kf.d2[((int64_t)q * kf.bp + b) * n + i];
+      h[(3 + l % 3) * n + i] = sum;
+      nl = sum;
+    } else if (fuse) {
       // K1 finalize: partials of every CTA whose chunk range covers test index i, in CTA order
       const int64_t G = pl.grid, T = pl.T;
       const int64_t g_lo = ((i * pl.cpi + 1) * G - 1) / T, g_hi = (((i + 1) * pl.cpi) * G - 1) / T;
@@ -92,7 +105,13 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
     }
     double ep, ip;
     int eb;
-    step_elem(a, h, n, l, k, i, nl, ep, ip, eb, sums);
+    const double un = step_elem<PLAIN>(a, h, n, l, k, i, nl, ep, ip, eb, sums);
+    if (fuse == 2) {
+      const float v = __double2float_rn(un);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      static_cast<__nv_bfloat16*>(kf.xh)[(int64_t)b * kf.np + i] = hi;
+      static_cast<__nv_bfloat16*>(kf.xl)[(int64_t)b * kf.np + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
     if (sums) {
       e_part += ep;
       i_part += ip;
@@ -118,6 +137,12 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
   if (last && threadIdx.x < 32) step_finish_last(a, b, l, step_index);
 }
 
+// The common case of the diagonal step: identity mass, no linear or forcing
+// term and no energy or invariant asked for.
+static bool step_plain(const StepArgs& a) {
+  return !a.mass_diag && !a.lin_diag && !a.forcing && !a.energy && !a.invariant;
+}
+
 cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
                                 int nbk, cudaStream_t s) {
   dim3 grid((unsigned)a.nblk, (unsigned)nb);
@@ -125,7 +150,19 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
   K1Args ka{};
   if (k1) pl = *k1;
   if (k1a) ka = *k1a;
-  k_step_diag_mc<<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, pl, ka, k1 ? 1 : 0, b0, nbk);
+  if (step_plain(a))
+    k_step_diag_mc<true><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, pl, ka, k1 ? 1 : 0, b0, nbk, K3TStepFuse{});
+  else
+    k_step_diag_mc<false><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, pl, ka, k1 ? 1 : 0, b0, nbk, K3TStepFuse{});
+  return cudaGetLastError();
+}
+
+cudaError_t step_diag_mc_k3t_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s) {
+  dim3 grid((unsigned)a.nblk, (unsigned)a.batch);
+  if (step_plain(a))
+    k_step_diag_mc<true><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, 2, 0, 1, f);
+  else
+    k_step_diag_mc<false><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, 2, 0, 1, f);
   return cudaGetLastError();
 }
 

@@ -45,9 +45,9 @@ static void check_k1(int sm) {
           CHECK(p.rpc >= 1 && p.cpi * p.rpc >= p.m, "K1 rows per chunk n %ld", (long)n);
           // every row of a chunk lands in some consumer thread's registers
           const int planes = st == GROM_F32X2 ? 2 : 1;
-          CHECK(k1_rmax(p.qm, planes) >= 1 && (p.rpc + p.rpr - 1) / p.rpr <= k1_rmax(p.qm, planes),
+          const int64_t rpr = k1_row_step(p, st);
+          CHECK(k1_rmax(p.qm, planes) >= 1 && (p.rpc + rpr - 1) / rpr <= k1_rmax(p.qm, planes),
                 "K1 rows per thread st %d packed %d n %ld", st, packed, (long)n);
-          CHECK(!packed || p.rpr == p.rg, "K1 packed row step n %ld", (long)n);
           CHECK(p.row_bytes <= K1_MAX_ROW_BYTES && p.row_bytes % 16 == 0, "K1 row bytes %ld", (long)p.row_bytes);
           CHECK((int64_t)p.grid * (p.maxseg - 1) * p.cpi >= p.T - p.grid * p.cpi, "K1 segments n %ld", (long)n);
         }
@@ -95,6 +95,13 @@ static void check_k3t(int64_t n, int64_t r, int form, int batch, int sm, int s1,
   CHECK((s1 == 0 || p.s1 == s1) && (s2 == 0 || p.s2 == s2), "K3T forced splits (%d, %d) -> (%d, %d)", s1, s2, p.s1,
         p.s2);
   CHECK(p.btile % 16 == 0 && p.btile <= 128 && p.bp >= batch && p.bp - batch < p.btile, "K3T btile");
+  // projection kernel: nseg accumulators of 2 btile columns in tensor memory
+  CHECK(p.smem_p <= SMEM_MAX && p.stages_p >= 2, "K3T projection smem %zu stages %d", p.smem_p, p.stages_p);
+  CHECK(tmem_ok(p.tmem_p) && p.tmem_p >= p.nseg * 2 * p.btile, "K3T projection tmem %d (nseg %d btile %d)", p.tmem_p,
+        p.nseg, p.btile);
+  CHECK(p.jtiles * 128 >= p.rp && p.ctiles <= K3T_MAX_CTILES, "K3T tiles %d x %d", p.jtiles, p.ctiles);
+  // the counters sit at the start of the scratch, one region per (n, r)
+  CHECK(k3t_counter_bytes(p) == k3t_counter_bytes(k3t_plan(n, r, form, 16, sm)), "K3T counter region moves");
   CHECK(k3t_scratch_bytes(p) <= need, "K3T scratch n %ld r %ld b %d (%d, %d): %zu > %zu", (long)n, (long)r, batch,
         p.s1, p.s2, k3t_scratch_bytes(p), need);
 }
