@@ -1180,6 +1180,28 @@ grom_status grom_step(grom_traj* t, int32_t nsteps, double* energy, double* inva
     cudaGetLastError();
     if (e0) --r->prof_used;  // the timing pair was not recorded
   }
+  // batched CP forms on the tensor cores (K3T, diagonal operators): every
+  // step of a call of two or more steps in one persistent cooperative
+  // launch, serving pools included, up to 2^18 state elements per batch
+  // (1024 trajectories of N = 1024 step faster through the per-step kernels,
+  // whose step kernel hides its latency with many more warps per SM);
+  // single-step calls, timed calls and launches that cannot be placed take
+  // the per-step kernels below
+  if (r->diagonal && is_cp(r) && r->k3t_factors && use_k3t(r, t->batch) && nsteps >= 2 && !r->prof &&
+      (int64_t)t->batch * r->n <= K3TP_MAX_ELEMENTS) {
+    StepArgs a = step_args(t, energy, invariant);
+    K3Args k = k3_args(r);
+    k.hist = t->hist;
+    k.taken = t->taken;
+    k.hist_stride = 6 * (int64_t)r->n;
+    k.active = t->active;
+    const cudaError_t e = k3tp_launch(k3t_plan_of(r, t->batch), &r->k3t_tmap_ft, &r->k3t_tmap_ae, k, t->batch,
+                                      r->k3t_scratch, r->err, a, nsteps, r->sm_count, r->stream);
+    if (e == cudaSuccess) return GROM_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorInvalidValue)
+      return cuda_fail(e, "grom_step persistent launch");
+    cudaGetLastError();
+  }
   constexpr int G = 8;  // steps per captured graph
   int done = 0;
   if (!energy && !invariant && nsteps >= G) {

@@ -243,6 +243,16 @@ cudaError_t k3t_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensor
 cudaError_t k3t_launch_step(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a,
                             int batch, void* scratch, int* err, bool prep, const StepArgs& st, int step_index,
                             cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s);
+// Persistent batched stepper: nsteps diagonal steps of the batch in one
+// cooperative launch of one CTA per SM (projection, expansion and step
+// phases between grid barriers; the same tiles and arithmetic as the
+// per-step kernels).  Returns an error without launching when the plan or
+// the device does not allow it; the caller then takes the per-step path.
+size_t k3tp_smem(const K3TPlan& p);
+constexpr int64_t K3TP_MAX_ELEMENTS = 1 << 18;  // batch x n up to which grom_step takes the persistent stepper
+cudaError_t k3tp_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a,
+                        int batch, void* scratch, int* err, const StepArgs& st, int nsteps, int sm_count,
+                        cudaStream_t s);
 // Persistent cooperative CPD-ROM stepper for a few trajectories.
 size_t k3p_scratch_bytes(int64_t n, int64_t rp, int storage, int sm_count);
 int k3p_max_batch(int storage);

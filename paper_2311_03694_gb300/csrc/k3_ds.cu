@@ -25,6 +25,7 @@
 namespace grom {
 
 constexpr int D_BM = 64, D_BN = 64, D_BK = 16;
+constexpr int D_FAST_SPLITS = 8;  // split counts whose partials the last CTA loads all at once
 
 struct DDims {
   int64_t n, rp, kp;  // modes, padded rank (factor row pitch), state row pitch (n rounded up to D_BK)
@@ -206,13 +207,34 @@ __global__ void __launch_bounds__(256) k3d_project(const DDims d, const float* f
       const int64_t r = r0 + tx * 4 + y;
       if (r >= d.rp) continue;
       float Sv[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f};
-      for (int z = 0; z < sp.ks; ++z)
+      const float* src0 = part + (int64_t)b * d.rp + r;
+      if (sp.ks <= D_FAST_SPLITS) {
+        // every split's pair loaded before the sums (the L2 reads in flight
+        // together), then summed in split order as below
+        float w[D_FAST_SPLITS][3][2];
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
-          if (f < d.nf) {
-            const float* src = part + (((int64_t)z * d.nf + f) * 2) * plane + (int64_t)b * d.rp + r;
-            ds_add(Sv[f], sv[f], __ldcg(src), __ldcg(src + plane));
-          }
+        for (int z = 0; z < D_FAST_SPLITS; ++z)
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            if (z < sp.ks && f < d.nf) {
+              const float* src = src0 + (((int64_t)z * d.nf + f) * 2) * plane;
+              w[z][f][0] = __ldcg(src);
+              w[z][f][1] = __ldcg(src + plane);
+            }
+#pragma unroll
+        for (int z = 0; z < D_FAST_SPLITS; ++z)
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            if (z < sp.ks && f < d.nf) ds_add(Sv[f], sv[f], w[z][f][0], w[z][f][1]);
+      } else {
+        for (int z = 0; z < sp.ks; ++z)
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            if (f < d.nf) {
+              const float* src = src0 + (((int64_t)z * d.nf + f) * 2) * plane;
+              ds_add(Sv[f], sv[f], __ldcg(src), __ldcg(src + plane));
+            }
+      }
       write_h(b, r, Sv, sv);
     }
   }
@@ -344,9 +366,23 @@ __global__ void __launch_bounds__(256) k3d_expand(const DDims d, const K3Args a,
       const int64_t i = i0 + tx * 4 + y;
       if (i >= d.n) continue;
       float Sv = 0.f, sv = 0.f;
-      for (int z = 0; z < sp.ks; ++z) {
-        const float* p = part + (int64_t)z * 2 * oplane + (int64_t)b * d.n + i;
-        ds_add(Sv, sv, __ldcg(p), __ldcg(p + oplane));
+      const float* p0 = part + (int64_t)b * d.n + i;
+      if (sp.ks <= D_FAST_SPLITS) {
+        float w[D_FAST_SPLITS][2];
+#pragma unroll
+        for (int z = 0; z < D_FAST_SPLITS; ++z)
+          if (z < sp.ks) {
+            w[z][0] = __ldcg(p0 + (int64_t)z * 2 * oplane);
+            w[z][1] = __ldcg(p0 + (int64_t)z * 2 * oplane + oplane);
+          }
+#pragma unroll
+        for (int z = 0; z < D_FAST_SPLITS; ++z)
+          if (z < sp.ks) ds_add(Sv, sv, w[z][0], w[z][1]);
+      } else {
+        for (int z = 0; z < sp.ks; ++z) {
+          const float* p = p0 + (int64_t)z * 2 * oplane;
+          ds_add(Sv, sv, __ldcg(p), __ldcg(p + oplane));
+        }
       }
       dst[i] = (double)Sv + (double)sv;
     }

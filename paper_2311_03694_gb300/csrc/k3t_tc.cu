@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "grom_internal.h"
+#include "step_mc.cuh"
 #include "tc.cuh"
 
 namespace grom {
@@ -70,36 +71,161 @@ __device__ __forceinline__ void k3t_abort(volatile int* abort_flag, int* err) {
   atomicOr(err, DEV_ERR_TIMEOUT);
 }
 
+// One pipeline ring of a tcgen05 GEMM: S stage slots, each stage_a bytes of
+// A boxes and stage_b bytes of the hi/lo B boxes, with full/empty barriers
+// and the accumulator barrier.  The roles count the K steps they have
+// handled (`it`) across tiles, so a CTA can run several tiles, and the
+// persistent stepper several phases, on one ring without re-arming it.
+struct K3TRing {
+  uint8_t* sa;
+  uint8_t* sb;
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* accum;
+  int S, stage_a, stage_b;
+};
+
+__device__ __forceinline__ K3TRing k3t_ring(uint8_t* base, uint64_t* bars, int S, int na, int btile) {
+  K3TRing R;
+  R.S = S;
+  R.stage_a = na * K3T_A_BYTES;
+  R.stage_b = 2 * btile * 128;
+  R.sa = base;
+  R.sb = base + (size_t)S * R.stage_a;
+  R.full = bars;
+  R.empty = bars + S;
+  R.accum = bars + 2 * S;
+  return R;
+}
+
+__device__ __forceinline__ void k3t_ring_init(const K3TRing& R) {
+  for (int s = 0; s < R.S; ++s) {
+    ptx::mbar_init(&R.full[s], 1);
+    ptx::mbar_init(&R.empty[s], 1);
+  }
+  ptx::mbar_init(R.accum, 1);
+}
+
+// TMA producer of one tile (one thread): T K steps of na A boxes (rows
+// a_row + seg a_step of ta) and the hi/lo B boxes (rows b_row).
+__device__ __forceinline__ void k3t_produce(const K3TRing& R, const CUtensorMap* ta, const CUtensorMap* tbh,
+                                            const CUtensorMap* tbl, int na, int32_t a_row, int32_t a_step,
+                                            int32_t b_row, int64_t kb0, int64_t T, uint32_t& it,
+                                            volatile int* abort_flag, int* err) {
+  const int b_half = R.stage_b / 2;
+  for (int64_t t = 0; t < T; ++t) {
+    const uint32_t s = it % (uint32_t)R.S;
+    if (it >= (uint32_t)R.S && !ptx::mbar_wait(&R.empty[s], ((it / R.S) & 1u) ^ 1u, abort_flag)) {
+      k3t_abort(abort_flag, err);
+      return;
+    }
+    const int32_t x = (int32_t)((kb0 + t) * 64);
+    ptx::mbar_arrive_expect_tx(&R.full[s], (uint32_t)(R.stage_a + R.stage_b));
+    uint8_t* a = R.sa + (size_t)s * R.stage_a;
+    for (int seg = 0; seg < na; ++seg) tc::tma_load_2d(a + seg * K3T_A_BYTES, ta, x, a_row + seg * a_step, &R.full[s]);
+    uint8_t* b = R.sb + (size_t)s * R.stage_b;
+    tc::tma_load_2d(b, tbh, x, b_row, &R.full[s]);
+    tc::tma_load_2d(b + b_half, tbl, x, b_row, &R.full[s]);
+    ++it;
+  }
+}
+
+// The last min(S, issued) loads of the ring have landed (before the CTA
+// exits: no copy may still be writing its shared memory).  it0: the count
+// when this CTA's producer started.
+__device__ __forceinline__ void k3t_drain(const K3TRing& R, uint32_t it0, uint32_t it, int* err) {
+  const uint32_t lo = it - it0 > (uint32_t)R.S ? it - (uint32_t)R.S : it0;
+  for (uint32_t q = lo; q < it; ++q)
+    if (!ptx::mbar_wait(&R.full[q % R.S], (q / R.S) & 1u, nullptr)) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+// MMA issuer of one tile (one thread): per K step, each of the na A boxes
+// times the B boxes (M = 128, N = 2 btile: hi | lo) into the accumulator at
+// tmem + seg acc_step columns; then the accumulator barrier.
+__device__ __forceinline__ void k3t_mma(const K3TRing& R, uint32_t tmem, int na, uint32_t acc_step, uint32_t idesc,
+                                        int64_t T, uint32_t& it, volatile int* abort_flag, int* err) {
+  for (int64_t t = 0; t < T; ++t) {
+    const uint32_t s = it % (uint32_t)R.S;
+    if (!ptx::mbar_wait(&R.full[s], (it / R.S) & 1u, abort_flag)) {
+      k3t_abort(abort_flag, err);
+      break;
+    }
+    tc::fence_after_sync();
+    const uint64_t bd = tc::sw128_kmajor_desc(R.sb + (size_t)s * R.stage_b);  // 2 btile rows
+    for (int seg = 0; seg < na; ++seg) {
+      const uint64_t ad = tc::sw128_kmajor_desc(R.sa + (size_t)s * R.stage_a + seg * K3T_A_BYTES);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tc::mma_bf16(tmem + (uint32_t)seg * acc_step, ad + 2 * k, bd + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
+    }
+    tc::commit(&R.empty[s]);
+    ++it;
+  }
+  tc::commit(R.accum);  // arrives once every issued MMA has completed
+}
+
+// Epilogue warps (2-5) wait for the tile's accumulator; parity: the tile's
+// index among the ring's tiles in this CTA.
+__device__ __forceinline__ bool k3t_wait_accum(const K3TRing& R, uint32_t parity, int* err) {
+  const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(R.accum, parity, nullptr));
+  if (!ok && (threadIdx.x & 31) == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+  tc::fence_after_sync();
+  return ok;
+}
+
+// Tile coordinates of a flattened tile index: split fastest, then the column tile.
+struct K3TTile {
+  int split, ct, mt;
+  int64_t kb0, T;
+};
+
+__device__ __forceinline__ K3TTile k3t_tile(int idx, int splits, int ctiles, int64_t K) {
+  K3TTile t;
+  t.split = idx % splits;
+  const int rest = idx / splits;
+  t.ct = rest % ctiles;
+  t.mt = rest / ctiles;
+  const int64_t kblocks = K / 64;
+  t.kb0 = (int64_t)t.split * kblocks / splits;
+  t.T = ((int64_t)t.split + 1) * kblocks / splits - t.kb0;
+  return t;
+}
+
+// Expansion epilogue: lane = output row m, column = trajectory; for each
+// column the 32 lanes store 32 consecutive m of that trajectory's row.
+__device__ __forceinline__ void k3t_gemm_epilogue(const K3TGemm& g, uint32_t tmem, const K3TTile& tl, bool run) {
+  const int q = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+  if (!run) return;
+  const int64_t m = (int64_t)tl.mt * 128 + 32 * q + lane;
+  const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
+  float* dst = g.out + ((int64_t)tl.split * g.bp + (int64_t)tl.ct * g.btile) * g.M + m;
+  for (int c0 = 0; c0 < g.btile; c0 += 16) {
+    uint32_t v[16], w[16];
+    tc::tmem_ld_32x32b_x16(acc + (uint32_t)c0, v);
+    tc::tmem_ld_32x32b_x16(acc + (uint32_t)(g.btile + c0), w);
+    tc::tmem_ld_wait();
+    if (m < g.M) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * g.M] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(K3T_THREADS, 1)
     k3t_gemm(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_bh,
              const __grid_constant__ CUtensorMap tmap_bl, const K3TGemm g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
-  const int S = g.stages;
-  const int b_half = g.btile * 128;
-  const int stage_b = 2 * b_half;
-  uint8_t* sa = smem;
-  uint8_t* sb = sa + (size_t)S * K3T_A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sb + (size_t)S * stage_b);
-  uint64_t* empty = full + S;
-  uint64_t* accum = empty + S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * (K3T_A_BYTES + 2 * g.btile * 128));
+  const K3TRing R = k3t_ring(smem, bars, g.stages, 1, g.btile);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(R.accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int split = blockIdx.x % g.splits;
-  const int rest = blockIdx.x / g.splits;
-  const int ct = rest % g.ctiles, mt = rest / g.ctiles;
-  const int64_t kblocks = g.K / 64;
-  const int64_t kb0 = (int64_t)split * kblocks / g.splits, kb1 = ((int64_t)split + 1) * kblocks / g.splits;
-  const int64_t T = kb1 - kb0;
+  const K3TTile tl = k3t_tile(blockIdx.x, g.splits, g.ctiles, g.K);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
-    }
-    ptx::mbar_init(accum, 1);
+    k3t_ring_init(R);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
@@ -118,67 +244,20 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int64_t t = 0;
-      for (; t < T; ++t) {
-        const int s = (int)(t % S);
-        if (t >= S && !ptx::mbar_wait(&empty[s], (uint32_t)(((t / S) & 1) ^ 1), abort_flag)) {
-          k3t_abort(abort_flag, g.err);
-          break;
-        }
-        const int32_t x = (int32_t)((kb0 + t) * 64);
-        ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(K3T_A_BYTES + stage_b));
-        tc::tma_load_2d(sa + (size_t)s * K3T_A_BYTES, &tmap_a, x, mt * 128, &full[s]);
-        uint8_t* b = sb + (size_t)s * stage_b;
-        tc::tma_load_2d(b, &tmap_bh, x, ct * g.btile, &full[s]);
-        tc::tma_load_2d(b + b_half, &tmap_bl, x, ct * g.btile, &full[s]);
-      }
-      for (int64_t q = t > S ? t - S : 0; q < t; ++q)
-        if (!ptx::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), nullptr)) atomicOr(g.err, DEV_ERR_TIMEOUT);
+      uint32_t it = 0;
+      k3t_produce(R, &tmap_a, &tmap_bh, &tmap_bl, 1, tl.mt * 128, 0, tl.ct * g.btile, tl.kb0, tl.T, it, abort_flag,
+                  g.err);
+      k3t_drain(R, 0, it, g.err);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(128, 2 * g.btile);  // hi | lo
-      for (int64_t t = 0; t < T; ++t) {
-        const int s = (int)(t % S);
-        if (!ptx::mbar_wait(&full[s], (uint32_t)((t / S) & 1), abort_flag)) {
-          k3t_abort(abort_flag, g.err);
-          break;
-        }
-        tc::fence_after_sync();
-        const uint64_t ad = tc::sw128_kmajor_desc(sa + (size_t)s * K3T_A_BYTES);
-        const uint64_t bd = tc::sw128_kmajor_desc(sb + (size_t)s * stage_b);  // 2 btile rows
-#pragma unroll
-        for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
-        tc::commit(&empty[s]);
-      }
-      tc::commit(accum);  // arrives once every issued MMA has completed
+      uint32_t it = 0;
+      k3t_mma(R, tmem, 1, 0, tc::idesc_bf16_f32(128, 2 * g.btile), tl.T, it, abort_flag, g.err);
     }
   } else {
-    // ----------------------------------------------------- epilogue (warps 2-5)
-    const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(accum, 0, nullptr));
-    if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
-    tc::fence_after_sync();
-    const int q = warp & 3;
-    if (ok && T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0)) {
-      // lane = output row m, column = trajectory: for each column the 32
-      // lanes store 32 consecutive m of that trajectory's row
-      const int64_t m = (int64_t)mt * 128 + 32 * q + lane;
-      const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
-      float* dst = g.out + ((int64_t)split * g.bp + (int64_t)ct * g.btile) * g.M + m;
-      for (int c0 = 0; c0 < g.btile; c0 += 16) {
-        uint32_t v[16], w[16];
-        tc::tmem_ld_32x32b_x16(acc + (uint32_t)c0, v);
-        tc::tmem_ld_32x32b_x16(acc + (uint32_t)(g.btile + c0), w);
-        tc::tmem_ld_wait();
-        if (m < g.M) {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * g.M] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
-        }
-      }
-    }
+    const bool ok = k3t_wait_accum(R, 0, g.err);
+    k3t_gemm_epilogue(g, tmem, tl, ok && tl.T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0));
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -239,46 +318,89 @@ __device__ __forceinline__ void k3t_reduce_splits(const K3TProj& g, int jt, int 
   }
 }
 
+// Projection epilogue of tile (jt = tl.mt, ct, split): Z rows of rank
+// indices j0 = 128 jt .. j0 + 127 (lane = row), or with split K this
+// split's partials and, for the last split of the tile to arrive, their sum
+// in split order.  Rows past rp belong to the next segment or lie past the
+// factor copy (zero-filled); they are not stored.
+__device__ __forceinline__ void k3t_proj_epilogue(const K3TProj& g, uint32_t tmem, const K3TTile& tl, bool run,
+                                                  volatile int* abort_flag, volatile int* last_flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;
+  const int jt = tl.mt, ct = tl.ct, split = tl.split;
+  const int64_t j = (int64_t)jt * 128 + 32 * q + lane;
+  const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
+  if (run) {
+    for (int c0 = 0; c0 < g.btile; c0 += 16) {
+      float pv[3][16];
+#pragma unroll
+      for (int seg = 0; seg < 3; ++seg) {
+        if (seg < g.nseg) {
+          uint32_t v[16], w[16];
+          tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + c0), v);
+          tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + g.btile + c0), w);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) pv[seg][c] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) pv[seg][c] = 0.f;
+        }
+      }
+      if (j < g.rp) {
+        const int64_t b0 = (int64_t)ct * g.btile + c0;
+        if (g.splits == 1) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) k3t_store_z(g, b0 + c, j, 0.f + pv[0][c], 0.f + pv[1][c], 0.f + pv[2][c]);
+        } else {
+          // this split's partials (all three segments; zero where the form has two)
+          float* blk = k3t_part_block(g, split, jt, ct) + c0 * 384 + 32 * q + lane;
+#pragma unroll
+          for (int seg = 0; seg < 3; ++seg)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) blk[(c * 3 + seg) * 128] = pv[seg][c];
+        }
+      }
+    }
+  }
+  if (g.splits > 1) {
+    // the last split of the tile to arrive sums the partials in split order
+    const int tile = jt * g.ctiles + ct;
+    __threadfence();
+    ptx::named_sync(1, 128);
+    if (warp == 2 && lane == 0) *last_flag = atomicAdd(&g.cnt[tile], 1u) == (unsigned)(g.splits - 1);
+    ptx::named_sync(1, 128);
+    if (*last_flag) {
+      __threadfence();
+      if (j < g.rp && !*abort_flag) k3t_reduce_splits(g, jt, ct, 32 * q + lane, j);
+      if (warp == 2 && lane == 0) g.cnt[tile] = 0u;
+    }
+  }
+}
+
 // The projections and the Hadamard products of one tile: rank indices
 // j0 = 128 jt .. j0 + 127 and trajectories of column tile ct.  Per K step the
 // producer loads the nseg A boxes (rows seg rp + j0 of FT: V^T, W^T, U^T for
 // the skew form, B^T, C^T for the general one) and the hi/lo state boxes; the
 // MMA warp multiplies each A box with the shared state tile into its own
-// accumulator (tensor-memory columns seg 2 btile .. +2 btile: hi | lo).  Rows
-// of an A box past rp belong to the next segment or lie past the tensor
-// (zero-filled); their outputs are not stored.
+// accumulator (tensor-memory columns seg 2 btile .. +2 btile: hi | lo).
 __global__ void __launch_bounds__(K3T_THREADS, 1)
     k3t_proj(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_bh,
              const __grid_constant__ CUtensorMap tmap_bl, const K3TProj g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
-  const int S = g.stages;
-  const int b_half = g.btile * 128;
-  const int stage_a = g.nseg * K3T_A_BYTES;
-  const int stage_b = 2 * b_half;
-  uint8_t* sa = smem;
-  uint8_t* sb = sa + (size_t)S * stage_a;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sb + (size_t)S * stage_b);
-  uint64_t* empty = full + S;
-  uint64_t* accum = empty + S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * (g.nseg * K3T_A_BYTES + 2 * g.btile * 128));
+  const K3TRing R = k3t_ring(smem, bars, g.stages, g.nseg, g.btile);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(R.accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* last_flag = abort_flag + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int split = blockIdx.x % g.splits;
-  const int rest = blockIdx.x / g.splits;
-  const int ct = rest % g.ctiles, jt = rest / g.ctiles;
-  const int64_t kblocks = g.K / 64;
-  const int64_t kb0 = (int64_t)split * kblocks / g.splits, kb1 = ((int64_t)split + 1) * kblocks / g.splits;
-  const int64_t T = kb1 - kb0;
+  const K3TTile tl = k3t_tile(blockIdx.x, g.splits, g.ctiles, g.K);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
-    }
-    ptx::mbar_init(accum, 1);
+    k3t_ring_init(R);
     *abort_flag = 0;
     *last_flag = 0;
     ptx::fence_mbar_init();
@@ -298,110 +420,282 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int64_t t = 0;
-      for (; t < T; ++t) {
-        const int s = (int)(t % S);
-        if (t >= S && !ptx::mbar_wait(&empty[s], (uint32_t)(((t / S) & 1) ^ 1), abort_flag)) {
-          k3t_abort(abort_flag, g.err);
-          break;
-        }
-        const int32_t x = (int32_t)((kb0 + t) * 64);
-        ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_a + stage_b));
-        for (int seg = 0; seg < g.nseg; ++seg)
-          tc::tma_load_2d(sa + (size_t)s * stage_a + seg * K3T_A_BYTES, &tmap_a, x,
-                          (int32_t)(seg * g.rp + (int64_t)jt * 128), &full[s]);
-        uint8_t* b = sb + (size_t)s * stage_b;
-        tc::tma_load_2d(b, &tmap_bh, x, ct * g.btile, &full[s]);
-        tc::tma_load_2d(b + b_half, &tmap_bl, x, ct * g.btile, &full[s]);
-      }
-      for (int64_t q = t > S ? t - S : 0; q < t; ++q)
-        if (!ptx::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), nullptr)) atomicOr(g.err, DEV_ERR_TIMEOUT);
+      uint32_t it = 0;
+      k3t_produce(R, &tmap_a, &tmap_bh, &tmap_bl, g.nseg, tl.mt * 128, (int32_t)g.rp, tl.ct * g.btile, tl.kb0, tl.T,
+                  it, abort_flag, g.err);
+      k3t_drain(R, 0, it, g.err);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(128, 2 * g.btile);  // hi | lo
-      for (int64_t t = 0; t < T; ++t) {
-        const int s = (int)(t % S);
-        if (!ptx::mbar_wait(&full[s], (uint32_t)((t / S) & 1), abort_flag)) {
-          k3t_abort(abort_flag, g.err);
-          break;
-        }
-        tc::fence_after_sync();
-        const uint64_t bd = tc::sw128_kmajor_desc(sb + (size_t)s * stage_b);  // 2 btile rows
-        for (int seg = 0; seg < g.nseg; ++seg) {
-          const uint64_t ad = tc::sw128_kmajor_desc(sa + (size_t)s * stage_a + seg * K3T_A_BYTES);
-          const uint32_t d = tmem + (uint32_t)(seg * 2 * g.btile);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) tc::mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (t > 0 || k > 0) ? 1u : 0u);
-        }
-        tc::commit(&empty[s]);
-      }
-      tc::commit(accum);  // arrives once every issued MMA has completed
+      uint32_t it = 0;
+      k3t_mma(R, tmem, g.nseg, (uint32_t)(2 * g.btile), tc::idesc_bf16_f32(128, 2 * g.btile), tl.T, it, abort_flag,
+              g.err);
     }
   } else {
-    // ----------------------------------------------------- epilogue (warps 2-5)
-    const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(accum, 0, nullptr));
-    if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
-    tc::fence_after_sync();
-    const int q = warp & 3;
-    const bool run = ok && T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0);
-    const int64_t j = (int64_t)jt * 128 + 32 * q + lane;
-    const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16);
-    if (run) {
-      for (int c0 = 0; c0 < g.btile; c0 += 16) {
-        float pv[3][16];
-#pragma unroll
-        for (int seg = 0; seg < 3; ++seg) {
-          if (seg < g.nseg) {
-            uint32_t v[16], w[16];
-            tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + c0), v);
-            tc::tmem_ld_32x32b_x16(acc + (uint32_t)(seg * 2 * g.btile + g.btile + c0), w);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int c = 0; c < 16; ++c) pv[seg][c] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) pv[seg][c] = 0.f;
-          }
-        }
-        if (j < g.rp) {
-          const int64_t b0 = (int64_t)ct * g.btile + c0;
-          if (g.splits == 1) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) k3t_store_z(g, b0 + c, j, 0.f + pv[0][c], 0.f + pv[1][c], 0.f + pv[2][c]);
-          } else {
-            // this split's partials (all three segments; zero where the form has two)
-            float* blk = k3t_part_block(g, split, jt, ct) + c0 * 384 + 32 * q + lane;
-#pragma unroll
-            for (int seg = 0; seg < 3; ++seg)
-#pragma unroll
-              for (int c = 0; c < 16; ++c) blk[(c * 3 + seg) * 128] = pv[seg][c];
-          }
-        }
-      }
-    }
-    if (g.splits > 1) {
-      // the last split of the tile to arrive sums the partials in split order
-      const int tile = jt * g.ctiles + ct;
-      __threadfence();
-      ptx::named_sync(1, 128);
-      if (warp == 2 && lane == 0) *last_flag = atomicAdd(&g.cnt[tile], 1u) == (unsigned)(g.splits - 1);
-      ptx::named_sync(1, 128);
-      if (*last_flag) {
-        __threadfence();
-        if (j < g.rp && !*abort_flag) k3t_reduce_splits(g, jt, ct, 32 * q + lane, j);
-        if (warp == 2 && lane == 0) g.cnt[tile] = 0u;
-      }
-    }
+    const bool ok = k3t_wait_accum(R, 0, g.err);
+    k3t_proj_epilogue(g, tmem, tl, ok && tl.T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0), abort_flag,
+                      last_flag);
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, (uint32_t)g.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------------------------
+// Persistent batched stepper: every step of a grom_step call on a batch of
+// trajectories (a serving pool, with its masks and step budgets) in one
+// cooperative launch of one CTA per SM.  Per step:
+//   projections (the tiles of k3t_proj)    -> grid barrier
+//   expansion   (the tiles of k3t_gemm)    -> grid barrier
+//   step        (the elements of k_step_diag_mc)  -> grid barrier
+// Each GEMM phase keeps its own ring, whose roles count K steps across tiles,
+// phases and steps, and the tensor memory is allocated once.  Rows a later
+// phase reads with TMA (Z, the next state's BF16 rows) are written through
+// the generic proxy, so the writers fence the async proxy before the barrier.
+// The tiles, the split sums and the step's arithmetic are those of the
+// per-step kernels, so the states are bitwise the same.  The step phase runs
+// the standalone kernel's blocks (same energy/invariant bits) when sums or
+// non-identity operators are asked for; in the plain case it spreads the
+// elements over all threads and advances each trajectory's step count (and
+// serving budget) after the next grid barrier.
+struct K3TPersist {
+  StepArgs st;
+  K3TStepFuse kf;
+  K3Args ka;             // the pool's states for the prep at the start of the call
+  int batch, nsteps;
+  int tiles_p, tiles_g;  // tiles of the two GEMM phases
+  int plain;             // 1: flat step phase (no sums, identity mass, no L or f)
+  int64_t np, bp;
+  unsigned int* bar;     // grid barrier word (zero at create; every barrier adds 2^31 in total)
+  uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ void k3tp_grid_sync(unsigned int* bar, int* err, volatile int* abort_flag, bool proxy) {
+  if (proxy) asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    __threadfence();
+    const unsigned int old = atomicAdd(bar, inc);
+    const uint64_t t0 = ptx::globaltimer();
+    for (uint32_t spin = 0;; ++spin) {
+      const unsigned int now = *reinterpret_cast<volatile unsigned int*>(bar);
+      if ((now ^ old) & 0x80000000u) break;
+      if ((spin & 255u) == 255u && ptx::globaltimer() - t0 > ptx::WAIT_LIMIT_NS) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (proxy) asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(K3T_THREADS, 1)
+    k3tp_kernel(const __grid_constant__ CUtensorMap tmap_ft, const __grid_constant__ CUtensorMap tmap_xh,
+                const __grid_constant__ CUtensorMap tmap_xl, const __grid_constant__ CUtensorMap tmap_ae,
+                const __grid_constant__ CUtensorMap tmap_zh, const __grid_constant__ CUtensorMap tmap_zl,
+                const K3TProj gp, const K3TGemm gg, const K3TPersist pp) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  const size_t area_p = (size_t)gp.stages * (gp.nseg * K3T_A_BYTES + 2 * gp.btile * 128);
+  const size_t area_g = (size_t)gg.stages * (K3T_A_BYTES + 2 * gg.btile * 128);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (area_p > area_g ? area_p : area_g));
+  const K3TRing RP = k3t_ring(smem, bars, gp.stages, gp.nseg, gp.btile);
+  const K3TRing RG = k3t_ring(smem, bars + 2 * gp.stages + 1, gg.stages, 1, gg.btile);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * gp.stages + 1 + 2 * gg.stages + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* last_flag = abort_flag + 1;
+  volatile int* bad_sh = abort_flag + 2;
+  volatile int* last_sh = abort_flag + 3;
+  double* sh = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(tmem_slot) + 24);  // 64 doubles
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int G = gridDim.x, g = blockIdx.x;
+  const StepArgs& st = pp.st;
+  int* err = gp.err;
+
+  if (tid == 0) {
+    k3t_ring_init(RP);
+    k3t_ring_init(RG);
+    *abort_flag = 0;
+    *last_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_ft);
+    tc::prefetch_tmap(&tmap_ae);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, pp.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  // the state prep of the call (the rows k3t_prep writes)
+  {
+    __nv_bfloat16* xh = static_cast<__nv_bfloat16*>(pp.kf.xh);
+    __nv_bfloat16* xl = static_cast<__nv_bfloat16*>(pp.kf.xl);
+    const K3Args& a = pp.ka;
+    for (int64_t t = (int64_t)g * K3T_THREADS + tid; t < pp.bp * pp.np; t += (int64_t)G * K3T_THREADS) {
+      const int64_t b = t / pp.np, k = t - b * pp.np;
+      float v = 0.f;
+      if (b < pp.batch && k < st.n && (a.active == nullptr || a.active[b])) {
+        const double* ub = a.hist + b * a.hist_stride + (a.taken[b] % 3) * st.n;
+        v = __double2float_rn(ub[k]);
+      }
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      xh[t] = hi;
+      xl[t] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+  }
+  k3tp_grid_sync(pp.bar, err, abort_flag, true);
+
+  uint32_t itp = 0, itg = 0;           // K steps of each ring (producer and MMA keep their own copy)
+  uint32_t nt_p = 0, nt_g = 0;         // tiles of each ring in this CTA (accumulator parity)
+  const uint32_t idesc = tc::idesc_bf16_f32(128, 2 * gp.btile);
+  for (int step = 0; step < pp.nsteps; ++step) {
+    if (pp.plain && step > 0 && tid == 0) {
+      // the previous step's counts: every element of it is done (grid barrier)
+      for (int b = g; b < pp.batch; b += G)
+        if (!st.active || st.active[b]) step_done(st, b, st.taken[b]);
+    }
+    // ---------------------------------------------------------- projections
+    for (int tile = g; tile < pp.tiles_p; tile += G, ++nt_p) {
+      const K3TTile tl = k3t_tile(tile, gp.splits, gp.ctiles, gp.K);
+      if (warp == 0) {
+        if (lane == 0)
+          k3t_produce(RP, &tmap_ft, &tmap_xh, &tmap_xl, gp.nseg, tl.mt * 128, (int32_t)gp.rp, tl.ct * gp.btile, tl.kb0,
+                      tl.T, itp, abort_flag, err);
+      } else if (warp == 1) {
+        if (lane == 0) k3t_mma(RP, tmem, gp.nseg, (uint32_t)(2 * gp.btile), idesc, tl.T, itp, abort_flag, err);
+      } else {
+        const bool ok = k3t_wait_accum(RP, nt_p & 1u, err);
+        k3t_proj_epilogue(gp, tmem, tl, ok && tl.T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0), abort_flag,
+                          last_flag);
+      }
+      tc::fence_before_sync();
+      __syncthreads();  // the accumulator is free for the next tile
+      tc::fence_after_sync();
+    }
+    k3tp_grid_sync(pp.bar, err, abort_flag, true);
+    // ------------------------------------------------------------ expansion
+    for (int tile = g; tile < pp.tiles_g; tile += G, ++nt_g) {
+      const K3TTile tl = k3t_tile(tile, gg.splits, gg.ctiles, gg.K);
+      if (warp == 0) {
+        if (lane == 0)
+          k3t_produce(RG, &tmap_ae, &tmap_zh, &tmap_zl, 1, tl.mt * 128, 0, tl.ct * gg.btile, tl.kb0, tl.T, itg,
+                      abort_flag, err);
+      } else if (warp == 1) {
+        if (lane == 0) k3t_mma(RG, tmem, 1, 0, idesc, tl.T, itg, abort_flag, err);
+      } else {
+        const bool ok = k3t_wait_accum(RG, nt_g & 1u, err);
+        k3t_gemm_epilogue(gg, tmem, tl, ok && tl.T > 0 && !__any_sync(0xffffffffu, *abort_flag != 0));
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+    k3tp_grid_sync(pp.bar, err, abort_flag, false);
+    // ----------------------------------------------------------------- step
+    if (!pp.plain) {
+      // the standalone kernel's blocks, run by the first STEP_MC_THREADS threads
+      const int nvb = st.nblk * pp.batch;
+      if (tid < STEP_MC_THREADS)
+        for (int vb = g; vb < nvb; vb += G)
+          step_mc_block<false>(st, step, K1Plan{}, K1Args{}, 2, 0, 1, pp.kf, vb % st.nblk, vb / st.nblk, tid,
+                               [] { ptx::named_sync(2, STEP_MC_THREADS); }, sh, bad_sh, last_sh);
+    } else {
+      // four elements per round: every operand of the four is loaded before
+      // any is stepped (the stores of a step could alias the next loads as
+      // far as the compiler knows, which would serialise the rounds)
+      const int64_t n = st.n;
+      __nv_bfloat16* xh = static_cast<__nv_bfloat16*>(pp.kf.xh);
+      __nv_bfloat16* xl = static_cast<__nv_bfloat16*>(pp.kf.xl);
+      const int64_t total = (int64_t)pp.batch * n, stride = (int64_t)G * K3T_THREADS;
+      for (int64_t t0 = (int64_t)g * K3T_THREADS + tid; t0 < total; t0 += 4 * stride) {
+        double uq[4][3], nq[4][3], hd[4], nl[4];
+        int64_t lq[4], iq[4];
+        int bq[4], kq[4];
+        bool on[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t t = t0 + e * stride;
+          on[e] = t < total;
+          const int b = on[e] ? (int)(t / n) : 0;
+          bq[e] = b;
+          iq[e] = t - (int64_t)b * n;
+          on[e] = on[e] && (!st.active || st.active[b]);
+          lq[e] = on[e] ? st.taken[b] : 0;
+          kq[e] = (int)(lq[e] + 1 < st.order ? lq[e] + 1 : st.order);
+          nl[e] = 0.0;
+          hd[e] = 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) uq[e][q] = nq[e][q] = 0.0;
+          if (on[e]) {
+            const double* h = st.hist + bq[e] * st.hist_stride;
+            const int m0 = (int)(lq[e] % 3);
+            for (int q = 0; q < pp.kf.s2; ++q) nl[e] += (double)pp.kf.d2[((int64_t)q * pp.kf.bp + b) * n + iq[e]];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const int m = m0 - q < 0 ? m0 - q + 3 : m0 - q;
+              if (q < kq[e]) {
+                uq[e][q] = h[m * n + iq[e]];
+                if (q > 0) nq[e][q] = h[(3 + m) * n + iq[e]];
+              }
+            }
+            hd[e] = st.hdiag[kq[e] - 1][iq[e]];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (!on[e]) continue;
+          // the plain diagonal step (step_elem with PLAIN), from the loaded operands
+          const int k = kq[e];
+          double ext = 0.0, bdf = 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if (q < k) {
+              const double gq = q == 0 ? nl[e] : nq[e][q];
+              ext = fma(c_alpha[k - 1][q], gq, ext);
+              bdf = fma(st.bdt[k - 1][q], uq[e][q], bdf);
+            }
+          }
+          const double un = -(ext + bdf) * hd[e];
+          double* h = st.hist + bq[e] * st.hist_stride;
+          h[(3 + lq[e] % 3) * n + iq[e]] = nl[e];
+          h[((lq[e] + 1) % 3) * n + iq[e]] = un;
+          const float v = __double2float_rn(un);
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+          xh[(int64_t)bq[e] * pp.np + iq[e]] = hi;
+          xl[(int64_t)bq[e] * pp.np + iq[e]] = __float2bfloat16_rn(v - __bfloat162float(hi));
+          if (((__double_as_longlong(un) >> 52) & 0x7FF) == 0x7FF) report_nonfinite(st, bq[e]);
+        }
+      }
+    }
+    k3tp_grid_sync(pp.bar, err, abort_flag, true);
+  }
+  if (pp.plain && pp.nsteps > 0 && tid == 0)
+    for (int b = g; b < pp.batch; b += G)
+      if (!st.active || st.active[b]) step_done(st, b, st.taken[b]);
+  if (warp == 0 && lane == 0) {
+    k3t_drain(RP, 0, itp, err);
+    k3t_drain(RG, 0, itg, err);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, pp.tmem_cols);
   }
 }
 
@@ -543,7 +837,8 @@ K3TPlan k3t_plan(int64_t n, int64_t r, int form, int batch, int sm_count, int s1
 // zh | zl | expansion partials.  The counters are zeroed at create and reset
 // by the last CTA of each tile.
 size_t k3t_counter_bytes(const K3TPlan& p) {
-  return ((size_t)p.jtiles * K3T_MAX_CTILES * sizeof(unsigned int) + 255) / 256 * 256;
+  // 256 bytes for the persistent stepper's grid-barrier word, then the counters
+  return 256 + ((size_t)p.jtiles * K3T_MAX_CTILES * sizeof(unsigned int) + 255) / 256 * 256;
 }
 
 size_t k3t_scratch_bytes(const K3TPlan& p) {
@@ -607,6 +902,7 @@ static cudaError_t k3t_gemm_launch(const K3TPlan& p, const CUtensorMap* ma, cons
 
 // The pieces of the scratch for plan p.
 struct K3TBufs {
+  unsigned int* bar;
   unsigned int* cnt;
   __nv_bfloat16 *xh, *xl, *zh, *zl;
   float *d1, *d2;
@@ -615,7 +911,8 @@ struct K3TBufs {
 static K3TBufs k3t_bufs(const K3TPlan& p, void* scratch) {
   K3TBufs q{};
   uint8_t* base = static_cast<uint8_t*>(scratch);
-  q.cnt = reinterpret_cast<unsigned int*>(base);
+  q.bar = reinterpret_cast<unsigned int*>(base);
+  q.cnt = reinterpret_cast<unsigned int*>(base + 256);
   q.xh = reinterpret_cast<__nv_bfloat16*>(base + k3t_counter_bytes(p));
   q.xl = q.xh + p.bp * p.np;
   q.d1 = reinterpret_cast<float*>(q.xl + p.bp * p.np);
@@ -691,6 +988,88 @@ cudaError_t k3t_launch_step(const K3TPlan& p, const CUtensorMap* m_ft, const CUt
   f.xh = q.xh;
   f.xl = q.xl;
   return step_diag_mc_k3t_launch(st, step_index, f, s);
+}
+
+size_t k3tp_smem(const K3TPlan& p) {
+  const size_t area_p = (size_t)p.stages_p * (p.nseg * K3T_A_BYTES + 2 * p.btile * 128);
+  const size_t area_g = (size_t)p.stages * (K3T_A_BYTES + 2 * p.btile * 128);
+  return 1024 + std::max(area_p, area_g) + (size_t)(2 * p.stages_p + 1 + 2 * p.stages + 1) * 8 + 24 + 64 * 8;
+}
+
+cudaError_t k3tp_launch(const K3TPlan& p, const CUtensorMap* m_ft, const CUtensorMap* m_ae, const K3Args& a,
+                        int batch, void* scratch, int* err, const StepArgs& st, int nsteps, int sm_count,
+                        cudaStream_t s) {
+  const size_t smem = k3tp_smem(p);
+  if (p.ctiles > K3T_MAX_CTILES || smem > (size_t)K3T_SMEM_MAX || nsteps < 1) return cudaErrorInvalidValue;
+  const K3TBufs q = k3t_bufs(p, scratch);
+  CUtensorMap mft = *m_ft, mae = *m_ae, mxh, mxl, mzh, mzl;
+  if (!k3t_tmap(&mxh, q.xh, p.k1, p.bp, p.btile) || !k3t_tmap(&mxl, q.xl, p.k1, p.bp, p.btile) ||
+      !k3t_tmap(&mzh, q.zh, p.k2, p.bp, p.btile) || !k3t_tmap(&mzl, q.zl, p.k2, p.bp, p.btile))
+    return cudaErrorInvalidValue;
+  K3TProj gp{};
+  gp.rp = p.rp;
+  gp.bp = p.bp;
+  gp.kz = p.k2;
+  gp.K = p.k1;
+  gp.nseg = p.nseg;
+  gp.btile = p.btile;
+  gp.jtiles = p.jtiles;
+  gp.ctiles = p.ctiles;
+  gp.splits = p.s1;
+  gp.stages = p.stages_p;
+  gp.tmem_cols = p.tmem_p;
+  gp.part = q.d1;
+  gp.cnt = q.cnt;
+  gp.zh = q.zh;
+  gp.zl = q.zl;
+  gp.err = err;
+  K3TGemm gg{};
+  gg.M = p.m2;
+  gg.K = p.k2;
+  gg.bp = p.bp;
+  gg.btile = p.btile;
+  gg.mtiles = (int)((p.m2 + 127) / 128);
+  gg.ctiles = p.ctiles;
+  gg.splits = p.s2;
+  gg.stages = p.stages;
+  gg.tmem_cols = p.tmem_cols;
+  gg.out = q.d2;
+  gg.err = err;
+  K3TPersist pp{};
+  pp.st = st;
+  pp.kf.d2 = q.d2;
+  pp.kf.s2 = p.s2;
+  pp.kf.bp = p.bp;
+  pp.kf.np = p.np;
+  pp.kf.xh = q.xh;
+  pp.kf.xl = q.xl;
+  pp.ka = a;
+  pp.batch = batch;
+  pp.nsteps = nsteps;
+  pp.tiles_p = p.jtiles * p.ctiles * p.s1;
+  pp.tiles_g = gg.mtiles * p.ctiles * p.s2;
+  pp.plain = !st.mass_diag && !st.lin_diag && !st.forcing && !st.energy && !st.invariant;
+  pp.np = p.np;
+  pp.bp = p.bp;
+  pp.bar = q.bar;
+  pp.tmem_cols = (uint32_t)std::max(p.tmem_p, p.tmem_cols);
+  cudaError_t e = cudaFuncSetAttribute(k3tp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3tp_kernel, K3T_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  // one CTA per SM at most, and not many more CTAs than the phases have work
+  // for, so a small ROM's pool leaves SMs to the other pools' kernels (64 at
+  // least: with fewer the barriers and the step phase took longer, measured
+  // on a 128-mode pool of 64 trajectories)
+  const int64_t step_units = pp.plain ? ((int64_t)batch * p.n + 4 * K3T_THREADS - 1) / (4 * K3T_THREADS)
+                                      : (int64_t)st.nblk * batch;
+  int64_t grid = std::max<int64_t>({(int64_t)pp.tiles_p, (int64_t)pp.tiles_g, step_units, 64});
+  if (grid > sm_count) grid = sm_count;
+  void* args[] = {&mft, &mxh, &mxl, &mae, &mzh, &mzl, &gp, &gg, &pp};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k3tp_kernel), dim3((unsigned)grid),
+                                     dim3(K3T_THREADS), args, smem, s);
 }
 
 }  // namespace grom

@@ -13,6 +13,7 @@
 #include "grom_internal.h"
 #include "ptx.cuh"
 #include "step_elem.cuh"
+#include "step_mc.cuh"
 
 namespace grom {
 
@@ -43,10 +44,6 @@ __device__ __forceinline__ void block_sum2(double& x, double& y, double* sh) {
   }
 }
 
-__device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
-  atomicOr(a.err, DEV_ERR_NONFINITE);
-  atomicMin(a.first_bad, b);
-}
 
 // Diagonal step spread over nblk CTAs per trajectory (STEP_MC_THREADS each,
 // a.ept elements per thread, strided by the block size).
@@ -54,10 +51,6 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
 // of the trajectory to arrive (arrival counter, no waiting), which also
 // advances the step count.  With k1 set, the K1 partials of the element are
 // summed first (the streaming kernel's finalize, fused).
-// fuse: 0 n^l from the history ring; 1 the K1 partials (finalize fused);
-// 2 the K3T expansion partials, with the new state's BF16 hi/lo rows written
-// for the next projections (the values the state prep would write).
-// PLAIN: identity mass, no linear or forcing term, no energy or invariant.
 template <bool PLAIN>
 __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs a, const int step_index,
                                                                   const K1Plan pl, const K1Args k1a, const int fuse,
@@ -65,76 +58,8 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
   __shared__ double sh[64];
   __shared__ int bad;
   __shared__ int last;
-  const int bl = blockIdx.y;      // trajectory within this launch
-  const int b = b0 + bl;          // trajectory index
-  if (a.active && !a.active[b]) return;
-  const int64_t n = a.n;
-  const int64_t l = a.taken[b];
-  const int k = (int)(l + 1 < a.order ? l + 1 : a.order);
-  double* h = a.hist + b * a.hist_stride;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  const bool sums = !PLAIN && (a.energy || a.invariant);  // energy and invariant asked for
-  double e_part = 0.0, i_part = 0.0;
-  int my_bad = 0;
-  for (int e = 0; e < a.ept; ++e) {
-    const int64_t i = ((int64_t)blockIdx.x * a.ept + e) * STEP_MC_THREADS + threadIdx.x;
-    if (i >= n) break;
-    double nl;
-    if (fuse == 2) {
-      // expansion splits in split order, FP64
-      double sum = 0.0;
-      for (int q = 0; q < kf.s2; ++q) sum += (double)kf.d2[((int64_t)q * kf.bp + b) * n + i];
-      h[(3 + l % 3) * n + i] = sum;
-      nl = sum;
-    } else if (fuse) {
-      // K1 finalize: partials of every CTA whose chunk range covers test index i, in CTA order
-      const int64_t G = pl.grid, T = pl.T;
-      const int64_t g_lo = ((i * pl.cpi + 1) * G - 1) / T, g_hi = (((i + 1) * pl.cpi) * G - 1) / T;
-      double sum = 0.0;
-      for (int64_t g = g_lo; g <= g_hi; ++g) {
-        const int64_t first_i = (g * T / G) / pl.cpi;
-        const double* src = k1a.part + ((g * pl.maxseg + (i - first_i)) * (K1_CONSUMERS / 32)) * nbk + bl;
-#pragma unroll
-        for (int w = 0; w < K1_CONSUMERS / 32; ++w) sum += src[w * nbk];
-      }
-      h[(3 + l % 3) * n + i] = sum;
-      nl = sum;
-    } else {
-      nl = h[(3 + l % 3) * n + i];
-    }
-    double ep, ip;
-    int eb;
-    const double un = step_elem<PLAIN>(a, h, n, l, k, i, nl, ep, ip, eb, sums);
-    if (fuse == 2) {
-      const float v = __double2float_rn(un);
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      static_cast<__nv_bfloat16*>(kf.xh)[(int64_t)b * kf.np + i] = hi;
-      static_cast<__nv_bfloat16*>(kf.xl)[(int64_t)b * kf.np + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-    if (sums) {
-      e_part += ep;
-      i_part += ip;
-    }
-    my_bad |= eb;
-  }
-  if (my_bad) bad = 1;
-  if (sums) {
-    block_sum2(e_part, i_part, sh);
-  } else {
-    __syncthreads();  // `bad` complete before thread 0 reads it
-  }
-  if (threadIdx.x == 0) {
-    if (bad) report_nonfinite(a, b);
-    double* r = a.red + ((int64_t)b * a.nblk + blockIdx.x) * 2;
-    r[0] = e_part;
-    r[1] = i_part;
-    __threadfence();
-    const unsigned prev = atomicAdd(&a.cnt[b], 1u);
-    last = prev == (unsigned)(a.nblk - 1);
-  }
-  __syncthreads();
-  if (last && threadIdx.x < 32) step_finish_last(a, b, l, step_index);
+  step_mc_block<PLAIN>(a, step_index, pl, k1a, fuse, b0, nbk, kf, blockIdx.x, blockIdx.y, threadIdx.x,
+                       [] { __syncthreads(); }, sh, &bad, &last);
 }
 
 // The common case of the diagonal step: identity mass, no linear or forcing

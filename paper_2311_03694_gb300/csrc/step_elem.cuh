@@ -62,8 +62,10 @@ __device__ __forceinline__ double step_elem(const StepArgs& a, double* h, int64_
   e_part = 0.0;
   i_part = 0.0;
   if (sums) {
-    e_part = mass ? mb * un * un : un * un;
-    i_part = u0 * nl;
+    // explicit roundings: the products must not contract into the caller's
+    // sums (FMA), whose form would then depend on the kernel inlining them
+    e_part = mass ? __dmul_rn(__dmul_rn(mb, un), un) : __dmul_rn(un, un);
+    i_part = __dmul_rn(u0, nl);
   }
   bad = ((__double_as_longlong(un) >> 52) & 0x7FF) == 0x7FF;  // inf or NaN
   h[((l + 1) % 3) * n + i] = un;

@@ -144,3 +144,81 @@ def test_tensor_kernel_needs_bf16_cp():
         rom.set_kernel("tensor")
     assert e.value.name == "UNSUPPORTED"
     rom.close()
+
+
+# The persistent batched stepper: a call of two or more steps runs every step
+# in one cooperative launch (projection, expansion and step phases between
+# grid barriers); single-step calls run the per-step kernels.  The tiles, the
+# split sums and the arithmetic are the same, so the states after K steps are
+# bitwise equal either way, and so are the energy and invariant series.
+@pytest.mark.parametrize("form", ["cp_skew", "cp"])
+@pytest.mark.parametrize("n,r,batch", [(200, 129, 70), (256, 96, 16), (130, 64, 130)])
+def test_persistent_stepper_is_bitwise_the_per_step_path(form, n, r, batch):
+    facs, _ = _factors(form, n, r, 500 + n)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, 600 + n, 0, batch)
+    steps = 12
+    rom = grom.Rom(n, form, "bf16", factors=facs, stiffness=a, nu=1e-2, dt=1e-3, max_batch=batch)
+    one = grom.Trajectories(rom, U0)
+    for _ in range(steps):
+        one.step(1)
+    many = grom.Trajectories(rom, U0)
+    many.step(steps)
+    assert many.status()[0] == 0 and one.status()[0] == 0
+    np.testing.assert_array_equal(many.get_state(), one.get_state())
+    # with the energy and invariant asked for (the standalone step blocks)
+    e1 = torch.empty((steps, batch), dtype=torch.float64, device="cuda")
+    i1 = torch.empty_like(e1)
+    e2, i2 = torch.empty_like(e1), torch.empty_like(e1)
+    for s in range(steps):
+        one.step(1, e1[s:s + 1], i1[s:s + 1])
+    many.step(steps, e2, i2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(many.get_state(), one.get_state())
+    assert torch.equal(e1, e2) and torch.equal(i1, i2)
+    one.close()
+    many.close()
+    rom.close()
+
+
+def test_persistent_stepper_matches_oracle():
+    n, r, batch, steps = 160, 80, 40, 25
+    (U, V, W), _ = _factors("cp_skew", n, r, 0)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, 77, 0, batch)
+    rom = grom.Rom(n, "cp_skew", "bf16", factors=(U, V, W), stiffness=a, nu=1e-2, dt=1e-3, max_batch=batch)
+    tr = grom.Trajectories(rom, U0)
+    tr.step(steps)
+    assert tr.status()[0] == 0
+    ref = oracle.Rom("cp_skew", n, a, 1e-2, 1e-3, factors=(U, V, W))
+    for b in (0, batch - 1):
+        h = ref.initial_history(U0[b])
+        ref.step(h, steps)
+        assert _rel(tr.get_state()[b][:n], h[:n]) <= TOL_BF16, b
+    tr.close()
+    rom.close()
+
+
+def test_persistent_stepper_serving_pool_masks_and_budgets():
+    # a pool of uneven requests: quanta of 8 steps (persistent launches) give
+    # the same final states, bit for bit, as quanta of one step (per-step kernels)
+    n, r = 96, 48
+    (U, V, W), _ = _factors("cp_skew", n, r, 0)
+    rom = grom.Rom(n, "cp_skew", "bf16", factors=(U, V, W), stiffness=synth.diag_stiffness(n), max_batch=24)
+    rng = np.random.default_rng(5)
+    count = 40
+    horizons = rng.integers(3, 60, count)
+    arrivals = np.sort(rng.random(count) * 0.01)
+    u0s = [synth.initial_condition(n, 900 + q)[0] for q in range(count)]
+    finals = []
+    for quantum in (8, 1):
+        srv = grom.Server(150 * 2 ** 30, quantum=quantum)
+        mid = srv.add_rom(rom, 24)
+        out = srv.serve([mid] * count, horizons, arrivals, u0s, want_final=True)
+        assert np.all(out["status"] == 0)
+        np.testing.assert_array_equal(out["steps"], horizons)
+        finals.append(out["final"])
+        srv.close()
+    for q in range(count):
+        np.testing.assert_array_equal(finals[0][q], finals[1][q], err_msg="request %d" % q)
+    rom.close()
