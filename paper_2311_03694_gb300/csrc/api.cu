@@ -1087,9 +1087,21 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch) && !use_k2p(r, t->batch);
   const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch) && !use_k3t(r, t->batch);
   const bool fused_k3t = r->diagonal && use_k3t(r, t->batch);
+  const bool fused_k3d = r->diagonal && use_k3d(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
-    if (fused_k3t) {
+    if (fused_k3d) {
+      // as K3T: the state planes once per call, then the ones the step kernel writes
+      K3Args k = k3_args(r);
+      k.hist = t->hist;
+      k.taken = t->taken;
+      k.hist_stride = 6 * (int64_t)r->n;
+      k.active = t->active;
+      cudaEvent_t e0, e1;
+      if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
+      e = k3d_launch_step(r->k3, k, r->k3d_factors, t->batch, r->k3d_scratch, r->sm_count, s == 0, a, s, e0, e1,
+                          strm);
+    } else if (fused_k3t) {
       // the state prep once per call; later steps reuse the rows the step kernel writes
       K3Args k = k3_args(r);
       k.hist = t->hist;

@@ -197,6 +197,14 @@ cudaError_t k3d_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, 
                               cudaStream_t s);
 cudaError_t k3d_launch(const K3Plan& p, const K3Args& a, const void* factors, int batch, int max_batch,
                        void* scratch, int sm_count, cudaStream_t s);
+struct StepArgs;
+// K3D evaluation of step step_index followed by the diagonal step, which sums
+// the expansion's splits and writes the next state's hi/lo planes; the state
+// planes are prepared from the ring only when prep is set (the first step of
+// a call).  ev0/ev1 (optional) bracket the evaluation.
+cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factors, int batch, void* scratch,
+                            int sm_count, bool prep, const StepArgs& st, int step_index, cudaEvent_t ev0,
+                            cudaEvent_t ev1, cudaStream_t s);
 // Batched CP form on the tensor cores (BF16 factors): projections and
 // expansion as two tcgen05 GEMMs over copies of the factors laid out for them.
 struct K3TPlan {
@@ -216,12 +224,14 @@ struct K3TPlan {
 constexpr int K3T_MIN_BATCH = 16;
 constexpr int K3T_MAX_CTILES = 1024;  // column tiles (batch / btile) the counter region covers
 // The expansion's trajectory-major split partials, summed by the step kernel
-// (which also writes the next state's BF16 hi/lo rows for the projections).
+// (which also writes the next state's hi/lo rows for the projections).
+// K3T: s2 x bp x n FP32 partials, BF16 rows; K3D: s2 x (hi, lo) x bp x n
+// double-single partials (bp = the batch), FP32 planes.
 struct K3TStepFuse {
-  const float* d2;  // s2 x bp x n
+  const float* d2;
   int s2;
   int64_t bp, np;
-  void* xh;         // bp x np BF16 (hi), then xl (lo)
+  void* xh;         // bp x np (hi), then xl (lo)
   void* xl;
 };
 // s1_force, s2_force in [1, s1_max] / [1, s2_max] replace the rule's splits.
@@ -323,6 +333,7 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
 // partials (written to the history ring) and the new state also written as
 // BF16 hi/lo rows for the next projections.
 cudaError_t step_diag_mc_k3t_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s);
+cudaError_t step_diag_mc_k3d_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s);
 cudaError_t step_diag_packed_launch(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a, int b0,
                                     int nb, int nbk, cudaStream_t s);
 // Persistent skew-packed stepper (k1p_persist.cuh): nsteps diagonal steps of

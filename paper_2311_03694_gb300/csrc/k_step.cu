@@ -82,13 +82,22 @@ cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan*
   return cudaGetLastError();
 }
 
-cudaError_t step_diag_mc_k3t_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s) {
+static cudaError_t step_diag_mc_fused(const StepArgs& a, int step_index, int fuse, const K3TStepFuse& f,
+                                      cudaStream_t s) {
   dim3 grid((unsigned)a.nblk, (unsigned)a.batch);
   if (step_plain(a))
-    k_step_diag_mc<true><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, 2, 0, 1, f);
+    k_step_diag_mc<true><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, fuse, 0, 1, f);
   else
-    k_step_diag_mc<false><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, 2, 0, 1, f);
+    k_step_diag_mc<false><<<grid, STEP_MC_THREADS, 0, s>>>(a, step_index, K1Plan{}, K1Args{}, fuse, 0, 1, f);
   return cudaGetLastError();
+}
+
+cudaError_t step_diag_mc_k3t_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s) {
+  return step_diag_mc_fused(a, step_index, 2, f, s);
+}
+
+cudaError_t step_diag_mc_k3d_launch(const StepArgs& a, int step_index, const K3TStepFuse& f, cudaStream_t s) {
+  return step_diag_mc_fused(a, step_index, 3, f, s);
 }
 
 // Diagonal step fused with the finalize of the skew-packed streaming kernel

@@ -10,6 +10,7 @@
 
 #include <cuda_bf16.h>
 
+#include "ds_arith.cuh"
 #include "grom_internal.h"
 #include "step_elem.cuh"
 
@@ -48,7 +49,10 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
 
 // fuse: 0 n^l from the history ring; 1 the K1 partials (finalize fused);
 // 2 the K3T expansion partials, with the new state's BF16 hi/lo rows written
-// for the next projections (the values the state prep would write).
+// for the next projections (the values the state prep would write);
+// 3 the K3D expansion's double-single split pairs (or, with one split, the
+// ring, which the expansion wrote), with the new state's FP32 hi/lo planes
+// written for the next projections.
 // PLAIN: identity mass, no linear or forcing term, no energy or invariant.
 template <bool PLAIN, typename Sync>
 __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a,
@@ -70,7 +74,21 @@ __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index,
     const int64_t i = ((int64_t)blk * a.ept + e) * STEP_MC_THREADS + tid;
     if (i >= n) break;
     double nl;
-    if (fuse == 2) {
+    if (fuse == 3) {
+      // expansion splits in split order, double-single (as the K3D finish)
+      if (kf.s2 > 1) {
+        const int64_t oplane = kf.bp * n;
+        float S = 0.f, s = 0.f;
+        for (int q = 0; q < kf.s2; ++q) {
+          const float* p = kf.d2 + (int64_t)q * 2 * oplane + (int64_t)b * n + i;
+          ds_add(S, s, __ldcg(p), __ldcg(p + oplane));
+        }
+        nl = (double)S + (double)s;
+        h[(3 + l % 3) * n + i] = nl;
+      } else {
+        nl = h[(3 + l % 3) * n + i];
+      }
+    } else if (fuse == 2) {
       // expansion splits in split order, FP64
       double sum = 0.0;
       for (int q = 0; q < kf.s2; ++q) sum += (double)kf.d2[((int64_t)q * kf.bp + b) * n + i];
@@ -95,7 +113,12 @@ __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index,
     double ep, ip;
     int eb;
     const double un = step_elem<PLAIN>(a, h, n, l, k, i, nl, ep, ip, eb, sums);
-    if (fuse == 2) {
+    if (fuse == 3) {
+      float hi, lo;
+      ds_split(un, hi, lo);
+      static_cast<float*>(kf.xh)[(int64_t)b * kf.np + i] = hi;
+      static_cast<float*>(kf.xl)[(int64_t)b * kf.np + i] = lo;
+    } else if (fuse == 2) {
       const float v = __double2float_rn(un);
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
       static_cast<__nv_bfloat16*>(kf.xh)[(int64_t)b * kf.np + i] = hi;

@@ -87,3 +87,33 @@ def test_k3d_stepping_matches_oracle():
         assert _rel(tr.get_state()[b][:n], h[:n]) <= 1e-12, b
     tr.close()
     rom.close()
+
+
+@pytest.mark.parametrize("form", ["cp_skew", "cp"])
+@pytest.mark.parametrize("steps", [6, 17])
+def test_k3d_fused_step_bitwise(form, steps):
+    # Stepping sums the expansion's splits in the step kernel, which also
+    # writes the next state's hi/lo planes; a call prepares the planes from
+    # the ring only at its first step.  One call of several steps (graph
+    # replays included) equals single-step calls bit for bit, and the first
+    # step's advection term equals the evaluation entry point's.
+    grom.build()
+    n, r, batch = 200, 129, 70
+    fac, _ = _factors(form, n, r, 3)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, 9, 0, batch)
+    rom = grom.Rom(n, form, "f64", factors=fac, stiffness=a, nu=1e-2, dt=1e-3, max_batch=batch)
+    c = _eval(rom, U0)
+    t1 = grom.Trajectories(rom, U0)
+    t1.step(steps)
+    t2 = grom.Trajectories(rom, U0)
+    for _ in range(steps):
+        t2.step(1)
+    assert t1.status()[0] == 0 and t2.status()[0] == 0
+    np.testing.assert_array_equal(t1.get_state(), t2.get_state())
+    t3 = grom.Trajectories(rom, U0)
+    t3.step(1)
+    np.testing.assert_array_equal(t3.get_state()[:, 4 * n:5 * n], c)
+    for t in (t1, t2, t3):
+        t.close()
+    rom.close()
