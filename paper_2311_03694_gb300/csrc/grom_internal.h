@@ -225,8 +225,9 @@ constexpr int K3T_MIN_BATCH = 16;
 constexpr int K3T_MAX_CTILES = 1024;  // column tiles (batch / btile) the counter region covers
 // The expansion's trajectory-major split partials, summed by the step kernel
 // (which also writes the next state's hi/lo rows for the projections).
-// K3T: s2 x bp x n FP32 partials, BF16 rows; K3D: s2 x (hi, lo) x bp x n
-// double-single partials (bp = the batch), FP32 planes.
+// K3T: s2 x bp x n FP32 partials, BF16 rows [b][i] of pitch np; K3D:
+// s2 x (hi, lo) x bp x n double-single partials (bp = the batch), FP32
+// planes [i][b] of pitch np.
 struct K3TStepFuse {
   const float* d2;
   int s2;

@@ -12,185 +12,246 @@
 // Per-evaluation error against exact FP64 arithmetic at N = R = 1024: ~1e-13.
 //
 //   prep:      the states of the batch as hi/lo planes (FP64 -> two floats).
-//   project:   P = X V, Q = X W (and S = X U for the skew form), B x rp, as
+//   project:   P = X V, Q = X W (and S = X U for the skew form), as
 //              register-tiled double-single GEMMs over K splits; with one
 //              split the epilogue forms H1 = P o Q, H2 = P o S itself.
-//   hadamard:  (K splits) every (b, r) sums its splits' pairs in split
+//   hadamard:  (K splits) every (r, b) sums its splits' pairs in split
 //              order and forms H1, H2 in double-single arithmetic.
-//   expand:    c = H1 A^T (- H2 W^T), B x n, over K splits; with one split
-//              the FP64 result goes straight to the output or to the
-//              advection slot of the history ring.
-//   finish:    (K splits) every (b, i) sums its splits' pairs in order.
-// Output tiles are 32 x 32, 2 x 2 per thread.  The split sums run one thread
-// per output over the whole GPU: a last-CTA reduction (one CTA summing a
-// whole tile, one output per thread and round trip) set the time of small
-// problems.  Every sum is in a fixed order (deterministic).
-// The factors' hi/lo copies are made once, at create, from the FP64 panels.
+//   expand:    c = H1 A^T (- H2 W^T) over K splits; with one split the FP64
+//              result goes straight to the output or to the advection slot
+//              of the history ring.
+//   finish:    (K splits) every (b, i) sums its splits' pairs in order (when
+//              stepping, the step kernel does this and writes the next
+//              state's planes).
+// Output tiles are 32 x 32, 2 x 2 per thread; several CTAs share an SM.
+// Every operand tile is a run of whole rows of a plane laid out for it (the
+// states and H as [k][b], the factors as [i][r] and, for the expansion,
+// transposed [r][i] with the sign of W folded in), so it is copied into
+// shared memory with 16-byte asynchronous copies, two stages deep: the next
+// K tile lands while the current one is multiplied.  Planes are padded with
+// zeros to whole tiles (batch and rank to 32, K to 16), so no copy needs a
+// bound check.  The split sums run one thread per output over the whole GPU
+// (a last-CTA reduction, one CTA summing a tile, set the time of small
+// problems), in a fixed order (deterministic).
+// The factor copies are made once, at create, from the FP64 panels.
 #include <algorithm>
 
 #include "ds_arith.cuh"
 #include "grom_internal.h"
+#include "ptx.cuh"
 
 namespace grom {
 
-constexpr int D_BK = 16;
+constexpr int D_BK = 16;          // K tile
+constexpr int D_T = 32;           // output tile (both dimensions)
 constexpr int D_MAX_SPLITS = 16;
-constexpr int D_GROUP = 4;  // split partials in flight per thread in the split sums
+constexpr int D_GROUP = 4;        // split partials in flight per thread in the split sums
+
+static inline int64_t d_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct DDims {
-  int64_t n, rp, kp;  // modes, padded rank (factor row pitch), state row pitch (n rounded up to D_BK)
+  int64_t n, rp;  // modes; row pitch of the FP64 factor panels (the rank rounded up to 8)
+  int64_t rq;     // rank rounded up to D_T: pitch of the factor copies, rows of H and the expansion's K
+  int64_t kp;     // n rounded up to D_BK: rows of the factor copies and the state planes
+  int64_t nq;     // n rounded up to D_T: pitch of the transposed factor copies
+  int64_t bq;     // batch rounded up to D_T: pitch of the state planes, H and the projection partials
   int batch, nf;
 };
 
 struct DSplit {
   int ks;
-  float* partial;  // ks x nf x 2 x batch x rp (project) or ks x 2 x batch x n (expand)
+  float* partial;  // ks x nf x 2 x rq x bq (project) or ks x 2 x batch x n (expand)
 };
 
-// One FP64 factor panel (count doubles) -> its hi and lo planes.
-__global__ void k3d_split_panel(const double* f, int64_t count, float* hi, float* lo) {
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (int64_t)gridDim.x * blockDim.x)
-    ds_split(f[idx], hi[idx], lo[idx]);
+static DDims d_dims(int64_t n, int64_t rp, int batch, int nf) {
+  return DDims{n, rp, d_up(rp, D_T), d_up(n, D_BK), d_up(n, D_T), d_up(batch, D_T), batch, nf};
 }
 
-// The states of the batch as hi/lo planes, batch x kp each (zero past n and
-// for inactive trajectories).
-__global__ void k3d_prep(const DDims d, const K3Args a, float* xh) {
-  const int b = blockIdx.y;
-  const bool on = b < d.batch && (a.active == nullptr || a.active[b]);
-  const double* u = on ? (a.taken ? a.hist + b * a.hist_stride + (a.taken[b] % 3) * d.n : a.u + b * a.u_stride)
-                       : nullptr;
-  float* xl = xh + (int64_t)d.batch * d.kp;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.kp; k += (int64_t)gridDim.x * blockDim.x) {
+// Factor copies: [fa | fb | fc] x [hi | lo], kp x rq each (zero past n and
+// past the rank), then [fa^T | -fc^T] x [hi | lo], rq x nq each.
+__host__ __device__ inline int64_t d_fplane(const DDims& d) { return d.kp * d.rq; }
+__host__ __device__ inline int64_t d_tplane(const DDims& d) { return d.rq * d.nq; }
+
+__global__ void k3d_build(const uint8_t* op, size_t panel_bytes, const DDims d, float* out) {
+  const int64_t fpl = d_fplane(d), tpl = d_tplane(d);
+  const int64_t total = 6 * fpl + 4 * tpl;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i, r;
+    int q, hl;
+    double sgn = 1.0;
+    if (t < 6 * fpl) {
+      const int64_t plane = t / fpl, e = t - plane * fpl;
+      q = (int)(plane / 2);
+      hl = (int)(plane % 2);
+      i = e / d.rq;
+      r = e - i * d.rq;
+    } else {
+      const int64_t u = t - 6 * fpl, plane = u / tpl, e = u - plane * tpl;
+      const int m = (int)(plane / 2);
+      hl = (int)(plane % 2);
+      q = m == 0 ? 0 : 2;
+      sgn = m == 0 ? 1.0 : -1.0;
+      r = e / d.nq;
+      i = e - r * d.nq;
+    }
     float h = 0.f, l = 0.f;
-    if (on && k < d.n) ds_split(u[k], h, l);
-    xh[(int64_t)b * d.kp + k] = h;
-    xl[(int64_t)b * d.kp + k] = l;
+    if (i < d.n && r < d.rp) {
+      const double* f = reinterpret_cast<const double*>(op + (size_t)q * panel_bytes);
+      ds_split(sgn * f[i * d.rp + r], h, l);
+    }
+    out[t] = hl ? l : h;
   }
 }
 
-// One K tile (16) of a TB x TC output tile, TB = TC = 16 MT, 256 threads as
-// 16 x 16, each owning MT x MT outputs of every term.  The operand tiles are
-// staged in shared memory as hi/lo planes [k][b] and [k][column].
-template <int NF, int MT>
-__global__ void __launch_bounds__(256) k3d_project(const DDims d, const float* fhl, const float* xh, float* hbuf,
+// The states of the batch as hi/lo planes [k][b], kp x bq each (zero past n,
+// for padding columns and for inactive trajectories).
+__global__ void k3d_prep(const DDims d, const K3Args a, float* xh) {
+  const int64_t plane = d.kp * d.bq;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / d.bq;
+    const int b = (int)(t - k * d.bq);
+    float h = 0.f, l = 0.f;
+    if (b < d.batch && k < d.n && (a.active == nullptr || a.active[b])) {
+      const double* u = a.taken ? a.hist + b * a.hist_stride + (a.taken[b] % 3) * d.n : a.u + b * a.u_stride;
+      ds_split(u[k], h, l);
+    }
+    xh[t] = h;
+    xh[plane + t] = l;
+  }
+}
+
+// Shared memory of one CTA: two stages of operand tiles, each [term][hi/lo]
+// [16 k][32], reused after the main loop to transpose the epilogue's
+// outputs.  NA terms of the row operand (states or H), NB of the column
+// operand (factors).
+template <int NA, int NB>
+struct DSmem {
+  float a[2][NA][2][D_BK][D_T];
+  float b[2][NB][2][D_BK][D_T];
+};
+
+// One CTA's K range of a 32 x 32 output tile: for every term t,
+// acc[t][x][y] += sum_k A[a_of(t)][k][2 ty + x] B[t][k][2 tx + y], with the
+// tiles arriving by cp.async two stages deep.  load(stage, kt) issues this
+// thread's copies of K tile kt; every thread commits one group per tile
+// (possibly empty) so that the wait counts match.
+template <int NA, int NB, int NT, typename Load, typename AOf>
+__device__ __forceinline__ void d_mainloop(DSmem<NA, NB>& sm, int64_t kb0, int64_t kb1, Load load, AOf a_of,
+                                           float (&S)[NT][2][2], float (&s)[NT][2][2], int tx, int ty) {
+  if (kb0 < kb1) load(0, kb0);
+  ptx::cp_async_commit();
+  for (int64_t kt = kb0; kt < kb1; ++kt) {
+    const int st = (int)((kt - kb0) & 1);
+    if (kt + 1 < kb1) load(st ^ 1, kt + 1);
+    ptx::cp_async_commit();
+    ptx::cp_async_wait<1>();  // tile kt has landed (this thread's copies) ...
+    __syncthreads();          // ... and every thread's
+#pragma unroll 2  // (rolled, the accumulators would be copied back every k)
+    for (int k = 0; k < D_BK; ++k) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int ta = a_of(t);
+        const float2 ah = *reinterpret_cast<const float2*>(&sm.a[st][ta][0][k][ty * 2]);
+        const float2 al = *reinterpret_cast<const float2*>(&sm.a[st][ta][1][k][ty * 2]);
+        const float2 bh = *reinterpret_cast<const float2*>(&sm.b[st][t][0][k][tx * 2]);
+        const float2 bl = *reinterpret_cast<const float2*>(&sm.b[st][t][1][k][tx * 2]);
+        ds_mac(ah.x, al.x, bh.x, bl.x, S[t][0][0], s[t][0][0]);
+        ds_mac(ah.x, al.x, bh.y, bl.y, S[t][0][1], s[t][0][1]);
+        ds_mac(ah.y, al.y, bh.x, bl.x, S[t][1][0], s[t][1][0]);
+        ds_mac(ah.y, al.y, bh.y, bl.y, S[t][1][1], s[t][1][1]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) ds_renorm(S[t][x][y], s[t][x][y]);
+    __syncthreads();  // stage st is refilled by the next iteration's copies
+  }
+}
+
+// Projections: rows b (the states, one term), columns r (NF factors in the
+// order fb, fc, fa: P, Q, S).  Grid (rq / 32, bq / 32, ks).
+template <int NF>
+__global__ void __launch_bounds__(256, 4) k3d_project(const DDims d, const float* fc, const float* xh, float* hbuf,
                                                    const DSplit sp) {
-  constexpr int TB = 16 * MT, TR = 16 * MT;
-  __shared__ __align__(16) float Us[2][D_BK][TB + 4];
-  __shared__ __align__(16) float Xs[NF][2][D_BK][TR + 4];
+  __shared__ __align__(16) DSmem<1, NF> sm;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int b0 = blockIdx.y * TB;
-  const int64_t r0 = (int64_t)blockIdx.x * TR;
-  const int64_t fplane = d.n * d.rp;
-  // factor q (0 = fa, 1 = fb, 2 = fc) hi plane at fhl + 2 q fplane, lo plane after it;
-  // projections in the order (fb, fc, fa): P, Q, S
-  const int fq[3] = {1, 2, 0};
-  const float* xl = xh + (int64_t)d.batch * d.kp;
-  float S[NF][MT][MT], s[NF][MT][MT];
+  const int64_t b0 = (int64_t)blockIdx.y * D_T, r0 = (int64_t)blockIdx.x * D_T;
+  const int64_t fpl = d_fplane(d), xpl = d.kp * d.bq;
+  float S[NF][2][2], s[NF][2][2];
 #pragma unroll
   for (int f = 0; f < NF; ++f)
 #pragma unroll
-    for (int x = 0; x < MT; ++x)
+    for (int x = 0; x < 2; ++x)
 #pragma unroll
-      for (int y = 0; y < MT; ++y) S[f][x][y] = s[f][x][y] = 0.f;
-  const int64_t nk = (d.n + D_BK - 1) / D_BK;
+      for (int y = 0; y < 2; ++y) S[f][x][y] = s[f][x][y] = 0.f;
+  // 16-byte chunk tid of a K tile's (hi, lo) pair of planes: plane tid / 128,
+  // row (tid % 128) / 8, columns 4 (tid % 8) .. + 3
+  const int hl = tid >> 7, kk = (tid & 127) >> 3, q4 = (tid & 7) * 4;
+  auto load = [&](int st, int64_t kt) {
+    const int64_t k = kt * D_BK + kk;
+    ptx::cp_async16(&sm.a[st][0][hl][kk][q4], xh + hl * xpl + k * d.bq + b0 + q4);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int q = f == 0 ? 1 : f == 1 ? 2 : 0;  // fb, fc, fa
+      ptx::cp_async16(&sm.b[st][f][hl][kk][q4], fc + (2 * q + hl) * fpl + k * d.rq + r0 + q4);
+    }
+  };
+  const int64_t nk = d.kp / D_BK;
   const int64_t kb0 = (int64_t)blockIdx.z * nk / sp.ks, kb1 = ((int64_t)blockIdx.z + 1) * nk / sp.ks;
-  for (int64_t k0 = kb0 * D_BK; k0 < kb1 * D_BK; k0 += D_BK) {
-    // states: TB rows of 16 k as float4 (k < kp always: kp is n rounded up to D_BK, zero past n)
-    for (int e = tid; e < TB * 4; e += 256) {
-      const int lb = e >> 2, li = (e & 3) * 4;
-      const int b = b0 + lb;
-      float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
-      if (b < d.batch) {
-        vh = *reinterpret_cast<const float4*>(xh + (int64_t)b * d.kp + k0 + li);
-        vl = *reinterpret_cast<const float4*>(xl + (int64_t)b * d.kp + k0 + li);
-      }
-      Us[0][li][lb] = vh.x; Us[0][li + 1][lb] = vh.y; Us[0][li + 2][lb] = vh.z; Us[0][li + 3][lb] = vh.w;
-      Us[1][li][lb] = vl.x; Us[1][li + 1][lb] = vl.y; Us[1][li + 2][lb] = vl.z; Us[1][li + 3][lb] = vl.w;
-    }
-    // factors: 16 rows i of TR columns as float4 (rp is a multiple of 8, so a
-    // group of four columns is wholly inside or wholly outside)
-    for (int e = tid; e < 4 * TR; e += 256) {
-      const int xi = e / (TR / 4), xr = (e % (TR / 4)) * 4;
-      const int64_t i = k0 + xi, r = r0 + xr;
-      const bool ok = i < d.n && r < d.rp;
+  d_mainloop<1, NF, NF>(sm, kb0, kb1, load, [](int) { return 0; }, S, s, tx, ty);
+  // epilogue through shared memory (the main loop ended on a barrier):
+  // planes [q][r][b], q = H1h, H1l, H2h, H2l (one split) or the split's pairs
+  constexpr int NQ = 2 * NF;
+  static_assert(sizeof(float) * NQ * D_T * (D_T + 1) <= sizeof(DSmem<1, NF>), "epilogue buffer");
+  float(*tp)[D_T][D_T + 1] = reinterpret_cast<float(*)[D_T][D_T + 1]>(&sm);
+  int nq;
+  if (sp.ks == 1) {
+    nq = NF == 3 ? 4 : 2;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const float* fh = fhl + 2 * fq[f] * fplane + i * d.rp + r;
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(&Xs[f][0][xi][xr]) = ok ? *reinterpret_cast<const float4*>(fh) : z;
-        *reinterpret_cast<float4*>(&Xs[f][1][xi][xr]) = ok ? *reinterpret_cast<const float4*>(fh + fplane) : z;
-      }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < D_BK; ++k) {
-      float uh[MT], ul[MT];
+    for (int x = 0; x < 2; ++x)
 #pragma unroll
-      for (int x = 0; x < MT; ++x) {
-        uh[x] = Us[0][k][ty * MT + x];
-        ul[x] = Us[1][k][ty * MT + x];
-      }
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        float vh[MT], vl[MT];
-#pragma unroll
-        for (int y = 0; y < MT; ++y) {
-          vh[y] = Xs[f][0][k][tx * MT + y];
-          vl[y] = Xs[f][1][k][tx * MT + y];
+      for (int y = 0; y < 2; ++y) {
+        const int rl = tx * 2 + y, bl = ty * 2 + x;
+        float h, l;
+        ds_mul(S[0][x][y], s[0][x][y], S[1][x][y], s[1][x][y], h, l);
+        tp[0][rl][bl] = h;
+        tp[1][rl][bl] = l;
+        if constexpr (NF == 3) {
+          ds_mul(S[0][x][y], s[0][x][y], S[2][x][y], s[2][x][y], h, l);
+          tp[2][rl][bl] = h;
+          tp[3][rl][bl] = l;
         }
-#pragma unroll
-        for (int x = 0; x < MT; ++x)
-#pragma unroll
-          for (int y = 0; y < MT; ++y) ds_mac(uh[x], ul[x], vh[y], vl[y], S[f][x][y], s[f][x][y]);
       }
-    }
+  } else {
+    nq = NQ;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int x = 0; x < MT; ++x)
+      for (int x = 0; x < 2; ++x)
 #pragma unroll
-        for (int y = 0; y < MT; ++y) ds_renorm(S[f][x][y], s[f][x][y]);
-    __syncthreads();
+        for (int y = 0; y < 2; ++y) {
+          tp[2 * f][tx * 2 + y][ty * 2 + x] = S[f][x][y];
+          tp[2 * f + 1][tx * 2 + y][ty * 2 + x] = s[f][x][y];
+        }
   }
-  const int64_t plane = (int64_t)d.batch * d.rp;
-#pragma unroll
-  for (int x = 0; x < MT; ++x) {
-    const int b = b0 + ty * MT + x;
-    if (b >= d.batch) continue;
-#pragma unroll
-    for (int y = 0; y < MT; ++y) {
-      const int64_t r = r0 + tx * MT + y;
-      if (r >= d.rp) continue;
-      const int64_t o = (int64_t)b * d.rp + r;
-      if (sp.ks == 1) {
-        // H1 = P o Q and H2 = P o S as hi/lo planes: hbuf = [H1h | H1l | H2h | H2l], batch x rp each
-        float h, l;
-        ds_mul(S[0][x][y], s[0][x][y], S[1][x][y], s[1][x][y], h, l);
-        hbuf[o] = h;
-        hbuf[plane + o] = l;
-        if constexpr (NF == 3) {
-          ds_mul(S[0][x][y], s[0][x][y], S[2][x][y], s[2][x][y], h, l);
-          hbuf[2 * plane + o] = h;
-          hbuf[3 * plane + o] = l;
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          float* dst = sp.partial + (((int64_t)blockIdx.z * NF + f) * 2) * plane + o;
-          dst[0] = S[f][x][y];
-          dst[plane] = s[f][x][y];
-        }
-      }
-    }
+  __syncthreads();
+  // rows of 32 b, coalesced; H planes rq x bq, partial planes likewise
+  const int64_t plane = d.rq * d.bq;
+  float* dst = sp.ks == 1 ? hbuf : sp.partial + (int64_t)blockIdx.z * NQ * plane;
+  for (int e = tid; e < nq * D_T * D_T; e += 256) {
+    const int q = e / (D_T * D_T), rl = (e / D_T) % D_T, bl = e % D_T;
+    dst[q * plane + (r0 + rl) * d.bq + b0 + bl] = tp[q][rl][bl];
   }
 }
 
-// The projections' K splits summed in split order, one thread per (b, r),
+// The projections' K splits summed in split order, one thread per (r, b),
 // and H1 = P o Q, H2 = P o S formed from the sums.
 template <int NF>
 __global__ void __launch_bounds__(256) k3d_hadamard(const DDims d, const DSplit sp, float* hbuf) {
-  const int64_t plane = (int64_t)d.batch * d.rp;
+  const int64_t plane = d.rq * d.bq;
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < plane; o += (int64_t)gridDim.x * blockDim.x) {
     float S[NF], s[NF];
 #pragma unroll
@@ -225,106 +286,62 @@ __global__ void __launch_bounds__(256) k3d_hadamard(const DDims d, const DSplit 
   }
 }
 
-template <int NM, int MT>
-__global__ void __launch_bounds__(256) k3d_expand(const DDims d, const K3Args a, const float* fhl, const float* hbuf,
+// Expansion: rows b (H1, H2), columns i (fa^T, -fc^T), K = r.  Grid
+// (nq / 32, bq / 32, ks).
+template <int NM>
+__global__ void __launch_bounds__(256) k3d_expand(const DDims d, const K3Args a, const float* fc, const float* hbuf,
                                                   const DSplit sp) {
-  constexpr int TB = 16 * MT, TI = 16 * MT;
-  __shared__ __align__(16) float Hs[NM][2][D_BK][TB + 4];  // [term][hi/lo][r][b]
-  __shared__ __align__(16) float As[NM][2][D_BK][TI + 4];  // [term][hi/lo][r][i]
+  __shared__ __align__(16) DSmem<NM, NM> sm;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int b0 = blockIdx.y * TB;
-  const int64_t i0 = (int64_t)blockIdx.x * TI;
-  const int64_t fplane = d.n * d.rp;
-  const int64_t plane = (int64_t)d.batch * d.rp;
-  // first term: A (fa); second (skew form): -W (fc)
-  const float* Fm[2] = {fhl, fhl + 4 * fplane};
-  float S[MT][MT], s[MT][MT];
+  const int64_t b0 = (int64_t)blockIdx.y * D_T, i0 = (int64_t)blockIdx.x * D_T;
+  const float* ft = fc + 6 * d_fplane(d);
+  const int64_t tpl = d_tplane(d), hpl = d.rq * d.bq;
+  float S[NM][2][2], s[NM][2][2];
 #pragma unroll
-  for (int x = 0; x < MT; ++x)
+  for (int m = 0; m < NM; ++m)
 #pragma unroll
-    for (int y = 0; y < MT; ++y) S[x][y] = s[x][y] = 0.f;
-  const int64_t nk = (d.rp + D_BK - 1) / D_BK;
-  const int64_t kb0 = (int64_t)blockIdx.z * nk / sp.ks, kb1 = ((int64_t)blockIdx.z + 1) * nk / sp.ks;
-  for (int64_t k0 = kb0 * D_BK; k0 < kb1 * D_BK; k0 += D_BK) {
-    // rows b of H and rows i of the factor, 16 r each as float4 (rp is a
-    // multiple of 8 and k0 of 16: a group of four is wholly inside or outside)
-    for (int e = tid; e < TB * 4; e += 256) {
-      const int lb = e >> 2, lr = (e & 3) * 4;
-      const int b = b0 + lb;
-      const int64_t r = k0 + lr;
-      const bool ok = b < d.batch && r < d.rp;
+    for (int x = 0; x < 2; ++x)
 #pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const float* hh = hbuf + 2 * m * plane + (int64_t)b * d.rp + r;
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 vh = ok ? __ldcg(reinterpret_cast<const float4*>(hh)) : z;
-        const float4 vl = ok ? __ldcg(reinterpret_cast<const float4*>(hh + plane)) : z;
-        Hs[m][0][lr][lb] = vh.x; Hs[m][0][lr + 1][lb] = vh.y; Hs[m][0][lr + 2][lb] = vh.z; Hs[m][0][lr + 3][lb] = vh.w;
-        Hs[m][1][lr][lb] = vl.x; Hs[m][1][lr + 1][lb] = vl.y; Hs[m][1][lr + 2][lb] = vl.z; Hs[m][1][lr + 3][lb] = vl.w;
-      }
-    }
-    for (int e = tid; e < TI * 4; e += 256) {
-      const int ai = e >> 2, ar = (e & 3) * 4;
-      const int64_t i = i0 + ai, r = k0 + ar;
-      const bool ok = i < d.n && r < d.rp;
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const float sgn = m == 0 ? 1.f : -1.f;
-        const float* fm = Fm[m] + i * d.rp + r;
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 vh = ok ? *reinterpret_cast<const float4*>(fm) : z;
-        const float4 vl = ok ? *reinterpret_cast<const float4*>(fm + fplane) : z;
-        As[m][0][ar][ai] = sgn * vh.x; As[m][0][ar + 1][ai] = sgn * vh.y;
-        As[m][0][ar + 2][ai] = sgn * vh.z; As[m][0][ar + 3][ai] = sgn * vh.w;
-        As[m][1][ar][ai] = sgn * vl.x; As[m][1][ar + 1][ai] = sgn * vl.y;
-        As[m][1][ar + 2][ai] = sgn * vl.z; As[m][1][ar + 3][ai] = sgn * vl.w;
-      }
-    }
-    __syncthreads();
+      for (int y = 0; y < 2; ++y) S[m][x][y] = s[m][x][y] = 0.f;
+  const int hl = tid >> 7, kk = (tid & 127) >> 3, q4 = (tid & 7) * 4;
+  auto load = [&](int st, int64_t kt) {
+    const int64_t k = kt * D_BK + kk;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-#pragma unroll 1
-      for (int k = 0; k < D_BK; ++k) {
-        float hh[MT], hl[MT], ah[MT], al[MT];
-#pragma unroll
-        for (int x = 0; x < MT; ++x) {
-          hh[x] = Hs[m][0][k][ty * MT + x];
-          hl[x] = Hs[m][1][k][ty * MT + x];
-        }
-#pragma unroll
-        for (int y = 0; y < MT; ++y) {
-          ah[y] = As[m][0][k][tx * MT + y];
-          al[y] = As[m][1][k][tx * MT + y];
-        }
-#pragma unroll
-        for (int x = 0; x < MT; ++x)
-#pragma unroll
-          for (int y = 0; y < MT; ++y) ds_mac(hh[x], hl[x], ah[y], al[y], S[x][y], s[x][y]);
-      }
-#pragma unroll
-      for (int x = 0; x < MT; ++x)
-#pragma unroll
-        for (int y = 0; y < MT; ++y) ds_renorm(S[x][y], s[x][y]);
+      ptx::cp_async16(&sm.a[st][m][hl][kk][q4], hbuf + (2 * m + hl) * hpl + k * d.bq + b0 + q4);
+      ptx::cp_async16(&sm.b[st][m][hl][kk][q4], ft + (2 * m + hl) * tpl + k * d.nq + i0 + q4);
     }
-    __syncthreads();
-  }
+  };
+  const int64_t nk = d.rq / D_BK;
+  const int64_t kb0 = (int64_t)blockIdx.z * nk / sp.ks, kb1 = ((int64_t)blockIdx.z + 1) * nk / sp.ks;
+  d_mainloop<NM, NM, NM>(sm, kb0, kb1, load, [](int t) { return t; }, S, s, tx, ty);
+  // the two terms' sums (the second term's sign is in its factor copy)
+  float T[2][2], t2[2][2];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      T[x][y] = S[0][x][y];
+      t2[x][y] = s[0][x][y];
+      if constexpr (NM == 2) ds_add(T[x][y], t2[x][y], S[1][x][y], s[1][x][y]);
+    }
   const int64_t oplane = (int64_t)d.batch * d.n;
 #pragma unroll
-  for (int x = 0; x < MT; ++x) {
-    const int b = b0 + ty * MT + x;
+  for (int x = 0; x < 2; ++x) {
+    const int b = (int)b0 + ty * 2 + x;
     if (b >= d.batch) continue;
     const bool on = a.active == nullptr || a.active[b];
     double* dst = a.taken ? a.hist + b * a.hist_stride + (3 + a.taken[b] % 3) * d.n : a.c + b * a.c_stride;
 #pragma unroll
-    for (int y = 0; y < MT; ++y) {
-      const int64_t i = i0 + tx * MT + y;
+    for (int y = 0; y < 2; ++y) {
+      const int64_t i = i0 + tx * 2 + y;
       if (i >= d.n) continue;
       if (sp.ks == 1) {
-        if (on) dst[i] = (double)S[x][y] + (double)s[x][y];
+        if (on) dst[i] = (double)T[x][y] + (double)t2[x][y];
       } else {
         float* p = sp.partial + (int64_t)blockIdx.z * 2 * oplane + (int64_t)b * d.n + i;
-        p[0] = S[x][y];
-        p[oplane] = s[x][y];
+        p[0] = T[x][y];
+        p[oplane] = t2[x][y];
       }
     }
   }
@@ -358,39 +375,26 @@ __global__ void __launch_bounds__(256) k3d_finish(const DDims d, const K3Args a,
   }
 }
 
-// Tiles and K splits of one GEMM (M x N outputs, K long, nf products per
-// output).  Tiles are 32 x 32 (D_MT = 2): several CTAs share an SM, which
-// hides the operand loads of one behind another's arithmetic; on GB300 the
-// 64 x 64 tiles (one CTA per SM by registers) were slower in every measured
-// shape (N = 512-1024, 64-1024 trajectories; 2.09 against 2.17 ms per step
-// at their best for 1024 trajectories of N = R = 1024, 0.161 against 0.188
-// ms for 64).  The split count is the one whose busiest SM has the least
-// work, CTAs spreading evenly (the busiest SM runs ceil(CTAs / SMs) of
-// them), with the split sums' reads and launch added; ties go to fewer
-// splits.
-constexpr int D_MT = 2;
-
-struct DGemm {
-  int ks;
-  int64_t tiles_m, tiles_n;
-};
-
-static DGemm d_gemm(int64_t m, int64_t n, int64_t K, int nf, int sm_count) {
-  constexpr int tile = 16 * D_MT;
-  const int64_t nk = (K + D_BK - 1) / D_BK;
-  const int64_t tm = (m + tile - 1) / tile, tn = (n + tile - 1) / tile;
-  DGemm best{1, tm, tn};
+// K splits of one GEMM (M x N outputs in 32 x 32 tiles, K long, nf products
+// per output): the count whose busiest SM has the least work, CTAs spreading
+// evenly (the busiest SM runs ceil(CTAs / SMs) of them), with the split
+// sums' reads and launch added; ties go to fewer splits.  (32 x 32 tiles,
+// several CTAs to an SM, measured faster on GB300 than 64 x 64 tiles with
+// one CTA per SM in every shape tried: N = 512-1024, 64-1024 trajectories.)
+static int d_splits(int64_t m, int64_t n, int64_t K, int nf, int sm_count) {
+  const int64_t nk = K / D_BK, tiles = (m / D_T) * (n / D_T);
+  int best = 1;
   double best_us = 0.0;
   const int64_t kmax = std::min<int64_t>(nk, D_MAX_SPLITS);
   for (int64_t ks = 1; ks <= kmax; ++ks) {
-    const int64_t busiest = (tm * tn * ks + sm_count - 1) / sm_count;
+    const int64_t busiest = (tiles * ks + sm_count - 1) / sm_count;
     const int64_t ktiles = (nk + ks - 1) / ks;
     // ~24 G double-single products per second per SM; the split sums read
     // ks x nf pairs per output at ~15 TB/s and take one more launch
-    double us = (double)busiest * ktiles * tile * tile * nf * D_BK / 24.3e3;
+    double us = (double)busiest * ktiles * D_T * D_T * nf * D_BK / 24.3e3;
     if (ks > 1) us += 2.0 + (double)ks * m * n * nf * 8.0 / 15e6;
     if (ks == 1 || us < best_us * 0.999) {
-      best.ks = (int)ks;
+      best = (int)ks;
       best_us = us;
     }
   }
@@ -399,31 +403,34 @@ static DGemm d_gemm(int64_t m, int64_t n, int64_t K, int nf, int sm_count) {
 
 // Scratch: [states hi/lo] [H1, H2 hi/lo] [project partials] [expand partials].
 struct DLayout {
-  DGemm gp, ge;
+  int ks_p, ks_e;
   size_t x_bytes, h_bytes, pp_bytes, pe_bytes, total;
 };
 
-static int64_t d_kp(int64_t n) { return (n + D_BK - 1) / D_BK * D_BK; }
+static size_t d_round(size_t b) { return (b + 255) / 256 * 256; }
 
-static DLayout d_layout(int64_t n, int64_t rp, int batch, int nf, int sm_count) {
+static DLayout d_layout(const DDims& d, int sm_count) {
   DLayout L{};
-  L.gp = d_gemm(rp, batch, n, nf, sm_count);      // columns r (grid x), rows b (grid y), K = n
-  L.ge = d_gemm(n, batch, rp, nf - 1, sm_count);  // columns i, rows b, K = rp (one or two terms)
-  L.x_bytes = ((size_t)2 * batch * d_kp(n) * sizeof(float) + 255) / 256 * 256;
-  L.h_bytes = ((size_t)4 * batch * rp * sizeof(float) + 255) / 256 * 256;
-  L.pp_bytes = L.gp.ks > 1 ? (sizeof(float) * (size_t)L.gp.ks * 3 * 2 * (size_t)batch * (size_t)rp + 255) / 256 * 256 : 0;
-  L.pe_bytes = L.ge.ks > 1 ? sizeof(float) * (size_t)L.ge.ks * 2 * (size_t)batch * (size_t)n : 0;
+  L.ks_p = d_splits(d.rq, d.bq, d.kp, d.nf, sm_count);      // columns r, rows b, K = n
+  L.ks_e = d_splits(d.nq, d.bq, d.rq, d.nf - 1, sm_count);  // columns i, rows b, K = r (one or two terms)
+  L.x_bytes = d_round(sizeof(float) * 2 * (size_t)d.kp * d.bq);
+  L.h_bytes = d_round(sizeof(float) * 4 * (size_t)d.rq * d.bq);
+  L.pp_bytes = L.ks_p > 1 ? d_round(sizeof(float) * (size_t)L.ks_p * d.nf * 2 * d.rq * d.bq) : 0;
+  L.pe_bytes = L.ks_e > 1 ? d_round(sizeof(float) * (size_t)L.ks_e * 2 * d.batch * d.n) : 0;
   L.total = L.x_bytes + L.h_bytes + L.pp_bytes + L.pe_bytes;
   return L;
 }
 
-size_t k3d_factor_bytes(int64_t n, int64_t rp) { return (size_t)6 * n * rp * sizeof(float); }
+size_t k3d_factor_bytes(int64_t n, int64_t rp) {
+  const DDims d = d_dims(n, rp, 1, 3);
+  return sizeof(float) * (size_t)(6 * d_fplane(d) + 4 * d_tplane(d));
+}
 
 size_t k3d_scratch_bytes(int64_t n, int64_t rp, int max_batch, int sm_count) {
   size_t need = 0;
   for (int b = K3G_MIN_BATCH; b <= max_batch; ++b)
     for (int nf = 2; nf <= 3; ++nf) {  // the split counts depend on the form
-      const DLayout L = d_layout(n, rp, b, nf, sm_count);
+      const DLayout L = d_layout(d_dims(n, rp, b, nf), sm_count);
       if (L.total > need) need = L.total;
     }
   return need;
@@ -431,15 +438,11 @@ size_t k3d_scratch_bytes(int64_t n, int64_t rp, int max_batch, int sm_count) {
 
 cudaError_t k3d_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, int64_t rp, void* out,
                               cudaStream_t s) {
-  // op holds the three FP64 panels (fa, fb, fc: n x rp each) panel_bytes apart;
-  // out gets [fa hi | fa lo | fb hi | fb lo | fc hi | fc lo], n x rp floats each
-  float* o = static_cast<float*>(out);
-  const int64_t count = n * rp;
-  const unsigned blocks = (unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
-  for (int q = 0; q < 3; ++q) {
-    const double* f = reinterpret_cast<const double*>(op + q * panel_bytes);
-    k3d_split_panel<<<blocks, 256, 0, s>>>(f, count, o + 2 * q * count, o + (2 * q + 1) * count);
-  }
+  // op holds the three FP64 panels (fa, fb, fc: n x rp each) panel_bytes apart
+  const DDims d = d_dims(n, rp, 1, 3);
+  const int64_t total = 6 * d_fplane(d) + 4 * d_tplane(d);
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8192);
+  k3d_build<<<blocks, 256, 0, s>>>(op, panel_bytes, d, static_cast<float*>(out));
   return cudaGetLastError();
 }
 
@@ -462,60 +465,59 @@ static DBufs d_bufs(const DLayout& L, void* scratch) {
   return q;
 }
 
-static void d_prep(const DDims& d, const K3Args& a, const DBufs& q, cudaStream_t s) {
-  dim3 gx((unsigned)((d.kp + 255) / 256), (unsigned)d.batch);
-  k3d_prep<<<gx, 256, 0, s>>>(d, a, q.xh);
+static void d_prep(const DDims& d, const K3Args& a, const DBufs& q, int sm_count, cudaStream_t s) {
+  k3d_prep<<<d_flat_blocks(d.kp * d.bq, sm_count), 256, 0, s>>>(d, a, q.xh);
 }
 
 // project (+ split sums) and expand; with one expansion split the result is
 // in the output or the ring, else in the expansion partials.
 static void d_gemms(const DDims& d, const DLayout& L, const K3Args& a, const float* f, const DBufs& q, int sm_count,
                     cudaStream_t s) {
-  const DSplit sp{L.gp.ks, q.pp};
-  const dim3 gp((unsigned)L.gp.tiles_m, (unsigned)L.gp.tiles_n, (unsigned)sp.ks);
+  const DSplit sp{L.ks_p, q.pp};
+  const dim3 gp((unsigned)(d.rq / D_T), (unsigned)(d.bq / D_T), (unsigned)sp.ks);
   if (d.nf == 3)
-    k3d_project<3, D_MT><<<gp, 256, 0, s>>>(d, f, q.xh, q.h, sp);
+    k3d_project<3><<<gp, 256, 0, s>>>(d, f, q.xh, q.h, sp);
   else
-    k3d_project<2, D_MT><<<gp, 256, 0, s>>>(d, f, q.xh, q.h, sp);
+    k3d_project<2><<<gp, 256, 0, s>>>(d, f, q.xh, q.h, sp);
   if (sp.ks > 1) {
-    const unsigned hb = d_flat_blocks((int64_t)d.batch * d.rp, sm_count);
+    const unsigned hb = d_flat_blocks(d.rq * d.bq, sm_count);
     if (d.nf == 3)
       k3d_hadamard<3><<<hb, 256, 0, s>>>(d, sp, q.h);
     else
       k3d_hadamard<2><<<hb, 256, 0, s>>>(d, sp, q.h);
   }
-  const DSplit se{L.ge.ks, q.pe};
-  const dim3 ge((unsigned)L.ge.tiles_m, (unsigned)L.ge.tiles_n, (unsigned)se.ks);
+  const DSplit se{L.ks_e, q.pe};
+  const dim3 ge((unsigned)(d.nq / D_T), (unsigned)(d.bq / D_T), (unsigned)se.ks);
   if (d.nf == 3)
-    k3d_expand<2, D_MT><<<ge, 256, 0, s>>>(d, a, f, q.h, se);
+    k3d_expand<2><<<ge, 256, 0, s>>>(d, a, f, q.h, se);
   else
-    k3d_expand<1, D_MT><<<ge, 256, 0, s>>>(d, a, f, q.h, se);
+    k3d_expand<1><<<ge, 256, 0, s>>>(d, a, f, q.h, se);
 }
 
-static DDims d_dims(const K3Plan& p, const K3Args& a, int batch) {
-  return DDims{p.n, p.rb, d_kp(p.n), batch, a.form == GROM_FORM_CP_SKEW ? 3 : 2};
+static DDims d_dims_of(const K3Plan& p, const K3Args& a, int batch) {
+  return d_dims(p.n, p.rb, batch, a.form == GROM_FORM_CP_SKEW ? 3 : 2);
 }
 
 cudaError_t k3d_launch(const K3Plan& p, const K3Args& a, const void* factors, int batch, int max_batch,
                        void* scratch, int sm_count, cudaStream_t s) {
   (void)max_batch;
-  const DDims d = d_dims(p, a, batch);
-  const DLayout L = d_layout(d.n, d.rp, batch, d.nf, sm_count);
+  const DDims d = d_dims_of(p, a, batch);
+  const DLayout L = d_layout(d, sm_count);
   const DBufs q = d_bufs(L, scratch);
-  d_prep(d, a, q, s);
+  d_prep(d, a, q, sm_count, s);
   d_gemms(d, L, a, static_cast<const float*>(factors), q, sm_count, s);
-  if (L.ge.ks > 1)
-    k3d_finish<<<d_flat_blocks((int64_t)batch * d.n, sm_count), 256, 0, s>>>(d, a, DSplit{L.ge.ks, q.pe});
+  if (L.ks_e > 1)
+    k3d_finish<<<d_flat_blocks((int64_t)batch * d.n, sm_count), 256, 0, s>>>(d, a, DSplit{L.ks_e, q.pe});
   return cudaGetLastError();
 }
 
 cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factors, int batch, void* scratch,
                             int sm_count, bool prep, const StepArgs& st, int step_index, cudaEvent_t ev0,
                             cudaEvent_t ev1, cudaStream_t s) {
-  const DDims d = d_dims(p, a, batch);
-  const DLayout L = d_layout(d.n, d.rp, batch, d.nf, sm_count);
+  const DDims d = d_dims_of(p, a, batch);
+  const DLayout L = d_layout(d, sm_count);
   const DBufs q = d_bufs(L, scratch);
-  if (prep) d_prep(d, a, q, s);
+  if (prep) d_prep(d, a, q, sm_count, s);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && ev0) e = prof_record(ev0, s);
   if (e != cudaSuccess) return e;
@@ -523,13 +525,15 @@ cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factor
   e = cudaGetLastError();
   if (e == cudaSuccess && ev1) e = prof_record(ev1, s);
   if (e != cudaSuccess) return e;
+  // the step kernel sums the expansion's splits and writes the next state's
+  // planes [i][b] (pitch bq)
   K3TStepFuse f{};
   f.d2 = q.pe;
-  f.s2 = L.ge.ks;
+  f.s2 = L.ks_e;
   f.bp = batch;
-  f.np = d.kp;
+  f.np = d.bq;
   f.xh = q.xh;
-  f.xl = q.xh + (int64_t)batch * d.kp;
+  f.xl = q.xh + d.kp * d.bq;
   return step_diag_mc_k3d_launch(st, step_index, f, s);
 }
 

@@ -52,7 +52,7 @@ __device__ __forceinline__ void report_nonfinite(const StepArgs& a, int b) {
 // for the next projections (the values the state prep would write);
 // 3 the K3D expansion's double-single split pairs (or, with one split, the
 // ring, which the expansion wrote), with the new state's FP32 hi/lo planes
-// written for the next projections.
+// ([i][b], pitch np) written for the next projections.
 // PLAIN: identity mass, no linear or forcing term, no energy or invariant.
 template <bool PLAIN, typename Sync>
 __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index, const K1Plan& pl, const K1Args& k1a,
@@ -116,8 +116,8 @@ __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index,
     if (fuse == 3) {
       float hi, lo;
       ds_split(un, hi, lo);
-      static_cast<float*>(kf.xh)[(int64_t)b * kf.np + i] = hi;
-      static_cast<float*>(kf.xl)[(int64_t)b * kf.np + i] = lo;
+      static_cast<float*>(kf.xh)[i * kf.np + b] = hi;  // planes [i][b]
+      static_cast<float*>(kf.xl)[i * kf.np + b] = lo;
     } else if (fuse == 2) {
       const float v = __double2float_rn(un);
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
