@@ -534,7 +534,12 @@ cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factor
   f.np = d.bq;
   f.xh = q.xh;
   f.xl = q.xh + d.kp * d.bq;
-  return step_diag_mc_k3d_launch(st, step_index, f, s);
+  if (f.s2 == 1) return step_diag_mc_k3d_launch(st, step_index, f, s);
+  // with split sums to load, one element per thread (more threads in flight)
+  StepArgs st1 = st;
+  st1.ept = 1;
+  st1.nblk = step_mc_blocks(d.n);
+  return step_diag_mc_k3d_launch(st1, step_index, f, s);
 }
 
 }  // namespace grom

@@ -79,9 +79,18 @@ __device__ __forceinline__ void step_mc_block(const StepArgs& a, int step_index,
       if (kf.s2 > 1) {
         const int64_t oplane = kf.bp * n;
         float S = 0.f, s = 0.f;
-        for (int q = 0; q < kf.s2; ++q) {
-          const float* p = kf.d2 + (int64_t)q * 2 * oplane + (int64_t)b * n + i;
-          ds_add(S, s, __ldcg(p), __ldcg(p + oplane));
+        for (int q0 = 0; q0 < kf.s2; q0 += 4) {  // four splits' loads in flight, summed in split order
+          float w[4][2];
+#pragma unroll
+          for (int z = 0; z < 4; ++z)
+            if (q0 + z < kf.s2) {
+              const float* p = kf.d2 + (int64_t)(q0 + z) * 2 * oplane + (int64_t)b * n + i;
+              w[z][0] = __ldcg(p);
+              w[z][1] = __ldcg(p + oplane);
+            }
+#pragma unroll
+          for (int z = 0; z < 4; ++z)
+            if (q0 + z < kf.s2) ds_add(S, s, w[z][0], w[z][1]);
         }
         nl = (double)S + (double)s;
         h[(3 + l % 3) * n + i] = nl;
