@@ -750,10 +750,13 @@ def main():
             brom = grom.Rom(n, "full", "bf16", tensor=C, stiffness=a, nu=NU, dt=DT, max_batch=B)
             U0 = synth.initial_condition(n, seed, 0, B)
             btr = grom.Trajectories(brom, U0)
-            btr.step(2)
-            torch.cuda.synchronize()
             bsteps = 10
+            # warm-up with timing on, so that the captured step graph (which
+            # carries the timing nodes) is built outside the timed region
             brom.profile(True)
+            btr.step(bsteps)
+            brom.profile_read()
+            torch.cuda.synchronize()
             e0b, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0b.record(stream)
             btr.step(bsteps)
@@ -789,9 +792,10 @@ def main():
             prom = grom.Rom(n, "full", "bf16", tensor=C, stiffness=a, nu=NU, dt=DT, max_batch=B,
                             layout="skew_packed")
             ptr = grom.Trajectories(prom, U0)
-            ptr.step(2)
-            torch.cuda.synchronize()
             prom.profile(True)
+            ptr.step(bsteps)
+            prom.profile_read()
+            torch.cuda.synchronize()
             e0b.record(stream)
             ptr.step(bsteps)
             e1b.record(stream)
@@ -837,7 +841,7 @@ def main():
                 crom = grom.Rom(n, "cp_skew", storage, factors=factors, stiffness=a, nu=NU, dt=DT, max_batch=B)
                 crom.set_kernel(kernel)
                 ctr = grom.Trajectories(crom, U0)
-                ctr.step(2)
+                ctr.step(bsteps)  # builds the captured step graph outside the timed region
                 torch.cuda.synchronize()
                 e0b.record(stream)
                 ctr.step(bsteps)
