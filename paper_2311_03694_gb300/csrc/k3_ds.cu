@@ -38,7 +38,7 @@
 
 #include "ds_arith.cuh"
 #include "grom_internal.h"
-#include "ptx.cuh"
+#include "cp_async.cuh"
 
 namespace grom {
 

@@ -300,10 +300,13 @@ __global__ void __launch_bounds__(256) k3g_expand(const GDims d, const K3Args a,
 }
 
 // K splits so that the grid covers about two waves of the GPU; each split
-// keeps at least 128 elements of the K range.
+// keeps at least 128 elements of the K range, or for short ranges one K
+// tile (up to 8 splits), so that a small problem (one output tile: 64
+// trajectories of an N = 128 ROM) spreads over several SMs instead of one.
 static int g_splits(int64_t tiles, int64_t K, int sm_count) {
   int64_t ks = (2 * sm_count + tiles - 1) / tiles;
-  const int64_t kmax = K / 128;
+  const int64_t kshort = K / G_BK < 8 ? K / G_BK : 8;
+  const int64_t kmax = K / 128 > kshort ? K / 128 : kshort;
   if (ks > kmax) ks = kmax;
   if (ks < 1) ks = 1;
   return (int)ks;
