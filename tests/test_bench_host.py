@@ -37,7 +37,7 @@ def test_every_traffic_entry_names_existing_sources_and_profile():
         assert len(e["source_sha256"]) == 64
 
 
-@pytest.mark.parametrize("key", ["k1_packed_bf16_n1024", "k1pp_bf16_n1024"])
+@pytest.mark.parametrize("key", ["k1pp_f32x2_n1024", "k1pp_bf16_n1024"])
 def test_traffic_is_dropped_once_a_source_changes(key, tmp_path, monkeypatch):
     e = _copy_tree_for(key, tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -51,6 +51,12 @@ def test_traffic_is_dropped_once_a_source_changes(key, tmp_path, monkeypatch):
     last.write_bytes(last.read_bytes() + b"\n")
     assert bench.kernel_traffic(key) is None
     assert bench.kernel_traffic("no_such_kernel") is None
+
+
+def test_headline_traffic_matches_the_current_sources():
+    # the bench line's traffic of its default workload (the F32X2 persistent
+    # stepper at N = 1024) describes the kernel as it is now
+    assert bench.kernel_traffic("k1pp_f32x2_n1024") is not None
 
 
 def test_traffic_absent_without_summary(tmp_path, monkeypatch):
