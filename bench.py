@@ -68,6 +68,7 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=10000, help="serving-mix requests (0 to skip)")
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-slots", type=int, default=64)
+    p.add_argument("--serve-quantum", type=int, default=16, help="steps a pool runs between scheduling decisions")
     p.add_argument("--json-out", default="")
     p.add_argument("--svd-ranks", default="64,256", help="SVD-ROM variant ranks ('none' to skip)")
     p.add_argument("--als-ranks", default="128,512", help="CP fitting (ALS, ALS-skew) ranks ('none' to skip)")
@@ -303,7 +304,7 @@ def serving_section(args, grom, synth, torch, a_of):
     seed = synth.seed_for(4)
     ns = [128, 256, 512, 1024]
     roms, keys, streams, fulls = [], [], [], {}
-    srv = grom.Server(150 * 2 ** 30, quantum=16)
+    srv = grom.Server(150 * 2 ** 30, quantum=args.serve_quantum)
     for n in ns:
         U, V, W, resid, _ = synth.cp_workload(n, n, 4)
         a = a_of(n)
@@ -327,7 +328,7 @@ def serving_section(args, grom, synth, torch, a_of):
     lat = out["t_done"] - times
     stats = out["stats"]
     res = {"requests": int(len(models)), "rate_per_s": args.serve_rate, "slots_per_rom": args.serve_slots,
-           "roms": len(roms), "quantum_steps": 16, "hbm_budget_gb": 150,
+           "roms": len(roms), "quantum_steps": args.serve_quantum, "hbm_budget_gb": 150,
            "status_ok": int(np.sum(out["status"] == 0)),
            "trajectory_steps": int(stats["trajectory_steps"]), "seconds": stats["seconds"],
            "steps_per_s": stats["trajectory_steps"] / stats["seconds"],
