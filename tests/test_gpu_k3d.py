@@ -117,3 +117,32 @@ def test_k3d_fused_step_bitwise(form, steps):
     for t in (t1, t2, t3):
         t.close()
     rom.close()
+
+
+@pytest.mark.parametrize("batch", [16, 70])
+def test_k3d_stepping_energy_invariant(batch):
+    # the fused step with energy and invariant asked for (the step kernel's
+    # full variant summing the expansion splits) against the oracle stepper
+    grom.build()
+    n, r, steps = 150, 100, 23
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    a = synth.diag_stiffness(n)
+    U0 = synth.initial_condition(n, seed, 0, batch)
+    rom = grom.Rom(n, "cp_skew", "f64", factors=(U, V, W), stiffness=a, nu=1e-2, dt=1e-3, max_batch=batch)
+    tr = grom.Trajectories(rom, U0)
+    energy = torch.empty((steps, batch), dtype=torch.float64, device="cuda")
+    inv = torch.empty((steps, batch), dtype=torch.float64, device="cuda")
+    tr.step(steps, energy, inv)
+    assert tr.status()[0] == 0
+    H = tr.get_state()
+    for b in (0, batch // 2, batch - 1):
+        ref = oracle.Rom("cp_skew", n, a, 1e-2, 1e-3, factors=(U, V, W))
+        h = ref.initial_history(U0[b])
+        e_ref, _ = ref.step(h, steps, want_energy=True, want_invariant=True)
+        assert _rel(H[b][:n], h[:n]) <= 1e-11, b
+        assert H[b][6 * n] == steps
+        np.testing.assert_allclose(energy.cpu().numpy()[:, b], e_ref, rtol=1e-12)
+        # the skew CP structure conserves u^T c(u) = 0 to rounding
+        assert np.max(np.abs(inv.cpu().numpy()[:, b])) <= 1e-9 * np.max(e_ref)
+    tr.close()
+    rom.close()
