@@ -839,7 +839,7 @@ def main():
             # factors on the tensor cores, FP64 factors in double-single FP32
             # arithmetic (K3D, FP64 tolerance) and, for reference, in FP64
             # arithmetic (K3g, GROM_KERNEL_STREAM)
-            for storage, kernel in (("bf16", "auto"), ("f64", "auto"), ("f64", "stream")):
+            for storage, kernel in (("bf16", "auto"), ("f64", "auto"), ("f64", "tensor"), ("f64", "stream")):
                 crom = grom.Rom(n, "cp_skew", storage, factors=factors, stiffness=a, nu=NU, dt=DT, max_batch=B)
                 crom.set_kernel(kernel)
                 ctr = grom.Trajectories(crom, U0)
@@ -851,11 +851,14 @@ def main():
                 torch.cuda.synchronize()
                 cms = e0b.elapsed_time(e1b) / bsteps
                 cflops = 2.0 * 5 * n * R * B  # p, q, s projections and two expansions
-                key = "B%d_cpd_%s%s" % (B, storage, "_fp64_gemm" if kernel == "stream" else "")
+                key = "B%d_cpd_%s%s" % (B, storage, {"stream": "_fp64_gemm", "tensor": "_tensor"}.get(kernel, ""))
                 entry = {
                     "ms_per_step": cms, "trajectory_steps_per_s": B * 1e3 / cms,
                     "alg_tflops": cflops / (cms * 1e-3) / 1e12,
                     "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
+                               else "k3o (tcgen05 GEMMs of 6-bit digit slices, FP64 tolerance)"
+                               if storage == "f64" and B >= 16 and (kernel == "tensor" or (
+                                   kernel == "auto" and n * R * B >= 2 ** 26))
                                else "k3d project/expand (double-single FP32 GEMMs, FP64 tolerance)"
                                if storage == "f64" and kernel == "auto" and B >= 16
                                else "k3g project/expand (register-tiled FP64 GEMMs)" if B >= 16

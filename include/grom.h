@@ -227,16 +227,21 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * BF16 storage and batches above 8 trajectories (full form) or of 16 and more
  * (CP forms), else the streaming (full) or SIMT (CP) kernels; an autotuning
  * entry for the batch's bucket (grom_autotune, grom_set_tuning) replaces that
- * rule.  FP64 CP ROMs step batches of 16 and more with K3D: the projections
- * and the expansion as double-single FP32 GEMMs (every operand a hi/lo FP32
- * pair, error-free products and sums) on hi/lo copies of the factors made at
- * create, at FP64 tolerance (per-evaluation error ~1e-13 against FP64) and
- * several times the FP64 GEMMs' speed on this part's FP32 pipe. */
+ * rule.  FP64 CP ROMs step batches of 16 and more at FP64 tolerance
+ * (per-evaluation error ~1e-13 against FP64) with K3D: the projections and
+ * the expansion as double-single FP32 GEMMs (every operand a hi/lo FP32 pair,
+ * error-free products and sums) on hi/lo copies of the factors made at
+ * create; from N R B >= 2^26 on (N modes, R rank, B trajectories), and with
+ * GROM_KERNEL_TENSOR, with K3O: every operand split into nine 6-bit integer
+ * digit slices, the slice products on the tcgen05 tensor cores (exact in
+ * FP32 for dot products of up to 4096 terms, so N and the expansion's 2R
+ * (skew) or R at most 4096) and the slice pairs summed in double-single
+ * arithmetic. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass, one
                                 launch per step (no persistent stepper); CP forms: the SIMT
                                 kernels (K3, K3g; FP64 factors in FP64 arithmetic, no K3D)    */
-#define GROM_KERNEL_TENSOR 2 /* BF16 storage only.  Dense layout, K2: tcgen05 GEMM over the
+#define GROM_KERNEL_TENSOR 2 /* BF16 storage (and FP64 CP forms, below).  Dense layout, K2: tcgen05 GEMM over the
                                 Khatri-Rao product of the states (Sec. 2.2, eq. Cu with the
                                 mode-1 matricisation).  Skew-packed layout, K2P: the factored
                                 form, one tcgen05 GEMM D_i = P_i^T U^T per test index i over
@@ -244,7 +249,9 @@ int64_t grom_rom_bytes(const grom_rom* rom);
                                 every stored pair (i, k); half the bytes and MMA work of K2.
                                 CP forms, K3T: the projections [B C]^T X (skew: [V W U]^T X)
                                 and the expansion A Z (skew: [U, -W] Z) of the batch as two
-                                tcgen05 GEMMs (Sec. 3.1, eq. tc_ap; Sec. 3.3)              */
+                                tcgen05 GEMMs (Sec. 3.1, eq. tc_ap; Sec. 3.3).  FP64 CP forms
+                                (batches of 16 and more): K3O, the same two GEMMs on digit
+                                slices of the factors and of the states (FP64 tolerance)     */
 grom_status grom_set_kernel(grom_rom* rom, int32_t kernel);
 
 /* ------------------------------------------------------------ autotuning

@@ -25,6 +25,7 @@ SOURCES = [
     "k3_cp.cu",
     "k3_gemm.cu",
     "k3_ds.cu",
+    "k3_oz.cu",
     "k3_persistent.cu",
     "k1_plan.cu",
     "k1_f64.cu",

@@ -216,7 +216,7 @@ static void rom_free(grom_rom* r) {
   if (!r) return;
   void* ptrs[] = {r->op,     r->hdiag,   r->hinv, r->mass, r->mass_diag, r->linear,
                   r->lin_diag, r->forcing, r->part, r->err,  r->k2_scratch, r->k3g_scratch, r->k3p_scratch,
-                  r->k3t_factors, r->k3t_scratch, r->k3d_factors, r->k3d_scratch,
+                  r->k3t_factors, r->k3t_scratch, r->k3d_factors, r->k3d_scratch, r->k3o_factors, r->k3o_scratch,
                   r->k1p_dg, r->k1p_tg, r->probe, r->svd_ut, r->svd_sigma, r->svd_beta, r->k1pp_scratch,
                   r->k2_tiles};
   for (void* p : ptrs)
@@ -288,6 +288,14 @@ static bool use_k3g(const grom_rom* r, int batch) {
 // GROM_KERNEL_STREAM keeps the FP64 GEMMs of K3g
 static bool use_k3d(const grom_rom* r, int batch) {
   return is_cp(r) && r->k3d_factors && batch >= K3G_MIN_BATCH && r->kernel_choice != GROM_KERNEL_STREAM;
+}
+
+// K3O: FP64 CP batches on the tensor cores (digit slices): GROM_KERNEL_TENSOR,
+// else from K3O_MIN_WORK (N R B) on, where it steps faster than K3D
+static bool use_k3o(const grom_rom* r, int batch) {
+  if (!is_cp(r) || !r->k3o_factors || batch < K3G_MIN_BATCH) return false;
+  if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
+  return r->kernel_choice == GROM_KERNEL_AUTO && (int64_t)r->n * r->rank * batch >= K3O_MIN_WORK;
 }
 
 // K3T: the batched CP form on the tensor cores (BF16 factors)
@@ -654,6 +662,17 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
       if (cudaMemsetAsync(r->k3d_scratch, 0, kd, r->stream) != cudaSuccess ||
           k3d_build_factors(r->op, r->panel_bytes, n, rp, r->k3d_factors, r->stream) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "grom_create: double-single factor copies"));
+      if (k3o_supported(n, r->rank, r->form)) {
+        // digit slices of the factors for the tensor-core path (K3O)
+        if ((st = dmalloc(&r->k3o_factors, k3o_factor_bytes(n, rp, r->rank, r->form), &r->total_bytes)))
+          return bail(st);
+        if ((st = dmalloc(&r->k3o_scratch, k3o_scratch_bytes(n, rp, r->rank, r->form, r->max_batch),
+                          &r->total_bytes)))
+          return bail(st);
+        if (k3o_build_factors(r->op, r->panel_bytes, n, rp, r->rank, r->form, r->k3o_factors, r->stream) !=
+            cudaSuccess)
+          return bail(cuda_fail(cudaGetLastError(), "grom_create: factor digit slices"));
+      }
     }
     if (r->storage == GROM_BF16) {
       // the factors again, laid out for the tensor-core GEMMs (K3T), and the
@@ -897,6 +916,8 @@ grom_status grom_nonlinear(grom_rom* r, int32_t batch, const double* u, double* 
     if (e0) prof_record(e0, r->stream);
     e = use_k3t(r, batch) ? k3t_launch(k3t_plan_of(r, batch), &r->k3t_tmap_ft,
                                        &r->k3t_tmap_ae, a, batch, r->k3t_scratch, r->err, r->stream)
+        : use_k3o(r, batch) ? k3o_launch(r->n, r->k3.rb, r->rank, a, r->k3o_factors, batch, r->k3o_scratch, r->err,
+                                         r->sm_count, r->stream)
         : use_k3d(r, batch) ? k3d_launch(r->k3, a, r->k3d_factors, batch, r->max_batch, r->k3d_scratch, r->sm_count,
                                          r->stream)
         : use_k3g(r, batch) ? k3g_launch(r->k3, r->storage, a, batch, r->max_batch, r->k3g_scratch, r->sm_count, r->stream)
@@ -1029,6 +1050,9 @@ static cudaError_t traj_nonlinear(grom_traj* t, cudaStream_t strm) {
   cudaError_t e = use_k3t(r, t->batch)
                       ? k3t_launch(k3t_plan_of(r, t->batch), &r->k3t_tmap_ft,
                                    &r->k3t_tmap_ae, a, t->batch, r->k3t_scratch, r->err, strm)
+                  : use_k3o(r, t->batch)
+                      ? k3o_launch(r->n, r->k3.rb, r->rank, a, r->k3o_factors, t->batch, r->k3o_scratch, r->err,
+                                   r->sm_count, strm)
                   : use_k3d(r, t->batch)
                       ? k3d_launch(r->k3, a, r->k3d_factors, t->batch, r->max_batch, r->k3d_scratch, r->sm_count, strm)
                   : use_k3g(r, t->batch)
@@ -1087,7 +1111,7 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   const bool fused_k1 = r->diagonal && !is_cp(r) && !use_k2(r, t->batch) && !use_k2p(r, t->batch);
   const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch) && !use_k3t(r, t->batch);
   const bool fused_k3t = r->diagonal && use_k3t(r, t->batch);
-  const bool fused_k3d = r->diagonal && use_k3d(r, t->batch);
+  const bool fused_k3d = r->diagonal && use_k3d(r, t->batch) && !use_k3o(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
     if (fused_k3d) {
@@ -1431,8 +1455,10 @@ grom_status grom_set_kernel(grom_rom* r, int32_t kernel) {
   if (kernel < GROM_KERNEL_AUTO || kernel > GROM_KERNEL_TENSOR)
     return fail(GROM_ERR_INVALID_ARG, "grom_set_kernel: unknown kernel");
   if (kernel == GROM_KERNEL_TENSOR && !(r->form == GROM_FORM_FULL && r->storage == GROM_BF16 && r->k2_ok) &&
-      !(is_cp(r) && r->k3t_factors))
-    return fail(GROM_ERR_UNSUPPORTED, "grom_set_kernel: the tensor-core kernels need BF16 storage (full or CP form)");
+      !(is_cp(r) && (r->k3t_factors || r->k3o_factors)))
+    return fail(GROM_ERR_UNSUPPORTED,
+                "grom_set_kernel: the tensor-core kernels need BF16 storage (full or CP form) or an FP64 CP ROM of "
+                "16 or more trajectories");
   if (kernel == GROM_KERNEL_TENSOR) {
     grom_status st = build_k2_tiles(r);
     if (st) return st;

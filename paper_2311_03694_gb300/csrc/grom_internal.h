@@ -188,6 +188,11 @@ size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int 
 cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
                        int sm_count, cudaStream_t s);
 constexpr int K3G_MIN_BATCH = 16;
+// AUTO steps FP64 CP batches on the tensor cores (K3O) from this much work
+// per step on (N R B; measured on GB300: N = R = 1024 at 64 trajectories
+// 0.130 against 0.143 ms for K3D, at 1024 trajectories 0.97 against 1.93 ms;
+// N = R = 512 at 64 trajectories 0.065 against 0.055 ms)
+constexpr int64_t K3O_MIN_WORK = (int64_t)1 << 26;
 // Batched CP form of FP64 ROMs at FP64 tolerance in double-single FP32
 // arithmetic (K3D, same batch sizes as K3g): hi/lo copies of the factors
 // made at create, then per step a state split and two GEMMs.
@@ -205,6 +210,18 @@ struct StepArgs;
 cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factors, int batch, void* scratch,
                             int sm_count, bool prep, const StepArgs& st, int step_index, cudaEvent_t ev0,
                             cudaEvent_t ev1, cudaStream_t s);
+// K3O: the batched CP form of FP64 ROMs on the BF16 tensor cores, every
+// operand split into 6-bit integer digit slices (Sec. 3.1, eq. tc_ap).
+bool k3o_supported(int64_t n, int64_t r, int form);
+size_t k3o_factor_bytes(int64_t n, int64_t rp, int64_t r, int form);
+size_t k3o_scratch_bytes(int64_t n, int64_t rp, int64_t r, int form, int max_batch);
+cudaError_t k3o_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, int64_t rp, int64_t r, int form,
+                              void* out, cudaStream_t s);
+cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
+                       void* scratch, int* err, int sm_count, cudaStream_t s);
+cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
+                            int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
+                            cudaStream_t s);
 // Batched CP form on the tensor cores (BF16 factors): projections and
 // expansion as two tcgen05 GEMMs over copies of the factors laid out for them.
 struct K3TPlan {
@@ -424,6 +441,8 @@ struct grom_rom {
   void* k3g_scratch = nullptr;       // batched CP: Hadamard products H1, H2
   void* k3d_factors = nullptr;       // batched FP64 CP in double-single arithmetic: hi/lo factor planes
   void* k3d_scratch = nullptr;       // its states, products and split partials
+  void* k3o_factors = nullptr;       // batched FP64 CP on sliced BF16 tensor cores: factor digits and scales
+  void* k3o_scratch = nullptr;       // its state and H digits and slice products
   void* k3t_factors = nullptr;       // batched CP on tensor cores: FT | AE (BF16)
   void* k3t_scratch = nullptr;
   CUtensorMap k3t_tmap_ft, k3t_tmap_ae;

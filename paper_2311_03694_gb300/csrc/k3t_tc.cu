@@ -267,6 +267,142 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
   }
 }
 
+// K3O (k3_oz.cu): D = A B^T for the sliced FP64 CP form, in 128 x 128
+// tiles.  A holds `slices` slices of mslice rows, B `slices` slices of
+// nslice rows (K-major BF16 integer digits); D[col][m] is stored raw (FP32,
+// exact: every product of two digits and every partial sum is an integer
+// below 2^24).  Only the tiles that hold a slice pair (p, q) of the kept
+// triangle p + q < slices are computed.  CTAs are persistent over tiles: the
+// producer streams the next tiles' K steps through the ring while the MMAs
+// fill one of two tensor-memory accumulators and the epilogue warps store
+// the other.  The B tile is two 64-row boxes in the ring's hi and lo slots,
+// one MMA of N = 128.
+struct K3OGemm {
+  int64_t M, K, mslice, nslice;
+  int slices, mtiles, ctiles, stages;
+  float* out;  // ncols x M
+  int* err;
+};
+constexpr int K3O_BT = 128;
+
+__device__ __forceinline__ bool k3o_tile(const K3OGemm& g, int tile, int& mt, int& ct) {
+  mt = tile % g.mtiles;
+  ct = tile / g.mtiles;
+  const int sp = (int)((int64_t)mt * 128 / g.mslice), sq = (int)((int64_t)ct * K3O_BT / g.nslice);
+  return sp + sq < g.slices;
+}
+
+__global__ void __launch_bounds__(K3T_THREADS, 1)
+    k3o_gemm(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b0,
+             const __grid_constant__ CUtensorMap tmap_b1, const K3OGemm g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * (K3T_A_BYTES + K3O_BT * 128));
+  const K3TRing R = k3t_ring(smem, bars, g.stages, 1, K3O_BT / 2);
+  uint64_t* accf = R.accum;  // accumulator b holds a finished tile (accf[0] is the ring's own barrier)
+  uint64_t* acce = accf + 2; // accumulator b has been stored
+  uint64_t* drain = acce + 2;  // every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t T = g.K / 64;
+  const int tiles = g.mtiles * g.ctiles;
+
+  if (threadIdx.x == 0) {
+    k3t_ring_init(R);  // full, empty and accf[0]
+    ptx::mbar_init(&accf[1], 1);
+    ptx::mbar_init(&acce[0], 4);  // the four epilogue warps
+    ptx::mbar_init(&acce[1], 4);
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_b0);
+    tc::prefetch_tmap(&tmap_b1);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, (uint32_t)(2 * K3O_BT));
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
+        int mt, ct;
+        if (!k3o_tile(g, tile, mt, ct)) continue;
+        k3t_produce(R, &tmap_a, &tmap_b0, &tmap_b1, 1, mt * 128, 0, ct * K3O_BT, 0, T, it, abort_flag, g.err);
+      }
+      k3t_drain(R, 0, it, g.err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(128, K3O_BT);
+      uint32_t it = 0;
+      int n = 0;  // tiles of this CTA so far
+      for (int tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
+        int mt, ct;
+        if (!k3o_tile(g, tile, mt, ct)) continue;
+        const int ab = n & 1;
+        if (n >= 2 && !ptx::mbar_wait(&acce[ab], (uint32_t)(((n >> 1) - 1) & 1), abort_flag)) {
+          k3t_abort(abort_flag, g.err);
+          break;
+        }
+        tc::fence_after_sync();
+        K3TRing Rb = R;
+        Rb.accum = &accf[ab];
+        k3t_mma(Rb, tmem + (uint32_t)(ab * K3O_BT), 1, 0, idesc, T, it, abort_flag, g.err);
+        ++n;
+      }
+      // the tensor memory is freed below only after every MMA has completed
+      tc::commit(drain);
+      if (!ptx::mbar_wait(drain, 0, nullptr)) atomicOr(g.err, DEV_ERR_TIMEOUT);
+    }
+  } else {
+    const int q = warp & 3;  // tensor-memory lanes 32q .. 32q + 31
+    int n = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      int mt, ct;
+      if (!k3o_tile(g, tile, mt, ct)) continue;
+      const int ab = n & 1;
+      const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(&accf[ab], (uint32_t)((n >> 1) & 1), abort_flag));
+      if (!got) {
+        if (lane == 0) k3t_abort(abort_flag, g.err);
+        break;
+      }
+      tc::fence_after_sync();
+      if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
+        const int64_t m = (int64_t)mt * 128 + 32 * q + lane;
+        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * K3O_BT);
+        float* dst = g.out + (int64_t)ct * K3O_BT * g.M + m;
+        for (int c0 = 0; c0 < K3O_BT; c0 += 16) {
+          uint32_t v[16];
+          tc::tmem_ld_32x32b_x16(acc + (uint32_t)c0, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) dst[(int64_t)(c0 + c) * g.M] = __uint_as_float(v[c]);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&acce[ab]);
+      ++n;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, (uint32_t)(2 * K3O_BT));
+  }
+}
+
 // Z[b][j] = P_j Q_j (and Z[b][rp + j] = P_j S_j) into BF16 hi/lo rows.
 __device__ __forceinline__ void k3t_store_z(const K3TProj& g, int64_t b, int64_t j, float p, float q, float s) {
   const float z1 = p * q;
@@ -897,6 +1033,40 @@ static cudaError_t k3t_gemm_launch(const K3TPlan& p, const CUtensorMap* ma, cons
   cudaError_t e = cudaFuncSetAttribute(k3t_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   k3t_gemm<<<(unsigned)(g.mtiles * g.ctiles * splits), K3T_THREADS, p.smem, s>>>(*ma, mh, ml, g);
+  return cudaGetLastError();
+}
+
+// D = A B^T of the sliced FP64 CP form; M, mslice multiples of 128, ncols and
+// nslice multiples of 64 with ncols a multiple of 128, K a multiple of 64.
+cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
+                            int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
+                            cudaStream_t s) {
+  if (M % 128 || mslice % 128 || ncols % K3O_BT || nslice % 64 || K % 64 || K <= 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb0, mb1;
+  const __nv_bfloat16* b1 = static_cast<const __nv_bfloat16*>(B) + 64 * K;  // rows 64 .. of every tile
+  if (!k3t_tmap(&ma, A, K, M, 128) || !k3t_tmap(&mb0, B, K, ncols, 64) || !k3t_tmap(&mb1, b1, K, ncols - 64, 64))
+    return cudaErrorInvalidValue;
+  K3OGemm g{};
+  g.M = M;
+  g.K = K;
+  g.mslice = mslice;
+  g.nslice = nslice;
+  g.slices = slices;
+  g.mtiles = (int)(M / 128);
+  g.ctiles = (int)(ncols / K3O_BT);
+  const int stage = K3T_A_BYTES + K3O_BT * 128;
+  int st = (int)((K3T_SMEM_MAX - 1024 - 256) / stage);
+  if (st > 6) st = 6;
+  g.stages = st;
+  g.out = out;
+  g.err = err;
+  // ring barriers, accf[2], acce[2], drain, the tensor-memory slot and the abort flag
+  const size_t smem = 1024 + (size_t)st * stage + (size_t)(2 * st + 5) * 8 + 16;
+  cudaError_t e = cudaFuncSetAttribute(k3o_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = g.mtiles * g.ctiles;
+  const int grid = tiles < sm_count ? tiles : sm_count;
+  k3o_gemm<<<(unsigned)grid, K3T_THREADS, smem, s>>>(ma, mb0, mb1, g);
   return cudaGetLastError();
 }
 
