@@ -51,7 +51,7 @@ struct ODims {
   int64_t me;        // expansion rows per slice: n rounded up to 128
   int64_t rk;        // expansion K: nt r rounded up to 64
   int64_t bq;        // columns per slice: the batch rounded up to 64
-  int64_t nc;        // GEMM columns: S bq rounded up to 128 (the rest unused)
+  int64_t nc;        // GEMM columns: S bq rounded up to the GEMM's tile width (the rest unused)
   int batch;
 };
 
@@ -68,6 +68,7 @@ static ODims oz_dims(int64_t n, int64_t rp, int64_t r, int form, int batch) {
   d.rk = oz_up(d.nt * r, 64);
   d.bq = oz_up(batch, 64);
   d.nc = oz_up(OZ_S * d.bq, 128);
+  if (d.nc >= 1024) d.nc = oz_up(d.nc, 256);  // the GEMM's 256-wide tiles
   d.batch = batch;
   return d;
 }
@@ -319,42 +320,43 @@ __device__ __forceinline__ void oz_scale_ds(float& S, float& s, int e) {
   s = __fmul_rn(s, f);
 }
 
-// One thread per (b, j), j fastest: P, Q (and S) of rank index j, then
-// H1 = P o Q (and H2 = P o S) as double-single pairs, and the bits of the
-// trajectory's largest |H hi|.
-__global__ void __launch_bounds__(256) k3o_combine_proj(const ODims d, const float* __restrict__ D1,
+// CTAs (64 rank indices j, trajectory b), one thread per (factor, j): the
+// factor's projection of j (P, Q or S) from D1; then, for each j, H1 = P o Q
+// (and H2 = P o S) as double-single pairs and the bits of the trajectory's
+// largest |H hi|.  (Three threads per output keep three times the loads in
+// flight of one thread per (b, j).)
+__global__ void __launch_bounds__(192) k3o_combine_proj(const ODims d, const float* __restrict__ D1,
                                                         const int* __restrict__ sproj, const int* __restrict__ tau,
                                                         float* Hh, float* Hl, unsigned int* hmax) {
-  const int64_t total = (int64_t)d.batch * d.r;
+  __shared__ float V[3][64][2];
+  const int f = threadIdx.x >> 6, jl = threadIdx.x & 63;
+  const int b = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.x * 64 + jl;
   const int64_t M = OZ_S * d.mp;
-  const int64_t hplane = (int64_t)d.bq * d.r;
-  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(o / d.r);
-    const int64_t j = o - (int64_t)b * d.r;
-    float V[3][2];
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      V[f][0] = V[f][1] = 0.f;
-      if (f < d.nf) {
-        const int64_t m = (int64_t)f * d.r + j;
-        oz_sum(D1, M, d.mp, d.bq, b, m, V[f][0], V[f][1]);
-        oz_scale_ds(V[f][0], V[f][1], sproj[m] + tau[b]);
-      }
-    }
-    float h, l;
-    ds_mul(V[0][0], V[0][1], V[1][0], V[1][1], h, l);
-    Hh[(int64_t)b * d.r + j] = h;
-    Hl[(int64_t)b * d.r + j] = l;
-    unsigned int hm = (unsigned int)__float_as_int(h) & 0x7fffffffu;
-    if (d.nt == 2) {
-      ds_mul(V[0][0], V[0][1], V[2][0], V[2][1], h, l);
-      Hh[hplane + (int64_t)b * d.r + j] = h;
-      Hl[hplane + (int64_t)b * d.r + j] = l;
-      const unsigned int h2 = (unsigned int)__float_as_int(h) & 0x7fffffffu;
-      hm = h2 > hm ? h2 : hm;
-    }
-    atomicMax(&hmax[b], hm);
+  if (f < d.nf && j < d.r) {
+    const int64_t m = (int64_t)f * d.r + j;
+    float S, s;
+    oz_sum(D1, M, d.mp, d.bq, b, m, S, s);
+    oz_scale_ds(S, s, sproj[m] + tau[b]);
+    V[f][jl][0] = S;
+    V[f][jl][1] = s;
   }
+  __syncthreads();
+  if (f != 0 || j >= d.r) return;
+  const int64_t hplane = (int64_t)d.bq * d.r;
+  float h, l;
+  ds_mul(V[0][jl][0], V[0][jl][1], V[1][jl][0], V[1][jl][1], h, l);
+  Hh[(int64_t)b * d.r + j] = h;
+  Hl[(int64_t)b * d.r + j] = l;
+  unsigned int hm = (unsigned int)__float_as_int(h) & 0x7fffffffu;
+  if (d.nt == 2) {
+    ds_mul(V[0][jl][0], V[0][jl][1], V[2][jl][0], V[2][jl][1], h, l);
+    Hh[hplane + (int64_t)b * d.r + j] = h;
+    Hl[hplane + (int64_t)b * d.r + j] = l;
+    const unsigned int h2 = (unsigned int)__float_as_int(h) & 0x7fffffffu;
+    hm = h2 > hm ? h2 : hm;
+  }
+  atomicMax(&hmax[b], hm);
 }
 
 // CTAs (b, chunk of 256), b < bq: the scale and digits of [H1 | H2] of
@@ -449,7 +451,7 @@ cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const 
   k3o_slice_states<<<dim3((unsigned)d.bq, (unsigned)((d.nk + 255) / 256)), 256, 0, s>>>(d, a, bst, tau, hmax);
   cudaError_t e = k3o_gemm_launch(fb + F.aproj, OZ_S * d.mp, d.mp, bst, d.nc, d.bq, d.nk, OZ_S, d1, err, sm_count, s);
   if (e != cudaSuccess) return e;
-  k3o_combine_proj<<<oz_flat_blocks((int64_t)batch * d.r, sm_count), 256, 0, s>>>(
+  k3o_combine_proj<<<dim3((unsigned)((d.r + 63) / 64), (unsigned)batch), 192, 0, s>>>(
       d, d1, reinterpret_cast<const int*>(fb + F.sproj), tau, hh, hl, hmax);
   k3o_slice_h<<<dim3((unsigned)d.bq, (unsigned)((d.rk + 255) / 256)), 256, 0, s>>>(d, a, hh, hl, hmax, bh, tau2);
   e = k3o_gemm_launch(fb + F.aexp, OZ_S * d.me, d.me, bh, d.nc, d.bq, d.rk, OZ_S, d2, err, sm_count, s);

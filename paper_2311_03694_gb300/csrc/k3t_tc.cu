@@ -276,29 +276,30 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
 // producer streams the next tiles' K steps through the ring while the MMAs
 // fill one of two tensor-memory accumulators and the epilogue warps store
 // the other.  The B tile is two 64-row boxes in the ring's hi and lo slots,
-// one MMA of N = 128.
+// one MMA of N = BT (128, or 256 for wide problems: half the state bytes per
+// product, which the L2 has to deliver to every SM).
 struct K3OGemm {
   int64_t M, K, mslice, nslice;
   int slices, mtiles, ctiles, stages;
   float* out;  // ncols x M
   int* err;
 };
-constexpr int K3O_BT = 128;
-
+template <int BT>
 __device__ __forceinline__ bool k3o_tile(const K3OGemm& g, int tile, int& mt, int& ct) {
   mt = tile % g.mtiles;
   ct = tile / g.mtiles;
-  const int sp = (int)((int64_t)mt * 128 / g.mslice), sq = (int)((int64_t)ct * K3O_BT / g.nslice);
+  const int sp = (int)((int64_t)mt * 128 / g.mslice), sq = (int)((int64_t)ct * BT / g.nslice);
   return sp + sq < g.slices;
 }
 
+template <int BT>
 __global__ void __launch_bounds__(K3T_THREADS, 1)
     k3o_gemm(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b0,
              const __grid_constant__ CUtensorMap tmap_b1, const K3OGemm g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * (K3T_A_BYTES + K3O_BT * 128));
-  const K3TRing R = k3t_ring(smem, bars, g.stages, 1, K3O_BT / 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)g.stages * (K3T_A_BYTES + BT * 128));
+  const K3TRing R = k3t_ring(smem, bars, g.stages, 1, BT / 2);
   uint64_t* accf = R.accum;  // accumulator b holds a finished tile (accf[0] is the ring's own barrier)
   uint64_t* acce = accf + 2; // accumulator b has been stored
   uint64_t* drain = acce + 2;  // every issued MMA has completed
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
     tc::prefetch_tmap(&tmap_b1);
   }
   if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, (uint32_t)(2 * K3O_BT));
+    tc::tmem_alloc(tmem_slot, (uint32_t)(2 * BT));
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -336,19 +337,19 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
       uint32_t it = 0;
       for (int tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
         int mt, ct;
-        if (!k3o_tile(g, tile, mt, ct)) continue;
-        k3t_produce(R, &tmap_a, &tmap_b0, &tmap_b1, 1, mt * 128, 0, ct * K3O_BT, 0, T, it, abort_flag, g.err);
+        if (!k3o_tile<BT>(g, tile, mt, ct)) continue;
+        k3t_produce(R, &tmap_a, &tmap_b0, &tmap_b1, 1, mt * 128, 0, ct * BT, 0, T, it, abort_flag, g.err);
       }
       k3t_drain(R, 0, it, g.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_bf16_f32(128, K3O_BT);
+      const uint32_t idesc = tc::idesc_bf16_f32(128, BT);
       uint32_t it = 0;
       int n = 0;  // tiles of this CTA so far
       for (int tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
         int mt, ct;
-        if (!k3o_tile(g, tile, mt, ct)) continue;
+        if (!k3o_tile<BT>(g, tile, mt, ct)) continue;
         const int ab = n & 1;
         if (n >= 2 && !ptx::mbar_wait(&acce[ab], (uint32_t)(((n >> 1) - 1) & 1), abort_flag)) {
           k3t_abort(abort_flag, g.err);
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
         tc::fence_after_sync();
         K3TRing Rb = R;
         Rb.accum = &accf[ab];
-        k3t_mma(Rb, tmem + (uint32_t)(ab * K3O_BT), 1, 0, idesc, T, it, abort_flag, g.err);
+        k3t_mma(Rb, tmem + (uint32_t)(ab * BT), 1, 0, idesc, T, it, abort_flag, g.err);
         ++n;
       }
       // the tensor memory is freed below only after every MMA has completed
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
     int n = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
       int mt, ct;
-      if (!k3o_tile(g, tile, mt, ct)) continue;
+      if (!k3o_tile<BT>(g, tile, mt, ct)) continue;
       const int ab = n & 1;
       const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(&accf[ab], (uint32_t)((n >> 1) & 1), abort_flag));
       if (!got) {
@@ -379,9 +380,9 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
       tc::fence_after_sync();
       if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
         const int64_t m = (int64_t)mt * 128 + 32 * q + lane;
-        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * K3O_BT);
-        float* dst = g.out + (int64_t)ct * K3O_BT * g.M + m;
-        for (int c0 = 0; c0 < K3O_BT; c0 += 16) {
+        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * BT);
+        float* dst = g.out + (int64_t)ct * BT * g.M + m;
+        for (int c0 = 0; c0 < BT; c0 += 16) {
           uint32_t v[16];
           tc::tmem_ld_32x32b_x16(acc + (uint32_t)c0, v);
           tc::tmem_ld_wait();
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(K3T_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, (uint32_t)(2 * K3O_BT));
+    tc::tmem_dealloc(tmem, (uint32_t)(2 * BT));
   }
 }
 
@@ -1038,13 +1039,15 @@ static cudaError_t k3t_gemm_launch(const K3TPlan& p, const CUtensorMap* ma, cons
 
 // D = A B^T of the sliced FP64 CP form; M, mslice multiples of 128, ncols and
 // nslice multiples of 64 with ncols a multiple of 128, K a multiple of 64.
-cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
-                            int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
-                            cudaStream_t s) {
-  if (M % 128 || mslice % 128 || ncols % K3O_BT || nslice % 64 || K % 64 || K <= 0) return cudaErrorInvalidValue;
+template <int BT>
+static cudaError_t k3o_gemm_run(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
+                                int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
+                                cudaStream_t s) {
+  if (M % 128 || mslice % 128 || ncols % BT || nslice % 64 || K % 64 || K <= 0) return cudaErrorInvalidValue;
   CUtensorMap ma, mb0, mb1;
-  const __nv_bfloat16* b1 = static_cast<const __nv_bfloat16*>(B) + 64 * K;  // rows 64 .. of every tile
-  if (!k3t_tmap(&ma, A, K, M, 128) || !k3t_tmap(&mb0, B, K, ncols, 64) || !k3t_tmap(&mb1, b1, K, ncols - 64, 64))
+  const __nv_bfloat16* b1 = static_cast<const __nv_bfloat16*>(B) + (BT / 2) * K;  // the tile's second half
+  if (!k3t_tmap(&ma, A, K, M, 128) || !k3t_tmap(&mb0, B, K, ncols, BT / 2) ||
+      !k3t_tmap(&mb1, b1, K, ncols - BT / 2, BT / 2))
     return cudaErrorInvalidValue;
   K3OGemm g{};
   g.M = M;
@@ -1053,8 +1056,8 @@ cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void
   g.nslice = nslice;
   g.slices = slices;
   g.mtiles = (int)(M / 128);
-  g.ctiles = (int)(ncols / K3O_BT);
-  const int stage = K3T_A_BYTES + K3O_BT * 128;
+  g.ctiles = (int)(ncols / BT);
+  const int stage = K3T_A_BYTES + BT * 128;
   int st = (int)((K3T_SMEM_MAX - 1024 - 256) / stage);
   if (st > 6) st = 6;
   g.stages = st;
@@ -1062,12 +1065,20 @@ cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void
   g.err = err;
   // ring barriers, accf[2], acce[2], drain, the tensor-memory slot and the abort flag
   const size_t smem = 1024 + (size_t)st * stage + (size_t)(2 * st + 5) * 8 + 16;
-  cudaError_t e = cudaFuncSetAttribute(k3o_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k3o_gemm<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles = g.mtiles * g.ctiles;
   const int grid = tiles < sm_count ? tiles : sm_count;
-  k3o_gemm<<<(unsigned)grid, K3T_THREADS, smem, s>>>(ma, mb0, mb1, g);
+  k3o_gemm<BT><<<(unsigned)grid, K3T_THREADS, smem, s>>>(ma, mb0, mb1, g);
   return cudaGetLastError();
+}
+
+cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
+                            int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
+                            cudaStream_t s) {
+  if (ncols % 256 == 0 && ncols >= 1024)
+    return k3o_gemm_run<256>(A, M, mslice, B, ncols, nslice, K, slices, out, err, sm_count, s);
+  return k3o_gemm_run<128>(A, M, mslice, B, ncols, nslice, K, slices, out, err, sm_count, s);
 }
 
 // The pieces of the scratch for plan p.

@@ -58,9 +58,9 @@ def test_k3d_matches_oracle(form, n, r, batch):
 @pytest.mark.parametrize("form", ["cp_skew", "cp"])
 def test_k3d_n1024_rank_n(form):
     # the batched workload's size: N = R = 1024, several column tiles and K
-    # splits (32 trajectories: above that AUTO takes the tensor-core path, K3O)
+    # splits (16 trajectories: from 32 on AUTO takes the tensor-core path, K3O)
     grom.build()
-    n, batch = 1024, 32
+    n, batch = 1024, 16
     fac, ref = _factors(form, n, n, 5)
     U0 = synth.initial_condition(n, 3, 0, batch)
     rom = grom.Rom(n, form, "f64", factors=fac, stiffness=synth.diag_stiffness(n), max_batch=batch)
