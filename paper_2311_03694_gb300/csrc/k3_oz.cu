@@ -16,8 +16,11 @@
 // emulation of the whole evaluation on the workload's factors gives 5.1e-15
 // per evaluation against FP64 at N = R = 1024 (1.2e-12 with S = 8; with
 // 7-bit digits, 2.7e-15 at S = 8, but exactness then holds only for K <=
-// 1024).  The sums over slice pairs run in double-single FP32 arithmetic
-// (ds_arith.cuh) from the smallest weights up.
+// 1024).  The projections of ROMs of N <= 1024 (K = N) therefore use eight
+// 7-bit digits (36 slice pairs, exact; 2.7e-15 in the emulation), the
+// expansion (K = 2R or R, up to 4096) the nine 6-bit ones.  The sums over
+// slice pairs run in double-single FP32 arithmetic (ds_arith.cuh) from the
+// smallest weights up.
 //
 //   slice_states  per trajectory: the state's scale and digits        (B rows)
 //   gemm          D1 = [digits of V W U]^T x [digits of the states]   (tcgen05)
@@ -37,9 +40,12 @@
 
 namespace grom {
 
-constexpr int OZ_S = 9;     // slices per operand
-constexpr int OZ_BITS = 6;  // bits per digit
-constexpr int64_t OZ_MAX_K = 4096;  // longest exact dot product of digits
+constexpr int OZ_S = 9;     // slices per operand: 6-bit digits (exact for K <= 4096)
+constexpr int OZ_BITS = 6;
+constexpr int OZ_S7 = 8;    // projections of N <= 1024: 7-bit digits (exact for K <= 1024)
+constexpr int OZ_BITS7 = 7;
+constexpr int64_t OZ_MAX_K = 4096;  // longest exact dot product of 6-bit digits
+constexpr int64_t OZ_MAX_K7 = 1024; // of 7-bit digits
 
 static inline int64_t oz_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -51,7 +57,9 @@ struct ODims {
   int64_t me;        // expansion rows per slice: n rounded up to 128
   int64_t rk;        // expansion K: nt r rounded up to 64
   int64_t bq;        // columns per slice: the batch rounded up to 64
-  int64_t nc;        // GEMM columns: S bq rounded up to the GEMM's tile width (the rest unused)
+  int64_t nc;        // expansion GEMM columns: S bq rounded up to the GEMM's tile width (the rest unused)
+  int sp;            // projection slices: OZ_S7 (7-bit digits) when nk <= OZ_MAX_K7, else OZ_S
+  int64_t ncp;       // projection GEMM columns: sp bq rounded up likewise
   int batch;
 };
 
@@ -69,6 +77,9 @@ static ODims oz_dims(int64_t n, int64_t rp, int64_t r, int form, int batch) {
   d.bq = oz_up(batch, 64);
   d.nc = oz_up(OZ_S * d.bq, 128);
   if (d.nc >= 1024) d.nc = oz_up(d.nc, 256);  // the GEMM's 256-wide tiles
+  d.sp = d.nk <= OZ_MAX_K7 ? OZ_S7 : OZ_S;
+  d.ncp = oz_up((int64_t)d.sp * d.bq, 128);
+  if (d.ncp >= 1024) d.ncp = oz_up(d.ncp, 256);
   d.batch = batch;
   return d;
 }
@@ -84,7 +95,7 @@ struct OFactors {
 static OFactors oz_factor_layout(const ODims& d) {
   OFactors L{};
   L.aproj = 0;
-  L.aexp = oz_round(2 * (size_t)OZ_S * d.mp * d.nk);
+  L.aexp = oz_round(2 * (size_t)d.sp * d.mp * d.nk);
   L.sproj = L.aexp + oz_round(2 * (size_t)OZ_S * d.me * d.rk);
   L.sexp = L.sproj + oz_round(4 * (size_t)d.mp);
   L.total = L.sexp + oz_round(4 * (size_t)d.me);
@@ -103,11 +114,11 @@ static OScratch oz_scratch_layout(const ODims& d) {
   OScratch L{};
   size_t off = 0;
   L.bst = off;
-  off += oz_round(2 * (size_t)d.nc * d.nk);
+  off += oz_round(2 * (size_t)d.ncp * d.nk);
   L.tau = off;
   off += oz_round(4 * (size_t)d.bq);
   L.d1 = off;
-  off += oz_round(4 * (size_t)d.nc * OZ_S * d.mp);
+  off += oz_round(4 * (size_t)d.ncp * d.sp * d.mp);
   L.h = off;
   off += oz_round(4 * 2 * (size_t)d.nt * d.bq * d.r);
   L.hmax = off;
@@ -123,8 +134,8 @@ static OScratch oz_scratch_layout(const ODims& d) {
 }
 
 // Everything per element is integer arithmetic on the bit patterns: this
-// part's FP64 pipe is slow.  A value x with |x| < 2^e becomes the 54-bit
-// fixed-point integer Y = rint(x 2^(54 - e)) (|Y| <= 2^54), from its
+// part's FP64 pipe is slow.  A value x with |x| < 2^e becomes the F-bit
+// fixed-point integer Y = rint(x 2^(F - e)) (|Y| <= 2^F), from its
 // significand and exponent: significand m, x = m 2^(ex - bias - mbits).
 __device__ __forceinline__ long long oz_fix(long long m, int sh, bool neg) {
   long long Y;
@@ -136,26 +147,30 @@ __device__ __forceinline__ long long oz_fix(long long m, int sh, bool neg) {
     Y = 0;
   return neg ? -Y : Y;
 }
+// F = S BITS fixed-point bits (54 for 6-bit digits, 56 for 7-bit ones).
+template <int F>
 __device__ __forceinline__ long long oz_fix_d(double x, int e) {
   const long long B = __double_as_longlong(x);
   const int ex = (int)((B >> 52) & 0x7ff);
   if (ex == 0) return 0;  // zero or below 2^-1022: far below the last digit
-  return oz_fix((B & 0xfffffffffffffLL) | 0x10000000000000LL, ex - 1075 + 54 - e, B < 0);
+  return oz_fix((B & 0xfffffffffffffLL) | 0x10000000000000LL, ex - 1075 + F - e, B < 0);
 }
+template <int F>
 __device__ __forceinline__ long long oz_fix_f(float x, int e) {
   const int B = __float_as_int(x);
   const int ex = (B >> 23) & 0xff;
   if (ex == 0) return 0;
-  return oz_fix((long long)((B & 0x7fffff) | 0x800000), ex - 150 + 54 - e, B < 0);
+  return oz_fix((long long)((B & 0x7fffff) | 0x800000), ex - 150 + F - e, B < 0);
 }
 
-// The S digits of Y: balanced base-64 digits from the top, each the rounded
-// quotient of what the digits before it left (|d_0| <= 64, |d_p| <= 32
-// after); sum_p d_p 2^(6 (S - 1 - p)) = Y exactly.
-__device__ __forceinline__ void oz_digits(long long Y, __nv_bfloat16 (&dg)[OZ_S]) {
+// The S digits of Y: balanced base-2^BITS digits from the top, each the
+// rounded quotient of what the digits before it left (|d_0| <= 2^BITS,
+// |d_p| <= 2^(BITS-1) after); sum_p d_p 2^(BITS (S - 1 - p)) = Y exactly.
+template <int S, int BITS>
+__device__ __forceinline__ void oz_digits(long long Y, __nv_bfloat16 (&dg)[S]) {
 #pragma unroll
-  for (int p = 0; p < OZ_S; ++p) {
-    const int sh = OZ_BITS * (OZ_S - 1 - p);  // 48, 42, ..., 0
+  for (int p = 0; p < S; ++p) {
+    const int sh = BITS * (S - 1 - p);
     const long long d = sh ? (Y + (1LL << (sh - 1))) >> sh : Y;
     Y -= d << sh;
     dg[p] = __int2bfloat16_rn((int)d);
@@ -201,6 +216,7 @@ __device__ __forceinline__ unsigned long long oz_absbits(double x) {
 // ------------------------------------------------------------ factor data
 // Projection row m = f r + j (f: fb, fc, fa; j the rank index): the column j
 // of factor f over the modes k.  One CTA per row (padding rows: zeros).
+template <int S, int BITS>
 __global__ void __launch_bounds__(256) k3o_build_proj(const uint8_t* op, size_t panel_bytes, const ODims d,
                                                       __nv_bfloat16* aproj, int* sproj) {
   __shared__ unsigned long long sh[33];
@@ -219,10 +235,10 @@ __global__ void __launch_bounds__(256) k3o_build_proj(const uint8_t* op, size_t 
   const int e = oz_exp_d(oz_block_max(mx, sh));
   if (threadIdx.x == 0) sproj[m] = e;
   for (int64_t k = threadIdx.x; k < d.nk; k += blockDim.x) {
-    __nv_bfloat16 dg[OZ_S];
-    oz_digits(on && k < d.n ? oz_fix_d(F[k * d.rp + j], e) : 0, dg);
+    __nv_bfloat16 dg[S];
+    oz_digits<S, BITS>(on && k < d.n ? oz_fix_d<S * BITS>(F[k * d.rp + j], e) : 0, dg);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) aproj[((int64_t)p * d.mp + m) * d.nk + k] = dg[p];
+    for (int p = 0; p < S; ++p) aproj[((int64_t)p * d.mp + m) * d.nk + k] = dg[p];
   }
 }
 
@@ -249,7 +265,7 @@ __global__ void __launch_bounds__(256) k3o_build_exp(const uint8_t* op, size_t p
   if (threadIdx.x == 0) sexp[i] = e;
   for (int64_t k = threadIdx.x; k < d.rk; k += blockDim.x) {
     __nv_bfloat16 dg[OZ_S];
-    oz_digits(oz_fix_d(val(k), e), dg);
+    oz_digits<OZ_S, OZ_BITS>(oz_fix_d<OZ_S * OZ_BITS>(val(k), e), dg);
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) aexp[((int64_t)p * d.me + i) * d.rk + k] = dg[p];
   }
@@ -259,6 +275,7 @@ __global__ void __launch_bounds__(256) k3o_build_exp(const uint8_t* op, size_t p
 // CTAs (b, chunk of 256 modes), b < bq: the state's scale (each CTA of the
 // column finds it) and the chunk's digits (zeros for padding and inactive
 // trajectories); also clears the trajectory's largest |H|.
+template <int S, int BITS>
 __global__ void __launch_bounds__(256) k3o_slice_states(const ODims d, const K3Args a, __nv_bfloat16* bst, int* tau,
                                                         unsigned int* hmax) {
   __shared__ unsigned long long sh[33];
@@ -279,36 +296,35 @@ __global__ void __launch_bounds__(256) k3o_slice_states(const ODims d, const K3A
     hmax[b] = 0u;
   }
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    __nv_bfloat16 dg[OZ_S];
-    oz_digits(on && k < d.n ? oz_fix_d(u[k], e) : 0, dg);
+    __nv_bfloat16 dg[S];
+    oz_digits<S, BITS>(on && k < d.n ? oz_fix_d<S * BITS>(u[k], e) : 0, dg);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) bst[((int64_t)p * d.bq + b) * d.nk + k] = dg[p];
+    for (int p = 0; p < S; ++p) bst[((int64_t)p * d.bq + b) * d.nk + k] = dg[p];
   }
 }
 
-constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;
-
 // The triangle's slice pairs of one output, D[(q bq + b) M + p mrows + m]:
 // all loaded first (one round trip), each level L = p + q summed exactly in
-// integers (|sum| <= 9 2^24 < 2^31), then the levels, weighted 2^-6(L+2),
-// in double-single arithmetic from the smallest weight up.
+// integers (|sum| <= 9 2^24 < 2^31), then the levels, weighted
+// 2^-BITS(L+2), in double-single arithmetic from the smallest weight up.
+template <int NS, int BITS>
 __device__ __forceinline__ void oz_sum(const float* __restrict__ D, int64_t M, int64_t mrows, int64_t bq, int b,
                                        int64_t m, float& S, float& s) {
-  float v[OZ_PAIRS];
+  float v[NS * (NS + 1) / 2];
 #pragma unroll
-  for (int L = 0, x = 0; L < OZ_S; ++L)
+  for (int L = 0, x = 0; L < NS; ++L)
 #pragma unroll
     for (int p = 0; p <= L; ++p, ++x) v[x] = __ldcg(D + ((int64_t)(L - p) * bq + b) * M + (int64_t)p * mrows + m);
   S = 0.f;
   s = 0.f;
 #pragma unroll
-  for (int L = OZ_S - 1; L >= 0; --L) {
+  for (int L = NS - 1; L >= 0; --L) {
     int acc = 0;
 #pragma unroll
     for (int p = 0; p <= L; ++p) acc += __float2int_rn(v[L * (L + 1) / 2 + p]);
     const float hi = __int2float_rn(acc);
     const float lo = __int2float_rn(acc - __float2int_rz(hi));  // exact: |acc| < 2^31, |lo| <= 2^4
-    const float w = __int_as_float((127 - OZ_BITS * (L + 2)) << 23);  // 2^-6(L+2)
+    const float w = __int_as_float((127 - BITS * (L + 2)) << 23);  // 2^-BITS(L+2)
     ds_add(S, s, __fmul_rn(hi, w), __fmul_rn(lo, w));
   }
 }
@@ -325,6 +341,7 @@ __device__ __forceinline__ void oz_scale_ds(float& S, float& s, int e) {
 // (and H2 = P o S) as double-single pairs and the bits of the trajectory's
 // largest |H hi|.  (Three threads per output keep three times the loads in
 // flight of one thread per (b, j).)
+template <int S, int BITS>
 __global__ void __launch_bounds__(192) k3o_combine_proj(const ODims d, const float* __restrict__ D1,
                                                         const int* __restrict__ sproj, const int* __restrict__ tau,
                                                         float* Hh, float* Hl, unsigned int* hmax) {
@@ -332,14 +349,14 @@ __global__ void __launch_bounds__(192) k3o_combine_proj(const ODims d, const flo
   const int f = threadIdx.x >> 6, jl = threadIdx.x & 63;
   const int b = blockIdx.y;
   const int64_t j = (int64_t)blockIdx.x * 64 + jl;
-  const int64_t M = OZ_S * d.mp;
+  const int64_t M = S * d.mp;
   if (f < d.nf && j < d.r) {
     const int64_t m = (int64_t)f * d.r + j;
-    float S, s;
-    oz_sum(D1, M, d.mp, d.bq, b, m, S, s);
-    oz_scale_ds(S, s, sproj[m] + tau[b]);
-    V[f][jl][0] = S;
-    V[f][jl][1] = s;
+    float hi, lo;
+    oz_sum<S, BITS>(D1, M, d.mp, d.bq, b, m, hi, lo);
+    oz_scale_ds(hi, lo, sproj[m] + tau[b]);
+    V[f][jl][0] = hi;
+    V[f][jl][1] = lo;
   }
   __syncthreads();
   if (f != 0 || j >= d.r) return;
@@ -375,10 +392,10 @@ __global__ void __launch_bounds__(256) k3o_slice_h(const ODims d, const K3Args a
     if (on && k < (int64_t)d.nt * d.r) {
       const int t = (int)(k / d.r);
       const int64_t x = t * hplane + (int64_t)b * d.r + (k - (int64_t)t * d.r);
-      Y = oz_fix_f(Hh[x], e) + oz_fix_f(Hl[x], e);
+      Y = oz_fix_f<OZ_S * OZ_BITS>(Hh[x], e) + oz_fix_f<OZ_S * OZ_BITS>(Hl[x], e);
     }
     __nv_bfloat16 dg[OZ_S];
-    oz_digits(Y, dg);
+    oz_digits<OZ_S, OZ_BITS>(Y, dg);
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) bh[((int64_t)p * d.bq + b) * d.rk + k] = dg[p];
   }
@@ -394,7 +411,7 @@ __global__ void __launch_bounds__(256) k3o_combine_exp(const ODims d, const K3Ar
     const int64_t i = o - (int64_t)b * d.n;
     if (a.active && !a.active[b]) continue;
     float S, s;
-    oz_sum(D2, M, d.me, d.bq, b, i, S, s);
+    oz_sum<OZ_S, OZ_BITS>(D2, M, d.me, d.bq, b, i, S, s);
     oz_scale_ds(S, s, sexp[i] + tau2[b]);
     double* dst = a.taken ? a.hist + b * a.hist_stride + (3 + a.taken[b] % 3) * d.n : a.c + b * a.c_stride;
     dst[i] = (double)S + (double)s;
@@ -420,8 +437,12 @@ cudaError_t k3o_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, 
   const ODims d = oz_dims(n, rp, r, form, 1);
   const OFactors L = oz_factor_layout(d);
   uint8_t* base = static_cast<uint8_t*>(out);
-  k3o_build_proj<<<(unsigned)d.mp, 256, 0, s>>>(op, panel_bytes, d, reinterpret_cast<__nv_bfloat16*>(base + L.aproj),
-                                                reinterpret_cast<int*>(base + L.sproj));
+  auto* ap = reinterpret_cast<__nv_bfloat16*>(base + L.aproj);
+  auto* sp = reinterpret_cast<int*>(base + L.sproj);
+  if (d.sp == OZ_S7)
+    k3o_build_proj<OZ_S7, OZ_BITS7><<<(unsigned)d.mp, 256, 0, s>>>(op, panel_bytes, d, ap, sp);
+  else
+    k3o_build_proj<OZ_S, OZ_BITS><<<(unsigned)d.mp, 256, 0, s>>>(op, panel_bytes, d, ap, sp);
   k3o_build_exp<<<(unsigned)d.me, 256, 0, s>>>(op, panel_bytes, d, reinterpret_cast<__nv_bfloat16*>(base + L.aexp),
                                                reinterpret_cast<int*>(base + L.sexp));
   return cudaGetLastError();
@@ -448,11 +469,19 @@ cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const 
   auto* bh = reinterpret_cast<__nv_bfloat16*>(sb + L.bh);
   auto* tau2 = reinterpret_cast<int*>(sb + L.tau2);
   auto* d2 = reinterpret_cast<float*>(sb + L.d2);
-  k3o_slice_states<<<dim3((unsigned)d.bq, (unsigned)((d.nk + 255) / 256)), 256, 0, s>>>(d, a, bst, tau, hmax);
-  cudaError_t e = k3o_gemm_launch(fb + F.aproj, OZ_S * d.mp, d.mp, bst, d.nc, d.bq, d.nk, OZ_S, d1, err, sm_count, s);
+  const dim3 gs((unsigned)d.bq, (unsigned)((d.nk + 255) / 256)), gc((unsigned)((d.r + 63) / 64), (unsigned)batch);
+  const int* spj = reinterpret_cast<const int*>(fb + F.sproj);
+  if (d.sp == OZ_S7)
+    k3o_slice_states<OZ_S7, OZ_BITS7><<<gs, 256, 0, s>>>(d, a, bst, tau, hmax);
+  else
+    k3o_slice_states<OZ_S, OZ_BITS><<<gs, 256, 0, s>>>(d, a, bst, tau, hmax);
+  cudaError_t e = k3o_gemm_launch(fb + F.aproj, (int64_t)d.sp * d.mp, d.mp, bst, d.ncp, d.bq, d.nk, d.sp, d1, err,
+                                  sm_count, s);
   if (e != cudaSuccess) return e;
-  k3o_combine_proj<<<dim3((unsigned)((d.r + 63) / 64), (unsigned)batch), 192, 0, s>>>(
-      d, d1, reinterpret_cast<const int*>(fb + F.sproj), tau, hh, hl, hmax);
+  if (d.sp == OZ_S7)
+    k3o_combine_proj<OZ_S7, OZ_BITS7><<<gc, 192, 0, s>>>(d, d1, spj, tau, hh, hl, hmax);
+  else
+    k3o_combine_proj<OZ_S, OZ_BITS><<<gc, 192, 0, s>>>(d, d1, spj, tau, hh, hl, hmax);
   k3o_slice_h<<<dim3((unsigned)d.bq, (unsigned)((d.rk + 255) / 256)), 256, 0, s>>>(d, a, hh, hl, hmax, bh, tau2);
   e = k3o_gemm_launch(fb + F.aexp, OZ_S * d.me, d.me, bh, d.nc, d.bq, d.rk, OZ_S, d2, err, sm_count, s);
   if (e != cudaSuccess) return e;

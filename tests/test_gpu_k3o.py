@@ -93,3 +93,39 @@ def test_k3o_stepping_energy_invariant():
         assert np.max(np.abs(inv.cpu().numpy()[:, b])) <= 1e-9 * np.max(e_ref)
     tr.close()
     rom.close()
+
+
+def test_k3o_serving_alone_equals_mix():
+    # a serving pool on K3O: every trajectory's digits, slice products and
+    # sums depend on its own state only, so a request's result is bitwise
+    # the same alone and in the mix; and it matches the oracle stepper
+    grom.build()
+    n, r, slots = 96, 64, 20
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    a = synth.diag_stiffness(n)
+    rom = grom.Rom(n, "cp_skew", "f64", factors=(U, V, W), stiffness=a, nu=1e-2, dt=1e-3, max_batch=slots)
+    rom.set_kernel("tensor")
+    rng = np.random.default_rng(5)
+    count = 40
+    horizons = rng.integers(5, 60, count)
+    arrivals = np.sort(rng.random(count) * 0.01)
+    u0s = [synth.initial_condition(n, 300 + q)[0] for q in range(count)]
+    srv = grom.Server(150 * 2 ** 30, quantum=8)
+    mid = srv.add_rom(rom, slots)
+    out = srv.serve([mid] * count, horizons, arrivals, u0s, want_final=True)
+    assert np.all(out["status"] == 0), out["status"]
+    assert out["stats"]["peak_active"] > 1
+    srv.close()
+    alone = grom.Server(150 * 2 ** 30, quantum=8)
+    aid = alone.add_rom(rom, slots)
+    for q in range(0, count, 4):
+        one = alone.serve([aid], [horizons[q]], [0.0], [u0s[q]], want_final=True)
+        assert one["status"][0] == 0
+        np.testing.assert_array_equal(one["final"][0], out["final"][q], err_msg="request %d" % q)
+    alone.close()
+    for q in range(0, count, 8):
+        ref = oracle.Rom("cp_skew", n, a, 1e-2, 1e-3, factors=(U, V, W))
+        h = ref.initial_history(u0s[q])
+        ref.step(h, int(horizons[q]))
+        assert _rel(out["final"][q], h[:n]) <= 1e-11, q
+    rom.close()
