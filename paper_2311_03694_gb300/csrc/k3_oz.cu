@@ -76,10 +76,10 @@ static ODims oz_dims(int64_t n, int64_t rp, int64_t r, int form, int batch) {
   d.rk = oz_up(d.nt * r, 64);
   d.bq = oz_up(batch, 64);
   d.nc = oz_up(OZ_S * d.bq, 128);
-  if (d.nc >= 1024) d.nc = oz_up(d.nc, 256);  // the GEMM's 256-wide tiles
+  if (d.nc >= 512) d.nc = oz_up(d.nc, 256);  // the GEMM's 256-wide tiles
   d.sp = d.nk <= OZ_MAX_K7 ? OZ_S7 : OZ_S;
   d.ncp = oz_up((int64_t)d.sp * d.bq, 128);
-  if (d.ncp >= 1024) d.ncp = oz_up(d.ncp, 256);
+  if (d.ncp >= 512) d.ncp = oz_up(d.ncp, 256);
   d.batch = batch;
   return d;
 }

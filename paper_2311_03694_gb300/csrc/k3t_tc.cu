@@ -1076,7 +1076,7 @@ static cudaError_t k3o_gemm_run(const void* A, int64_t M, int64_t mslice, const 
 cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
                             int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
                             cudaStream_t s) {
-  if (ncols % 256 == 0 && ncols >= 1024)
+  if (ncols % 256 == 0 && ncols >= 512)
     return k3o_gemm_run<256>(A, M, mslice, B, ncols, nslice, K, slices, out, err, sm_count, s);
   return k3o_gemm_run<128>(A, M, mslice, B, ncols, nslice, K, slices, out, err, sm_count, s);
 }
