@@ -858,7 +858,7 @@ def main():
                     "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
                                else "k3o (tcgen05 GEMMs of 6-bit digit slices, FP64 tolerance)"
                                if storage == "f64" and B >= 16 and (kernel == "tensor" or (
-                                   kernel == "auto" and B >= 32 and n * R * B >= 2 ** 24))
+                                   kernel == "auto" and n * R * B >= 2 ** 24))
                                else "k3d project/expand (double-single FP32 GEMMs, FP64 tolerance)"
                                if storage == "f64" and kernel == "auto" and B >= 16
                                else "k3g project/expand (register-tiled FP64 GEMMs)" if B >= 16

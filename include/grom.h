@@ -231,8 +231,7 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * (per-evaluation error ~1e-13 against FP64) with K3D: the projections and
  * the expansion as double-single FP32 GEMMs (every operand a hi/lo FP32 pair,
  * error-free products and sums) on hi/lo copies of the factors made at
- * create; from 32 trajectories and N R B >= 2^24 on (N modes, R rank, B
- * trajectories), and with
+ * create; from N R B >= 2^24 on (N modes, R rank, B trajectories), and with
  * GROM_KERNEL_TENSOR, with K3O: every operand split into nine 6-bit integer
  * digit slices, the slice products on the tcgen05 tensor cores (exact in
  * FP32 for dot products of up to 4096 terms, so N and the expansion's 2R

@@ -291,12 +291,11 @@ static bool use_k3d(const grom_rom* r, int batch) {
 }
 
 // K3O: FP64 CP batches on the tensor cores (digit slices): GROM_KERNEL_TENSOR,
-// else from K3O_MIN_WORK (N R B) and K3O_MIN_BATCH on, where it steps faster than K3D
+// else from K3O_MIN_WORK (N R B) on, where it steps faster than K3D
 static bool use_k3o(const grom_rom* r, int batch) {
   if (!is_cp(r) || !r->k3o_factors || batch < K3G_MIN_BATCH) return false;
   if (r->kernel_choice == GROM_KERNEL_TENSOR) return true;
-  return r->kernel_choice == GROM_KERNEL_AUTO && batch >= K3O_MIN_BATCH &&
-         (int64_t)r->n * r->rank * batch >= K3O_MIN_WORK;
+  return r->kernel_choice == GROM_KERNEL_AUTO && (int64_t)r->n * r->rank * batch >= K3O_MIN_WORK;
 }
 
 // K3T: the batched CP form on the tensor cores (BF16 factors)

@@ -188,13 +188,12 @@ size_t k3g_scratch_bytes(int64_t n, int64_t rp, int max_batch, int storage, int 
 cudaError_t k3g_launch(const K3Plan& p, int storage, const K3Args& a, int batch, int max_batch, void* scratch,
                        int sm_count, cudaStream_t s);
 constexpr int K3G_MIN_BATCH = 16;
-// AUTO steps FP64 CP batches on the tensor cores (K3O) from this much work
-// per step (N R B) and this many trajectories on, else with K3D (measured on
-// GB300, 64 trajectories: N = R = 512 0.046 against 0.053 ms, N = 512, R =
-// 256 0.038 against 0.034 ms; 16 trajectories of N = R = 1024: 0.087
-// against 0.082 ms; 1024 trajectories of N = R = 1024: 0.62 against 1.93 ms)
+// AUTO steps FP64 CP batches (16 trajectories and more) on the tensor cores
+// (K3O) from this much work per step (N R B) on, else with K3D (measured on
+// GB300: N = R = 1024 at 16 trajectories 0.063 against 0.085 ms, at 1024
+// 0.535 against 1.93 ms; 64 trajectories of N = 512, R = 256 0.035 against
+// 0.034 ms, of N = R = 256 0.031 against 0.023 ms)
 constexpr int64_t K3O_MIN_WORK = (int64_t)1 << 24;
-constexpr int K3O_MIN_BATCH = 32;
 // Batched CP form of FP64 ROMs at FP64 tolerance in double-single FP32
 // arithmetic (K3D, same batch sizes as K3g): hi/lo copies of the factors
 // made at create, then per step a state split and two GEMMs.

@@ -56,12 +56,12 @@ def test_k3d_matches_oracle(form, n, r, batch):
 
 
 @pytest.mark.parametrize("form", ["cp_skew", "cp"])
-def test_k3d_n1024_rank_n(form):
-    # the batched workload's size: N = R = 1024, several column tiles and K
-    # splits (16 trajectories: from 32 on AUTO takes the tensor-core path, K3O)
+def test_k3d_n1024_large_rank(form):
+    # N = 1024 and R = 768, several column tiles and K splits (AUTO takes the
+    # tensor-core path, K3O, from N R B = 2^24 on)
     grom.build()
     n, batch = 1024, 16
-    fac, ref = _factors(form, n, n, 5)
+    fac, ref = _factors(form, n, 768, 5)
     U0 = synth.initial_condition(n, 3, 0, batch)
     rom = grom.Rom(n, form, "f64", factors=fac, stiffness=synth.diag_stiffness(n), max_batch=batch)
     c = _eval(rom, U0)
