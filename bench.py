@@ -803,16 +803,32 @@ def main():
             e1b.record(stream)
             torch.cuda.synchronize()
             kms, kl = prom.profile_read()
-            prom.profile(False)
             pms = e0b.elapsed_time(e1b) / bsteps
             kavg = kms / max(1, kl)
+            pairs = B > 8 and _packed_len(n) > 128  # the rule: SM pairs wherever a row has two blocks
+            single_ms = None
+            if pairs:
+                # the same steps on single CTAs (one 128-row MMA per CTA), for comparison
+                prom.set_tuning({"batch": B, "kernel": "tensor", "tile_m": 0, "split_a": 0, "split_b": 1})
+                str1 = grom.Trajectories(prom, U0)
+                str1.step(bsteps)
+                prom.profile_read()
+                torch.cuda.synchronize()
+                str1.step(bsteps)
+                torch.cuda.synchronize()
+                sms, sl = prom.profile_read()
+                single_ms = sms / max(1, sl)
+                str1.close()
+                prom.set_tuning({"batch": B, "kernel": "auto", "tile_m": 0, "split_a": 0, "split_b": 0})
+            prom.profile(False)
             pbytes = float(n) * n * _packed_len(n) * 2
             # the factored kernel's own work: one multiply-add per stored entry
             # and trajectory (N x N x lp of them, the stored half); the dense
             # contraction's 2 N^3 B is reported beside it as an equivalent rate
             own = 2.0 * n * n * _packed_len(n) * B
             pentry = {"ms_per_step": pms, "trajectory_steps_per_s": B * 1e3 / pms,
-                      "kernel": "k2p_tc_kernel (tcgen05, factored, skew-packed)" if B > 8 else "k1_packed_kernel",
+                      "kernel": ("k2p_pair_kernel (tcgen05 over SM pairs, cta_group::2, factored, skew-packed)" if pairs
+                                 else "k2p_tc_kernel (tcgen05, factored, skew-packed)" if B > 8 else "k1_packed_kernel"),
                       "kernel_ms": kavg, "alg_tflops": own / (kavg * 1e-3) / 1e12,
                       "alg_flops": "2 N N lp B (lp = %d stored positions per row)" % _packed_len(n),
                       "tc_frac_of_sustained_bf16": own / (kavg * 1e-3) / 1e12 / tc_sustained,
@@ -821,6 +837,9 @@ def main():
                       "issued_note": "twice the own work: the states enter the MMA as BF16 hi and lo parts",
                       "stored_tensor_bytes": pbytes,
                       "hbm_frac_per_tensor_read": pbytes / (kavg * 1e-3) / 1e9 / hbm_peak}
+            if single_ms is not None:
+                pentry["single_cta_kernel_ms"] = single_ms
+                pentry["single_cta_tc_frac_of_sustained_bf16"] = own / (single_ms * 1e-3) / 1e12 / tc_sustained
             if rank_id == 0:
                 uf = torch.from_numpy(U0.copy()).cuda()
                 cf = torch.empty_like(uf)

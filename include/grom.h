@@ -273,7 +273,8 @@ typedef struct grom_tuning {
   int32_t tile_m;  /* K2P: test indices per tile, 8..32; 0 = the plan's rule           */
   int32_t split_a; /* K2: CTAs sharing one output tile (split of j), 1..n;
                       K3T: splits of the projection GEMM; 0 = the rule                  */
-  int32_t split_b; /* K3T: splits of the expansion GEMM; 0 = the rule                  */
+  int32_t split_b; /* K3T: splits of the expansion GEMM; K2P: 1 = one CTA per tile,
+                      2 = SM pairs (one 256-row MMA over two CTAs); 0 = the rule        */
   int32_t timed;   /* grom_autotune: configurations timed                              */
   float ms;        /* grom_autotune: median device ms per evaluation of this entry      */
   float ms_rule;   /* grom_autotune: the same for the rules' configuration             */

@@ -311,7 +311,7 @@ static K2Plan k2_plan_of(const grom_rom* r, int batch) {
 }
 static K2PPlan k2p_plan_of(const grom_rom* r, int batch) {
   const grom_tuning* t = tuned(r, batch);
-  return k2p_plan(r->n, r->k1.lp, batch, r->sm_count, t ? t->tile_m : 0);
+  return k2p_plan(r->n, r->k1.lp, batch, r->sm_count, t ? t->tile_m : 0, t ? t->split_b : 0);
 }
 static K3TPlan k3t_plan_of(const grom_rom* r, int batch) {
   const grom_tuning* t = tuned(r, batch);
@@ -354,9 +354,9 @@ static bool tuning_ok(const TuneShape& s, const grom_tuning& t) {
     return k2_scratch_bytes(k2_plan(s.n, t.batch, s.sm_count, t.split_a)) <= s.k2_scratch;
   }
   if (s.form == GROM_FORM_FULL) {
-    if (t.split_a != 0 || t.split_b != 0) return false;
+    if (t.split_a != 0 || t.split_b < 0 || t.split_b > 2 || (t.split_b == 2 && !k2p_pair_ok(s.lp))) return false;
     if (t.tile_m != 0 && !k2p_tile_m_ok(t.batch, t.tile_m)) return false;
-    return k2p_scratch_bytes(k2p_plan(s.n, s.lp, t.batch, s.sm_count, t.tile_m)) <= s.k2_scratch;
+    return k2p_scratch_bytes(k2p_plan(s.n, s.lp, t.batch, s.sm_count, t.tile_m, t.split_b)) <= s.k2_scratch;
   }
   const K3TPlan p = k3t_plan(s.n, s.rank, s.form, t.batch, s.sm_count, t.split_a, t.split_b);
   if (t.tile_m != 0 || t.split_a < 0 || t.split_a > p.s1_max || t.split_b < 0 || t.split_b > p.s2_max) return false;
@@ -407,13 +407,18 @@ static void tune_space(const TuneShape& s, int batch, std::vector<grom_tuning>& 
         add(c);
       }
   } else if (s.form == GROM_FORM_FULL) {
-    const int rule = k2p_plan(s.n, s.lp, batch, s.sm_count).m;
+    const K2PPlan rp = k2p_plan(s.n, s.lp, batch, s.sm_count);
     for (int m = 8; m <= 32; ++m)
-      if (m != rule) {
+      if (m != rp.m) {
         grom_tuning c{};
         c.tile_m = m;
         add(c);
       }
+    if (k2p_pair_ok(s.lp)) {  // the other kernel (single CTAs or SM pairs) with its rule height
+      grom_tuning c{};
+      c.split_b = rp.ctas == 2 ? 1 : 2;
+      add(c);
+    }
   } else if (shape_is_cp(s)) {
     const K3TPlan p = k3t_plan(s.n, s.rank, s.form, batch, s.sm_count);
     for (int a : split_candidates(p.s1, p.s1_max))

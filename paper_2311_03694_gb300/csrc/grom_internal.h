@@ -131,20 +131,24 @@ struct K2PPlan {
   int btile;       // trajectories per column tile (multiple of 16, <= 128)
   int col_tiles;   // column tiles
   int pblks;       // 128-position blocks of a stored row
+  int ctas;        // 1: one CTA per tile; 2: SM pairs (cta_group::2), one pair per two blocks
+  int pbs;         // blocks in the tile numbering: pblks, rounded up to even for pairs
   int m;           // test indices per CTA tile
   int ranges;      // ceil(n / m)
-  int tiles;       // ranges * pblks * col_tiles
+  int tiles;       // CTA tiles: ranges * pbs * col_tiles
   int stages;      // pipeline depth (C tile + U hi/lo tiles)
   int tmem_cols;   // two accumulators of btile columns
   int wrows;       // rows of the mirrored-entry window (m + 127)
   int wpitch;      // its pitch in floats (btile + 1)
-  int grid;        // persistent CTAs
+  int grid;        // persistent CTAs (pairs: even, at most the pairs that fit at once)
   int64_t bp;      // padded batch
   size_t smem;
 };
-// m_force replaces the rule's tile height when k2p_tile_m_ok admits it.
-K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force = 0);
+// m_force replaces the rule's tile height when k2p_tile_m_ok admits it;
+// ctas_force (1 or 2) the rule's kernel, 2 only where k2p_pair_ok.
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force = 0, int ctas_force = 0);
 bool k2p_tile_m_ok(int batch, int m);
+bool k2p_pair_ok(int64_t lp);
 // Scratch of the largest plan over every batch a ROM with max_batch accepts.
 size_t k2_scratch_need(int64_t n, int max_batch, int sm_count);
 size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count);

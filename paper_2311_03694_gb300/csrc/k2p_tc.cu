@@ -42,6 +42,7 @@
 
 #include "grom_internal.h"
 #include "tc.cuh"
+#include "tc_pair.cuh"
 
 namespace grom {
 
@@ -52,9 +53,11 @@ constexpr int K2P_SMEM_MAX = 232448;             // opt-in shared memory per CTA
 
 struct K2PDev {
   int64_t n, np, lp, bp;
-  int btile, col_tiles, pblks, m, ranges, tiles, stages, tmem_cols, wrows, wpitch;
+  int btile, col_tiles, pblks, pbs, m, ranges, tiles, stages, tmem_cols, wrows, wpitch;
+  // pbs: position blocks in the tile and scratch numbering (pblks, or pblks
+  // rounded up to even for SM pairs; a block past pblks is all padding)
   const float* uf;  // bp x np FP32 states (zero padded)
-  float* cdp;       // pblks x n x bp direct partials (per position block)
+  float* cdp;       // pbs x n x bp direct partials (per position block)
   float* ep;        // tiles x wrows x btile mirrored-entry windows
   int* err;
 };
@@ -62,8 +65,8 @@ struct K2PDev {
 __device__ __forceinline__ void k2p_tile(const K2PDev& p, int tile, int& ct, int& pb, int64_t& i0, int64_t& i1) {
   ct = tile % p.col_tiles;
   const int rest = tile / p.col_tiles;
-  pb = rest % p.pblks;
-  const int r = rest / p.pblks;
+  pb = rest % p.pbs;
+  const int r = rest / p.pbs;
   i0 = (int64_t)r * p.m;
   i1 = i0 + p.m < p.n ? i0 + p.m : p.n;
 }
@@ -316,6 +319,238 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------- SM pairs
+// The same contraction with one pair MMA (cta_group::2, M = 256) per K step
+// over a cluster of two CTAs.  Each CTA holds the A tile of its own
+// 128-position block (blocks 2q and 2q + 1 of a pair tile) and one half of
+// the states operand (the leader the hi part, the peer the lo part), so a CTA
+// brings in 16 KB + 128 btile bytes per K step for the same MMA work per SM
+// as the single-CTA kernel's 16 KB + 256 btile bytes, and one more pipeline
+// stage fits beside the window.  The leader's MMA thread writes both SMs'
+// tensor memory.  Barriers: full (in the leader; both CTAs' TMA loads
+// complete on it), empty and accumulator-full (in both, multicast commits),
+// accumulator-empty (in the leader; the 16 epilogue warps of the pair arrive
+// on it).  Each CTA's epilogue is the single-CTA one for its own block.
+__device__ __forceinline__ void k2p_pair_tile(const K2PDev& p, int t2, uint32_t rank, int& ct, int& pb, int64_t& i0,
+                                              int64_t& i1, int& tile) {
+  ct = t2 % p.col_tiles;
+  const int rest = t2 / p.col_tiles;
+  const int halves = p.pbs >> 1;
+  pb = 2 * (rest % halves) + (int)rank;
+  const int r = rest / halves;
+  i0 = (int64_t)r * p.m;
+  i1 = i0 + p.m < p.n ? i0 + p.m : p.n;
+  tile = (r * p.pbs + pb) * p.col_tiles + ct;
+}
+
+// Stops both CTAs of the pair: their waits return at the next check.
+__device__ __forceinline__ void k2p_pair_abort(volatile int* abort_flag, uint32_t peer_abort, int* err) {
+  *abort_flag = 1;
+  tcp::st_cluster_u32(peer_abort, 1u);
+  atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2P_THREADS, 1)
+    k2p_pair_kernel(const __grid_constant__ CUtensorMap tmap_c, const __grid_constant__ CUtensorMap tmap_uh,
+                    const __grid_constant__ CUtensorMap tmap_ul, const K2PDev p) {
+  extern __shared__ uint8_t smem_raw[];
+  // the same 1024-byte aligned offset in both CTAs (the pair MMA reads the
+  // peer's operands at the leader's offsets)
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int S = p.stages;
+  const int stage_b = p.btile * 128;  // this CTA's half of U^T (hi or lo)
+  uint8_t* sa = smem;                                   // S x (128 positions x 64 j)
+  uint8_t* sb = sa + (size_t)S * K2P_A_BYTES;           // S x (hi or lo)
+  float* win = reinterpret_cast<float*>(sb + (size_t)S * stage_b);
+  const size_t wbytes = ((size_t)p.wrows * p.wpitch * 4 + 15) / 16 * 16;
+  float* red = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(win) + wbytes);  // 4 quadrants x 128 columns
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + 4 * 128);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;  // accumulator b holds a finished D_i
+  uint64_t* acce = accf + 2;   // accumulator b has been read back (leader)
+  uint64_t* drain = acce + 2;  // every issued MMA has completed (leader)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* ep_abort = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = tcp::cta_rank();
+  const bool leader = rank == 0;
+  const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
+  const int pair_tiles = p.tiles >> 1;
+  const int jblocks = (int)((p.n + 63) / 64);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], 2 * K2P_EPI / 32);
+    }
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    *ep_abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_c);
+    tc::prefetch_tmap(leader ? &tmap_uh : &tmap_ul);
+  }
+  if (warp == 1) {
+    tcp::tmem_alloc2(tmem_slot, (uint32_t)p.tmem_cols);
+    tcp::tmem_relinquish2();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tcp::cluster_sync();  // both CTAs' barriers exist before any arrival from the other
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t peer_abort = tcp::map_shared((const void*)abort_flag, rank ^ 1u);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      const CUtensorMap* tmap_u = leader ? &tmap_uh : &tmap_ul;
+      int64_t q = 0;  // K steps issued
+      bool run = true;
+      for (int t2 = cluster; run && t2 < pair_tiles; t2 += nclusters) {
+        int ct, pb, tile;
+        int64_t i0, i1;
+        k2p_pair_tile(p, t2, rank, ct, pb, i0, i1, tile);
+        for (int64_t i = i0; run && i < i1; ++i) {
+          for (int jb = 0; jb < jblocks; ++jb, ++q) {
+            const int s = (int)(q % S);
+            if (q >= S && !ptx::mbar_wait(&empty[s], (uint32_t)(((q / S) & 1) ^ 1), abort_flag)) {
+              k2p_pair_abort(abort_flag, peer_abort, p.err);
+              run = false;
+              break;
+            }
+            const uint32_t fb = tcp::map_shared(&full[s], 0);
+            if (leader) ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(2 * (K2P_A_BYTES + stage_b)));
+            uint8_t* a = sa + (size_t)s * K2P_A_BYTES;
+            tcp::tma_load_3d_pair(a, &tmap_c, pb * 128, jb * 64, (int32_t)i, fb);
+            tcp::tma_load_3d_pair(a + K2P_A_BYTES / 2, &tmap_c, pb * 128 + 64, jb * 64, (int32_t)i, fb);
+            tcp::tma_load_2d_pair(sb + (size_t)s * stage_b, tmap_u, jb * 64, ct * p.btile, fb);
+          }
+        }
+      }
+      // the leader's full barriers count both CTAs' copies: the copies still
+      // in flight land before the leader reaches the closing cluster barrier
+      if (leader)
+        for (int64_t x = q > S ? q - S : 0; x < q; ++x)
+          if (!ptx::mbar_wait(&full[x % S], (uint32_t)((x / S) & 1), nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------- MMA issuer (leader)
+    if (lane == 0 && leader) {
+      const uint32_t idesc = tc::idesc_bf16_f32_amn(256, 2 * p.btile);  // hi (leader) | lo (peer)
+      int64_t q = 0, icnt = 0;
+      bool run = true;
+      for (int t2 = cluster; run && t2 < pair_tiles; t2 += nclusters) {
+        int ct, pb, tile;
+        int64_t i0, i1;
+        k2p_pair_tile(p, t2, rank, ct, pb, i0, i1, tile);
+        for (int64_t i = i0; run && i < i1; ++i, ++icnt) {
+          const int bi = (int)(icnt & 1);
+          if (icnt >= 2 &&
+              !tcp::mbar_wait_cluster(&acce[bi], (uint32_t)(((icnt >> 1) - 1) & 1), abort_flag)) {
+            k2p_pair_abort(abort_flag, peer_abort, p.err);
+            run = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + (uint32_t)(bi * 2 * p.btile);
+          for (int jb = 0; jb < jblocks; ++jb, ++q) {
+            const int s = (int)(q % S);
+            if (!ptx::mbar_wait(&full[s], (uint32_t)((q / S) & 1), abort_flag)) {
+              k2p_pair_abort(abort_flag, peer_abort, p.err);
+              run = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint64_t a0 = tc::sw128_mnmajor_desc(sa + (size_t)s * K2P_A_BYTES, K2P_A_BYTES / 2, 1024);
+            const uint64_t b0 = tc::sw128_kmajor_desc(sb + (size_t)s * stage_b);  // btile rows per CTA
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t accum = (jb > 0 || k > 0) ? 1u : 0u;
+              tcp::mma2_bf16(acc, a0 + (uint64_t)(128 * k), b0 + 2 * k, idesc, accum);
+            }
+            tcp::commit2_mc(&empty[s], 3);
+          }
+          if (run) tcp::commit2_mc(&accf[bi], 3);
+        }
+      }
+      tcp::commit2_mc(drain, 3);
+      if (!ptx::mbar_wait(drain, 0, nullptr)) atomicOr(p.err, DEV_ERR_TIMEOUT);
+    }
+  } else {
+    // ----------------------------------------------- epilogue (warps 2-9)
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int et = threadIdx.x - 64;
+    const uint32_t acce_l0 = tcp::map_shared(&acce[0], 0), acce_l1 = tcp::map_shared(&acce[1], 0);
+    for (int x = et; x < p.wrows * p.wpitch; x += K2P_EPI) win[x] = 0.f;
+    ptx::named_sync(1, K2P_EPI);
+    int64_t icnt = 0;
+    bool run = true;
+    for (int t2 = cluster; run && t2 < pair_tiles; t2 += nclusters) {
+      int ct, pb, tile;
+      int64_t i0, i1;
+      k2p_pair_tile(p, t2, rank, ct, pb, i0, i1, tile);
+      const int64_t pp = (int64_t)pb * 128 + 32 * q + lane;
+      const float* ut = p.uf + (int64_t)ct * p.btile * p.np;
+      float* cd = p.cdp + (int64_t)pb * p.n * p.bp + (int64_t)ct * p.btile;
+      for (int64_t i = i0; i < i1; ++i, ++icnt) {
+        const int bi = (int)(icnt & 1);
+        const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(&accf[bi], (uint32_t)((icnt >> 1) & 1), abort_flag));
+        if (!got && lane == 0) {
+          *ep_abort = 1;
+          k2p_pair_abort(abort_flag, peer_abort, p.err);
+        }
+        ptx::named_sync(1, K2P_EPI);
+        if (*ep_abort) {
+          run = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const int64_t k = (i + 1 + pp) % p.n;
+        float* wrow = win + ((int)(i - i0) + 32 * q + lane) * p.wpitch;
+        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(bi * 2 * p.btile);
+        for (int c0 = 32 * half; c0 < p.btile; c0 += 64) {
+          const uint32_t ahi = acc + (uint32_t)c0, alo = acc + (uint32_t)(p.btile + c0);
+          const float* ucol = ut + (int64_t)c0 * p.np;
+          if (p.btile - c0 >= 32)
+            k2p_chunk<32>(ahi, alo, ucol, p.np, k, i, wrow + c0, red + q * 128 + c0, lane);
+          else
+            k2p_chunk<16>(ahi, alo, ucol, p.np, k, i, wrow + c0, red + q * 128 + c0, lane);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tcp::mbar_arrive_cluster(bi ? acce_l1 : acce_l0);
+        ptx::named_sync(1, K2P_EPI);
+        if (et < p.btile) cd[i * p.bp + et] = ((red[et] + red[128 + et]) + red[256 + et]) + red[384 + et];
+      }
+      if (!run) break;
+      float* dst = p.ep + (int64_t)tile * p.wrows * p.btile;
+      for (int x = et; x < p.wrows * p.btile; x += K2P_EPI) {
+        const int w = x / p.btile, b = x - w * p.btile;
+        dst[x] = win[w * p.wpitch + b];
+        win[w * p.wpitch + b] = 0.f;
+      }
+      ptx::named_sync(1, K2P_EPI);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tcp::cluster_sync();  // no thread of either CTA touches the other's memory or the tensor memory after this
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tcp::tmem_dealloc2(tmem, (uint32_t)p.tmem_cols);
+  }
+}
+
 // uf[b][k] = u_b[k] (FP32) and its BF16 hi/lo parts, zero for padding and
 // inactive trajectories.
 __global__ void k2p_prep_kernel(const K2PDev p, float* uf, __nv_bfloat16* uh, __nv_bfloat16* ul, const double* u,
@@ -355,7 +590,7 @@ __global__ void k2p_finish_kernel(const K2PDev p, double* c, int64_t c_stride, d
     auto add = [&](int r) {
       int64_t w = x - (int64_t)r * p.m;
       if (w < 0) w += p.n;
-      const float* e = p.ep + ((int64_t)(r * p.pblks + pb) * p.col_tiles + ct) * p.wrows * p.btile + bl;
+      const float* e = p.ep + ((int64_t)(r * p.pbs + pb) * p.col_tiles + ct) * p.wrows * p.btile + bl;
       for (; w < p.wrows; w += p.n) sm += e[w * p.btile];
     };
     if (p.n <= p.wrows) {
@@ -418,8 +653,14 @@ static int k2p_btile(int batch) {
   return btile > 128 ? 128 : btile;
 }
 
+// SM pairs need at least two position blocks (a stored row longer than
+// 128 positions).
+bool k2p_pair_ok(int64_t lp) { return (lp + 127) / 128 >= 2; }
+
 // The tile heights the plan considers: m in [8, 32] that keep the deepest
-// pipeline the shared memory allows at m = 8 (the window grows with m).
+// pipeline the shared memory allows at m = 8 (the window grows with m).  The
+// SM-pair kernel's stages are smaller, so every height admitted here keeps at
+// least as many stages there.
 bool k2p_tile_m_ok(int batch, int m) {
   if (m < 8 || m > 32) return false;
   const int btile = k2p_btile(batch);
@@ -428,7 +669,7 @@ bool k2p_tile_m_ok(int batch, int m) {
   return k2p_stages_for(m, btile + 1, stage) >= (s8 < 3 ? s8 : 3);
 }
 
-K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force) {
+K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force, int ctas_force) {
   K2PPlan p{};
   p.n = n;
   p.np = padded_n(n);
@@ -438,17 +679,25 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force) {
   p.col_tiles = (batch + btile - 1) / btile;
   p.bp = (int64_t)p.col_tiles * btile;
   p.pblks = (int)((lp + 127) / 128);
+  // SM pairs wherever a row has two blocks: measured 4-7 % faster than
+  // single CTAs from 16 to 1024 trajectories at N = 512 and 1024
+  const bool pair_ok = k2p_pair_ok(lp) && sm_count >= 2;
+  int ctas = pair_ok ? 2 : 1;
+  if (ctas_force == 1 || (ctas_force == 2 && pair_ok)) ctas = ctas_force;
+  p.ctas = ctas;
+  p.pbs = ctas == 2 ? (p.pblks + 1) / 2 * 2 : p.pblks;
   p.wpitch = btile + 1;  // odd pitch: the 32 lanes of a warp hit 32 banks
-  const int stage = K2P_A_BYTES + 2 * btile * 128;
+  const int stage = K2P_A_BYTES + (ctas == 2 ? 1 : 2) * btile * 128;
   // test indices per tile: among the heights k2p_tile_m_ok admits, the
-  // largest whose tile count fills whole waves of SMs best
+  // largest whose tile count fills whole waves of SMs (pairs of SMs) best
+  const int units = ctas == 2 ? sm_count / 2 : sm_count;
   double best = -1.0;
   int bm = 8;
   for (int m = 32; m >= 8; --m) {
     if (!k2p_tile_m_ok(batch, m)) continue;
-    const int64_t tiles = (n + m - 1) / m * p.pblks * p.col_tiles;
-    const int64_t waves = (tiles + sm_count - 1) / sm_count;
-    const double eff = (double)tiles / (double)(waves * sm_count);
+    const int64_t tiles = (n + m - 1) / m * (p.pbs / ctas) * p.col_tiles;
+    const int64_t waves = (tiles + units - 1) / units;
+    const double eff = (double)tiles / (double)(waves * units);
     if (eff > best + 1e-9) {
       best = eff;
       bm = m;
@@ -457,7 +706,7 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force) {
   if (m_force > 0 && k2p_tile_m_ok(batch, m_force)) bm = m_force;
   p.m = bm;
   p.ranges = (int)((n + bm - 1) / bm);
-  p.tiles = p.ranges * p.pblks * p.col_tiles;
+  p.tiles = p.ranges * p.pbs * p.col_tiles;
   p.wrows = bm + 127;
   int st = k2p_stages_for(bm, p.wpitch, stage);
   if (st < 2) st = 2;
@@ -466,21 +715,50 @@ K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force) {
   int cols = 64;  // two accumulators of 2 btile columns (hi | lo); chunks of 32 stay inside
   while (cols < 4 * btile) cols <<= 1;
   p.tmem_cols = cols;
-  p.grid = p.tiles < sm_count ? p.tiles : sm_count;
+  if (ctas == 2) {
+    const int pairs = p.tiles / 2;
+    p.grid = 2 * (pairs < units ? pairs : units);
+  } else {
+    p.grid = p.tiles < sm_count ? p.tiles : sm_count;
+  }
   return p;
 }
 
 // uf | uh | ul | direct partials | windows
 size_t k2p_scratch_bytes(const K2PPlan& p) {
   const size_t st = (size_t)p.bp * p.np;
-  return st * (4 + 2 + 2) + 4 * ((size_t)p.pblks * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
+  return st * (4 + 2 + 2) + 4 * ((size_t)p.pbs * p.n * p.bp + (size_t)p.tiles * p.wrows * p.btile);
 }
 
+// Over both kernels (the tuning may pick either).
 size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count) {
   size_t need = 0;
   for (int b = 16; b - 16 < max_batch; b += 16)
-    need = std::max(need, k2p_scratch_bytes(k2p_plan(n, lp, b < max_batch ? b : max_batch, sm_count)));
+    for (int ctas = 1; ctas <= 2; ++ctas)
+      need = std::max(need, k2p_scratch_bytes(k2p_plan(n, lp, b < max_batch ? b : max_batch, sm_count, 0, ctas)));
   return need;
+}
+
+// Clusters of two that fit on the device at once with this shared memory
+// (one CTA per SM); 0 if none.
+static int k2p_pair_clusters(size_t smem) {
+  static int cached[64];
+  static size_t cached_smem[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev] > 0 && cached_smem[dev] == smem) return cached[dev];
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(K2P_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, (void*)k2p_pair_kernel, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cached[dev] = nc;
+  cached_smem[dev] = smem;
+  return nc;
 }
 
 cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
@@ -492,6 +770,7 @@ cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& 
   d.btile = p.btile;
   d.col_tiles = p.col_tiles;
   d.pblks = p.pblks;
+  d.pbs = p.pbs;
   d.m = p.m;
   d.ranges = p.ranges;
   d.tiles = p.tiles;
@@ -506,17 +785,29 @@ cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& 
   __nv_bfloat16* ul = uh + st;
   d.uf = uf;
   d.cdp = reinterpret_cast<float*>(ul + st);
-  d.ep = d.cdp + (size_t)p.pblks * p.n * p.bp;
+  d.ep = d.cdp + (size_t)p.pbs * p.n * p.bp;
   CUtensorMap mh, ml;
   if (!k2p_make_tmap_u(&mh, uh, p.np, p.bp, p.btile) || !k2p_make_tmap_u(&ml, ul, p.np, p.bp, p.btile))
     return cudaErrorInvalidValue;
   const int64_t prep = p.bp * p.np;
   k2p_prep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(d, uf, uh, ul, a.u, a.u_stride, a.hist, a.taken,
                                                                  a.hist_stride, a.active, a.batch);
-  cudaError_t e = cudaFuncSetAttribute(k2p_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-  if (e != cudaSuccess) return e;
-  if (a.ev0) prof_record(a.ev0, s);
-  k2p_tc_kernel<<<(unsigned)p.grid, K2P_THREADS, p.smem, s>>>(*tmap, mh, ml, d);
+  cudaError_t e;
+  if (p.ctas == 2) {
+    e = cudaFuncSetAttribute(k2p_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    // persistent pairs: no more clusters than fit at once
+    const int fit = k2p_pair_clusters(p.smem);
+    if (fit < 1) return cudaErrorInvalidConfiguration;
+    const int grid = p.grid / 2 < fit ? p.grid : 2 * fit;
+    if (a.ev0) prof_record(a.ev0, s);
+    k2p_pair_kernel<<<(unsigned)grid, K2P_THREADS, p.smem, s>>>(*tmap, mh, ml, d);
+  } else {
+    e = cudaFuncSetAttribute(k2p_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    if (a.ev0) prof_record(a.ev0, s);
+    k2p_tc_kernel<<<(unsigned)p.grid, K2P_THREADS, p.smem, s>>>(*tmap, mh, ml, d);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.ev1) prof_record(a.ev1, s);

@@ -68,14 +68,24 @@ static void check_k2(int64_t n, int batch, int sm, int splits, size_t need) {
         k2_scratch_bytes(p), need);
 }
 
-static void check_k2p(int64_t n, int64_t lp, int batch, int sm, int m, size_t need) {
-  const K2PPlan p = k2p_plan(n, lp, batch, sm, m);
+static void check_k2p(int64_t n, int64_t lp, int batch, int sm, int m, int ctas, size_t need) {
+  const K2PPlan p = k2p_plan(n, lp, batch, sm, m, ctas);
+  CHECK(p.ctas == 1 || p.ctas == 2, "K2P ctas %d", p.ctas);
+  CHECK(ctas == 0 || p.ctas == ctas || (ctas == 2 && !k2p_pair_ok(lp) && p.ctas == 1), "K2P forced ctas %d -> %d",
+        ctas, p.ctas);
+  CHECK(p.ctas == 1 || (p.pblks >= 2 && k2p_pair_ok(lp)), "K2P pairs with %d blocks", p.pblks);
+  // pairs: both CTAs of a pair tile take blocks 2q, 2q + 1 < pbs, so every
+  // CTA tile has its own windows and direct partials in the scratch
+  CHECK(p.ctas == 1 ? p.pbs == p.pblks : (p.pbs % 2 == 0 && p.pbs >= p.pblks && p.pbs <= p.pblks + 1),
+        "K2P block stride %d (blocks %d, ctas %d)", p.pbs, p.pblks, p.ctas);
+  CHECK(p.ctas == 1 || (p.grid % 2 == 0 && p.grid >= 2 && p.grid <= p.tiles && p.tiles % 2 == 0), "K2P pair grid %d",
+        p.grid);
   CHECK(p.smem <= SMEM_MAX, "K2P n %ld b %d m %d smem %zu", (long)n, batch, p.m, p.smem);
   CHECK(p.stages >= 2, "K2P stages %d", p.stages);
   CHECK(tmem_ok(p.tmem_cols) && p.tmem_cols >= 4 * p.btile, "K2P tmem %d", p.tmem_cols);
   CHECK(p.m >= 8 && p.m <= 32 && (m == 0 || p.m == m), "K2P m %d forced %d", p.m, m);
   CHECK((int64_t)p.ranges * p.m >= n && (int64_t)(p.ranges - 1) * p.m < n, "K2P ranges");
-  CHECK(p.tiles == p.ranges * p.pblks * p.col_tiles && p.grid >= 1 && p.grid <= sm, "K2P tiles");
+  CHECK(p.tiles == p.ranges * p.pbs * p.col_tiles && p.grid >= 1 && p.grid <= sm, "K2P tiles");
   CHECK((int64_t)p.pblks * 128 >= p.lp && p.lp % 64 == 0, "K2P position blocks lp %ld", (long)p.lp);
   CHECK(p.wrows == p.m + 127 && p.wpitch == p.btile + 1, "K2P window");
   CHECK(p.btile % 16 == 0 && p.btile <= 128 && p.bp >= batch && p.bp - batch < p.btile, "K2P btile");
@@ -123,12 +133,12 @@ int main() {
         const size_t need2 = k2_scratch_need(n, max_batch, sm), need2p = k2p_scratch_need(n, lp, max_batch, sm);
         for (int b = 1; b <= max_batch; b += (b < 300 ? 1 : 37)) {
           check_k2(n, b, sm, 0, need2);
-          check_k2p(n, lp, b, sm, 0, need2p);
+          for (int ctas = 0; ctas <= 2; ++ctas) check_k2p(n, lp, b, sm, 0, ctas, need2p);
           if (b % 16 == 1 || b == max_batch) {  // one batch per bucket: the tune space
             for (const grom_tuning& t : space(GROM_FORM_FULL, GROM_LAYOUT_DENSE, n, 0, max_batch, b, sm))
               if (t.kernel == GROM_KERNEL_TENSOR) check_k2(n, b, sm, t.split_a, need2);
             for (const grom_tuning& t : space(GROM_FORM_FULL, GROM_LAYOUT_SKEW_PACKED, n, 0, max_batch, b, sm))
-              if (t.kernel == GROM_KERNEL_TENSOR) check_k2p(n, lp, b, sm, t.tile_m, need2p);
+              if (t.kernel == GROM_KERNEL_TENSOR) check_k2p(n, lp, b, sm, t.tile_m, t.split_b, need2p);
           }
         }
         for (int form : {GROM_FORM_CP, GROM_FORM_CP_SKEW})

@@ -51,7 +51,10 @@ def test_space_starts_with_the_rule_and_has_no_duplicates(form, storage, layout,
         if form == "full" and layout == "dense":
             assert e["tile_m"] == 0 and e["split_b"] == 0 and 1 <= e["split_a"] <= n
         elif form == "full":
-            assert e["split_a"] == 0 and e["split_b"] == 0 and 8 <= e["tile_m"] <= 32
+            # every admissible height of the rule's kernel, then the other
+            # kernel (1: single CTAs, 2: SM pairs) with its rule height
+            assert e["split_a"] == 0
+            assert (e["split_b"] == 0 and 8 <= e["tile_m"] <= 32) or (e["split_b"] in (1, 2) and e["tile_m"] == 0)
         else:
             assert e["tile_m"] == 0
             assert 1 <= e["split_a"] <= _k3t_split_max(n, rank, form, 1)
@@ -71,6 +74,17 @@ def test_svd_bf16_has_no_tensor_kernel():
     assert len(sp) == 1 and sp[0]["kernel"] == "stream"
 
 
+def test_packed_space_has_the_other_k2p_kernel():
+    # n = 1024 (four 128-position blocks): SM pairs by the rule, so the space
+    # offers single CTAs
+    for batch, other in [(9, 1), (64, 1), (256, 1), (1024, 1)]:
+        sp = grom.tune_space("full", "bf16", 1024, batch, max_batch=1024, layout="skew_packed", sm_count=SM)
+        assert [e["split_b"] for e in sp if e["split_b"] != 0] == [other]
+    # n = 200: one block, no pairs
+    sp = grom.tune_space("full", "bf16", 200, 512, max_batch=512, layout="skew_packed", sm_count=SM)
+    assert all(e["split_b"] == 0 for e in sp)
+
+
 @pytest.mark.parametrize("form,layout,rank", [("full", "dense", 0), ("full", "skew_packed", 0), ("cp_skew", "dense", 512)])
 def test_one_entry_serves_a_bucket(form, layout, rank):
     # batches with the same ceil(batch / 16) share every plan: same space
@@ -84,13 +98,14 @@ def test_k2p_tile_heights_are_bounded_by_the_scratch():
     # lower tiles mean more tiles and a larger mirrored-entry scratch: the
     # heights admitted are the tallest ones, down to what create's scratch holds
     sp = grom.tune_space("full", "bf16", 1024, 40, max_batch=64, layout="skew_packed", sm_count=SM)
+    sp = [e for e in sp if e["split_b"] == 0]  # the rule's kernel (single CTAs at 40 trajectories)
     ms = sorted(e["tile_m"] for e in sp[2:])
     assert len(ms) >= 8 and set(ms) <= set(range(8, 33))
     rule = (set(range(min(ms), 33)) - set(ms))
     assert len(rule) <= 1  # a contiguous range up to 32, less the rule's own height
     # a ROM sized for larger batches holds more scratch: more heights
     big = grom.tune_space("full", "bf16", 1024, 40, max_batch=1024, layout="skew_packed", sm_count=SM)
-    assert {e["tile_m"] for e in sp[2:]} <= {e["tile_m"] for e in big[2:]}
+    assert {e["tile_m"] for e in sp[2:]} <= {e["tile_m"] for e in big[2:] if e["split_b"] == 0}
 
 
 def test_larger_scratch_admits_more_splits():
