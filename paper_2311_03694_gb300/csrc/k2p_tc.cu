@@ -454,8 +454,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2P_THREADS, 1)
         k2p_pair_tile(p, t2, rank, ct, pb, i0, i1, tile);
         for (int64_t i = i0; run && i < i1; ++i, ++icnt) {
           const int bi = (int)(icnt & 1);
-          if (icnt >= 2 &&
-              !tcp::mbar_wait_cluster(&acce[bi], (uint32_t)(((icnt >> 1) - 1) & 1), abort_flag)) {
+          if (icnt >= 2 && !ptx::mbar_wait(&acce[bi], (uint32_t)(((icnt >> 1) - 1) & 1), abort_flag)) {
             k2p_pair_abort(abort_flag, peer_abort, p.err);
             run = false;
             break;
@@ -528,7 +527,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2P_THREADS, 1)
         }
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tcp::mbar_arrive_cluster(bi ? acce_l1 : acce_l0);
+        // the loads above are complete (tcgen05.wait::ld): the signal orders no memory access
+        if (lane == 0) tcp::mbar_arrive_remote(bi ? acce_l1 : acce_l0);
         ptx::named_sync(1, K2P_EPI);
         if (et < p.btile) cd[i * p.bp + et] = ((red[et] + red[128 + et]) + red[256 + et]) + red[384 + et];
       }

@@ -1,8 +1,8 @@
 // Inline-PTX helpers for tcgen05 work shared by the two CTAs of a cluster
 // of two (an SM pair, `cta_group::2`): cluster rank and addressing, cluster
-// barriers, cluster-scope mbarrier arrivals and waits, pair-wide tensor
-// memory, the pair MMA, multicast commits and TMA loads that complete on the
-// leader CTA's mbarrier.
+// barriers, mbarrier arrivals on the other CTA, pair-wide tensor memory, the
+// pair MMA, multicast commits and TMA loads that complete on the leader CTA's
+// mbarrier.
 //
 // In a pair MMA of shape M x N, issued by one thread of the even (leader)
 // CTA, each CTA supplies M/2 rows of A and N/2 rows of B from the same
@@ -45,36 +45,12 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// Arrive (release at cluster scope) on an mbarrier of either CTA.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(ptx::smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// A local mbarrier that the other CTA arrives on: waits (acquire at cluster
-// scope) for the phase of the given parity; false after one second or once
-// *abort is set.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try_wait_cluster(bar, parity)) return true;
-  const uint64_t t0 = ptx::globaltimer();
-  for (uint32_t spin = 0;; ++spin) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((spin & 63u) == 63u) {
-      if (abort && *abort) return false;
-      if (ptx::globaltimer() - t0 > ptx::WAIT_LIMIT_NS) return false;
-    }
-  }
+// Arrive on an mbarrier of either CTA with the default (CTA-scope)
+// semantics: for signals that order no generic memory accesses, e.g. that
+// tensor-memory loads completed by tcgen05.wait::ld are done.  Avoids the
+// cluster-scope release fence.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
 // ------------------------------------------------------- pair tensor memory
