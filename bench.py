@@ -875,7 +875,8 @@ def main():
                     "ms_per_step": cms, "trajectory_steps_per_s": B * 1e3 / cms,
                     "alg_tflops": cflops / (cms * 1e-3) / 1e12,
                     "kernel": ("k3t_gemm x2 (tcgen05 projections and expansion)" if storage == "bf16" and B >= 16
-                               else "k3o (tcgen05 GEMMs of 6-bit digit slices, FP64 tolerance)"
+                               else ("k3o (tcgen05 GEMMs of digit slices: %s-bit for the projections, 6-bit for the "
+                                     "expansion; FP64 tolerance)" % ("7" if n <= 1024 else "6"))
                                if storage == "f64" and B >= 16 and (kernel == "tensor" or (
                                    kernel == "auto" and n * R * B >= 2 ** 24))
                                else "k3d project/expand (double-single FP32 GEMMs, FP64 tolerance)"
