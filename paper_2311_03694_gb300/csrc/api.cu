@@ -1117,9 +1117,23 @@ static cudaError_t launch_steps(grom_traj* t, int count, double* energy, double*
   const bool fused_k3 = r->diagonal && is_cp(r) && !use_k3g(r, t->batch) && !use_k3t(r, t->batch);
   const bool fused_k3t = r->diagonal && use_k3t(r, t->batch);
   const bool fused_k3d = r->diagonal && use_k3d(r, t->batch) && !use_k3o(r, t->batch);
+  const bool fused_k3o = r->diagonal && !use_k3t(r, t->batch) && use_k3o(r, t->batch);
   for (int s = 0; s < count; ++s) {
     cudaError_t e;
-    if (fused_k3d) {
+    if (fused_k3o) {
+      // the expansion's combine and the step in one kernel
+      K3Args k = k3_args(r);
+      k.hist = t->hist;
+      k.taken = t->taken;
+      k.hist_stride = 6 * (int64_t)r->n;
+      k.active = t->active;
+      cudaEvent_t e0, e1;
+      if (!prof_pair(r, &e0, &e1)) return cudaErrorMemoryAllocation;
+      if (e0) prof_record(e0, strm);
+      e = k3o_launch_step(r->n, r->k3.rb, r->rank, k, r->k3o_factors, t->batch, r->k3o_scratch, r->err,
+                          r->sm_count, a, s, strm);
+      if (e1 && e == cudaSuccess) e = prof_record(e1, strm);
+    } else if (fused_k3d) {
       // as K3T: the state planes once per call, then the ones the step kernel writes
       K3Args k = k3_args(r);
       k.hist = t->hist;

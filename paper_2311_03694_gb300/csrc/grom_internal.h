@@ -216,7 +216,7 @@ cudaError_t k3d_launch_step(const K3Plan& p, const K3Args& a, const void* factor
                             int sm_count, bool prep, const StepArgs& st, int step_index, cudaEvent_t ev0,
                             cudaEvent_t ev1, cudaStream_t s);
 // K3O: the batched CP form of FP64 ROMs on the BF16 tensor cores, every
-// operand split into 6-bit integer digit slices (Sec. 3.1, eq. tc_ap).
+// operand split into 7- or 6-bit integer digit slices (Sec. 3.1, eq. tc_ap).
 bool k3o_supported(int64_t n, int64_t r, int form);
 size_t k3o_factor_bytes(int64_t n, int64_t rp, int64_t r, int form);
 size_t k3o_scratch_bytes(int64_t n, int64_t rp, int64_t r, int form, int max_batch);
@@ -224,6 +224,12 @@ cudaError_t k3o_build_factors(const uint8_t* op, size_t panel_bytes, int64_t n, 
                               void* out, cudaStream_t s);
 cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
                        void* scratch, int* err, int sm_count, cudaStream_t s);
+// The same evaluation for stepping (a.hist/a.taken set): the expansion's
+// combine and the diagonal BDF3/EXT3 step (the blocks of k_step_diag_mc)
+// run as one kernel; the same bits as k3o_launch followed by the step.
+cudaError_t k3o_launch_step(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
+                            void* scratch, int* err, int sm_count, const StepArgs& st, int step_index,
+                            cudaStream_t s);
 cudaError_t k3o_gemm_launch(const void* A, int64_t M, int64_t mslice, const void* B, int64_t ncols,
                             int64_t nslice, int64_t K, int slices, float* out, int* err, int sm_count,
                             cudaStream_t s);
@@ -340,6 +346,11 @@ __device__ __forceinline__ void step_done(const StepArgs& a, int b, int64_t l) {
     a.steps_left[b] = left;
     if (left <= 0) a.active_rw[b] = 0;
   }
+}
+// The common case of the diagonal step: identity mass, no linear or forcing
+// term and no energy or invariant asked for (the PLAIN kernel variants).
+inline bool step_plain(const StepArgs& a) {
+  return !a.mass_diag && !a.lin_diag && !a.forcing && !a.energy && !a.invariant;
 }
 constexpr int STEP_MC_THREADS = 128;
 inline int step_mc_blocks(int64_t n) { return (int)((n + STEP_MC_THREADS - 1) / STEP_MC_THREADS); }

@@ -37,6 +37,7 @@
 
 #include "ds_arith.cuh"
 #include "grom_internal.h"
+#include "step_mc.cuh"
 
 namespace grom {
 
@@ -418,6 +419,36 @@ __global__ void __launch_bounds__(256) k3o_combine_exp(const ODims d, const K3Ar
   }
 }
 
+// The expansion's combine fused with the diagonal BDF3/EXT3 step: a block of
+// the step (k_step_diag_mc's grid and element mapping) first forms c_bi for
+// exactly the elements its threads then step, as k3o_combine_exp does, and
+// writes it into the history ring; each thread then reads back only what it
+// wrote itself.  One launch and one pass over c fewer than the combine
+// followed by the step kernel, with the same bits.
+template <bool PLAIN>
+__global__ void __launch_bounds__(STEP_MC_THREADS)
+    k3o_exp_step(const ODims d, const float* __restrict__ D2, const int* __restrict__ sexp,
+                 const int* __restrict__ tau2, const StepArgs st, const int step_index) {
+  __shared__ double sh[64];
+  __shared__ int bad;
+  __shared__ int last;
+  const int blk = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  if (!st.active || st.active[b]) {
+    const int64_t M = OZ_S * d.me;
+    double* ring = st.hist + b * st.hist_stride + (3 + st.taken[b] % 3) * d.n;
+    for (int e = 0; e < st.ept; ++e) {
+      const int64_t i = ((int64_t)blk * st.ept + e) * STEP_MC_THREADS + tid;
+      if (i >= d.n) break;
+      float S, s;
+      oz_sum<OZ_S, OZ_BITS>(D2, M, d.me, d.bq, b, i, S, s);
+      oz_scale_ds(S, s, sexp[i] + tau2[b]);
+      ring[i] = (double)S + (double)s;
+    }
+  }
+  step_mc_block<PLAIN>(st, step_index, K1Plan{}, K1Args{}, 0, 0, 1, K3TStepFuse{}, blk, b, tid,
+                       [] { __syncthreads(); }, sh, &bad, &last);
+}
+
 // ------------------------------------------------------------------- host
 bool k3o_supported(int64_t n, int64_t r, int form) {
   const ODims d = oz_dims(n, r, r, form, 1);
@@ -453,9 +484,12 @@ static unsigned oz_flat_blocks(int64_t count, int sm_count) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 8 * (int64_t)sm_count));
 }
 
-cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
-                       void* scratch, int* err, int sm_count, cudaStream_t s) {
-  const ODims d = oz_dims(n, rp, r, a.form, batch);
+// Everything up to the expansion GEMM (digit slices of the states, the
+// projections and their combine, the slices of [H1 H2], the expansion's
+// slice products in d2); returns d2 and the expansion scales.
+static cudaError_t k3o_front(const ODims& d, const K3Args& a, const void* factors, void* scratch, int* err,
+                             int sm_count, cudaStream_t s, const float** d2_out, const int** sexp_out,
+                             const int** tau2_out) {
   const OFactors F = oz_factor_layout(d);
   const OScratch L = oz_scratch_layout(d);
   const uint8_t* fb = static_cast<const uint8_t*>(factors);
@@ -469,7 +503,7 @@ cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const 
   auto* bh = reinterpret_cast<__nv_bfloat16*>(sb + L.bh);
   auto* tau2 = reinterpret_cast<int*>(sb + L.tau2);
   auto* d2 = reinterpret_cast<float*>(sb + L.d2);
-  const dim3 gs((unsigned)d.bq, (unsigned)((d.nk + 255) / 256)), gc((unsigned)((d.r + 63) / 64), (unsigned)batch);
+  const dim3 gs((unsigned)d.bq, (unsigned)((d.nk + 255) / 256)), gc((unsigned)((d.r + 63) / 64), (unsigned)d.batch);
   const int* spj = reinterpret_cast<const int*>(fb + F.sproj);
   if (d.sp == OZ_S7)
     k3o_slice_states<OZ_S7, OZ_BITS7><<<gs, 256, 0, s>>>(d, a, bst, tau, hmax);
@@ -484,9 +518,40 @@ cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const 
     k3o_combine_proj<OZ_S, OZ_BITS><<<gc, 192, 0, s>>>(d, d1, spj, tau, hh, hl, hmax);
   k3o_slice_h<<<dim3((unsigned)d.bq, (unsigned)((d.rk + 255) / 256)), 256, 0, s>>>(d, a, hh, hl, hmax, bh, tau2);
   e = k3o_gemm_launch(fb + F.aexp, OZ_S * d.me, d.me, bh, d.nc, d.bq, d.rk, OZ_S, d2, err, sm_count, s);
+  *d2_out = d2;
+  *sexp_out = reinterpret_cast<const int*>(fb + F.sexp);
+  *tau2_out = tau2;
+  return e;
+}
+
+cudaError_t k3o_launch(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
+                       void* scratch, int* err, int sm_count, cudaStream_t s) {
+  const ODims d = oz_dims(n, rp, r, a.form, batch);
+  const float* d2;
+  const int *sexp, *tau2;
+  cudaError_t e = k3o_front(d, a, factors, scratch, err, sm_count, s, &d2, &sexp, &tau2);
   if (e != cudaSuccess) return e;
-  k3o_combine_exp<<<oz_flat_blocks((int64_t)batch * d.n, sm_count), 256, 0, s>>>(
-      d, a, d2, reinterpret_cast<const int*>(fb + F.sexp), tau2);
+  k3o_combine_exp<<<oz_flat_blocks((int64_t)batch * d.n, sm_count), 256, 0, s>>>(d, a, d2, sexp, tau2);
+  return cudaGetLastError();
+}
+
+cudaError_t k3o_launch_step(int64_t n, int64_t rp, int64_t r, const K3Args& a, const void* factors, int batch,
+                            void* scratch, int* err, int sm_count, const StepArgs& st, int step_index,
+                            cudaStream_t s) {
+  const ODims d = oz_dims(n, rp, r, a.form, batch);
+  const float* d2;
+  const int *sexp, *tau2;
+  cudaError_t e = k3o_front(d, a, factors, scratch, err, sm_count, s, &d2, &sexp, &tau2);
+  if (e != cudaSuccess) return e;
+  // one element per thread: each carries a 45-pair combine before its step
+  StepArgs st1 = st;
+  st1.ept = 1;
+  st1.nblk = step_mc_blocks(n);
+  const dim3 grid((unsigned)st1.nblk, (unsigned)batch);
+  if (step_plain(st1))
+    k3o_exp_step<true><<<grid, STEP_MC_THREADS, 0, s>>>(d, d2, sexp, tau2, st1, step_index);
+  else
+    k3o_exp_step<false><<<grid, STEP_MC_THREADS, 0, s>>>(d, d2, sexp, tau2, st1, step_index);
   return cudaGetLastError();
 }
 

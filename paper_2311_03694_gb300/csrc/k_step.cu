@@ -62,12 +62,6 @@ __global__ void __launch_bounds__(STEP_MC_THREADS) k_step_diag_mc(const StepArgs
                        [] { __syncthreads(); }, sh, &bad, &last);
 }
 
-// The common case of the diagonal step: identity mass, no linear or forcing
-// term and no energy or invariant asked for.
-static bool step_plain(const StepArgs& a) {
-  return !a.mass_diag && !a.lin_diag && !a.forcing && !a.energy && !a.invariant;
-}
-
 cudaError_t step_diag_mc_launch(const StepArgs& a, int step_index, const K1Plan* k1, const K1Args* k1a, int b0, int nb,
                                 int nbk, cudaStream_t s) {
   dim3 grid((unsigned)a.nblk, (unsigned)nb);

@@ -1,8 +1,9 @@
 """K3O, the batched CP form of FP64 ROMs on the BF16 tensor cores with every
-operand split into 6-bit integer digit slices (Sec. 3.1 eq. tc_ap; skew
+operand split into 7- or 6-bit integer digit slices (Sec. 3.1 eq. tc_ap; skew
 structure Sec. 3.3), against the FP64 oracle: per-evaluation relative l2
 error within the FP64 tolerance (1e-12), agreement with the double-single
-kernels (K3D) on the same factors, stepping with energy and invariant, and
+kernels (K3D) on the same factors, stepping with energy and invariant, the
+fused combine-and-step kernel against the plain evaluation (bitwise), and
 determinism."""
 import numpy as np
 import pytest
@@ -91,6 +92,44 @@ def test_k3o_stepping_energy_invariant():
         assert H[b][6 * n] == steps
         np.testing.assert_allclose(energy.cpu().numpy()[:, b], e_ref, rtol=1e-12)
         assert np.max(np.abs(inv.cpu().numpy()[:, b])) <= 1e-9 * np.max(e_ref)
+    tr.close()
+    rom.close()
+
+
+# Stepping runs the expansion's combine and the step as one kernel; it forms c
+# with the plain evaluation's arithmetic, so after a step the ring's c slot
+# holds the evaluation of the state the step was taken at, bitwise.  One and
+# four elements per thread (40 and 70 trajectories); with and without the
+# energy and invariant (the two step variants).
+@pytest.mark.parametrize("batch", [40, 70])
+@pytest.mark.parametrize("sums", [False, True])
+def test_k3o_fused_step_ring_holds_the_plain_evaluation(batch, sums):
+    grom.build()
+    n, r = 150, 100
+    U, V, W, _, seed = synth.cp_workload(n, r, 1)
+    U0 = synth.initial_condition(n, seed, 0, batch)
+    rom = grom.Rom(n, "cp_skew", "f64", factors=(U, V, W), stiffness=synth.diag_stiffness(n), nu=1e-2, dt=1e-3,
+                   max_batch=batch)
+    rom.set_kernel("tensor")
+    tr = grom.Trajectories(rom, U0)
+
+    def step():
+        if sums:
+            e = torch.empty((1, batch), dtype=torch.float64, device="cuda")
+            tr.step(1, e, torch.empty_like(e))
+        else:
+            tr.step(1)
+        assert tr.status()[0] == 0
+        return tr.get_state()
+
+    # get_state exports newest first: u^l, u^(l-1), u^(l-2), then the c of
+    # each (that of u^l evaluated by the export itself), then l
+    H1 = step()
+    np.testing.assert_array_equal(H1[:, n:2 * n], U0)
+    np.testing.assert_array_equal(H1[:, 4 * n:5 * n], _eval(rom, U0, "tensor"))  # written by the fused step
+    H2 = step()
+    np.testing.assert_array_equal(H2[:, 4 * n:5 * n], _eval(rom, np.ascontiguousarray(H1[:, :n]), "tensor"))
+    assert np.all(H2[:, 6 * n] == 2)
     tr.close()
     rom.close()
 
