@@ -1099,9 +1099,10 @@ static StepArgs step_args(grom_traj* t, double* energy, double* invariant) {
   a.first_bad = t->err + 1;
   a.red = t->red;
   a.cnt = t->cnt;
-  // large batches: four elements per thread, so the per-block FP64
-  // reduction of energy and invariant is paid once per four elements
-  a.ept = t->batch >= 64 ? 4 : 1;
+  // large batches with the energy or invariant asked for: four elements per
+  // thread, so the per-block FP64 reduction is paid once per four elements;
+  // otherwise one (more, shorter blocks)
+  a.ept = t->batch >= 64 && (energy || invariant) ? 4 : 1;
   a.nblk = (int)((r->n + (int64_t)STEP_MC_THREADS * a.ept - 1) / ((int64_t)STEP_MC_THREADS * a.ept));
   a.active = t->active;
   a.active_rw = t->active;
