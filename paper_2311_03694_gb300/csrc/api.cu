@@ -311,7 +311,9 @@ static K2Plan k2_plan_of(const grom_rom* r, int batch) {
 }
 static K2PPlan k2p_plan_of(const grom_rom* r, int batch) {
   const grom_tuning* t = tuned(r, batch);
-  return k2p_plan(r->n, r->k1.lp, batch, r->sm_count, t ? t->tile_m : 0, t ? t->split_b : 0);
+  // single CTAs where no cluster of two fits (the rule and a tuning entry alike)
+  const int ctas = !r->k2p_pairs ? 1 : t ? t->split_b : 0;
+  return k2p_plan(r->n, r->k1.lp, batch, r->sm_count, t ? t->tile_m : 0, ctas);
 }
 static K3TPlan k3t_plan_of(const grom_rom* r, int batch) {
   const grom_tuning* t = tuned(r, batch);
@@ -571,6 +573,7 @@ grom_status grom_create(const grom_desc* d, void* stream, grom_rom** out) {
     }
     if (r->storage == GROM_BF16 && packed) {
       r->k2_ok = k2p_make_tmap(&r->k2_tmap, r->op, n, r->k1.lp);
+      r->k2p_pairs = r->k2_ok && k2p_pairs_supported();
       if (r->k2_ok) {
         // scratch for the largest plan over the batch sizes this ROM accepts
         const size_t need = k2p_scratch_need(n, r->k1.lp, r->max_batch, r->sm_count);

@@ -149,6 +149,9 @@ struct K2PPlan {
 K2PPlan k2p_plan(int64_t n, int64_t lp, int batch, int sm_count, int m_force = 0, int ctas_force = 0);
 bool k2p_tile_m_ok(int batch, int m);
 bool k2p_pair_ok(int64_t lp);
+// Whether clusters of two K2P pair CTAs (at the largest shared memory a plan
+// uses) fit on the current device at all.
+bool k2p_pairs_supported();
 // Scratch of the largest plan over every batch a ROM with max_batch accepts.
 size_t k2_scratch_need(int64_t n, int max_batch, int sm_count);
 size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count);
@@ -449,6 +452,7 @@ struct grom_rom {
   int kernel_choice = 0;             // GROM_KERNEL_* override
   int version = 0;                   // bumped when cached launch graphs become stale
   bool k2_ok = false;                // tensor map built (BF16 full form; K2P's map for the packed layout)
+  bool k2p_pairs = false;            // clusters of two fit on this device: K2P may run on SM pairs
   CUtensorMap k2_tmap;               // TMA descriptor of the stored tensor
   void* k2_tiles = nullptr;          // tile-major copy for K2 (nullable)
   bool no_tile_copy = false;         // grom_desc.no_tile_copy

@@ -39,6 +39,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "grom_internal.h"
 #include "tc.cuh"
@@ -739,14 +740,20 @@ size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count) {
   return need;
 }
 
-// Clusters of two that fit on the device at once with this shared memory
-// (one CTA per SM); 0 if none.
+// Clusters of two that fit on the current device at once with this shared
+// memory; 0 if none.  Every plan's shared memory allows one CTA per SM, so
+// the count is the same for all of them and is kept per device (atomically:
+// ROMs on different threads may launch concurrently).
 static int k2p_pair_clusters(size_t smem) {
-  static int cached[64];
-  static size_t cached_smem[64];
+  static std::atomic<int> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  if (cached[dev] > 0 && cached_smem[dev] == smem) return cached[dev];
+  const int c = cached[dev].load(std::memory_order_relaxed);
+  if (c > 0) return c;
+  if (cudaFuncSetAttribute(k2p_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(2, 1, 1);
   cfg.blockDim = dim3(K2P_THREADS, 1, 1);
@@ -756,10 +763,11 @@ static int k2p_pair_clusters(size_t smem) {
     (void)cudaGetLastError();
     return 0;
   }
-  cached[dev] = nc;
-  cached_smem[dev] = smem;
+  if (nc > 0) cached[dev].store(nc, std::memory_order_relaxed);
   return nc;
 }
+
+bool k2p_pairs_supported() { return k2p_pair_clusters(K2P_SMEM_MAX) > 0; }
 
 cudaError_t k2p_launch(const K2PPlan& p, const CUtensorMap* tmap, const K2Args& a, cudaStream_t s) {
   K2PDev d{};
