@@ -152,6 +152,20 @@ bool k2p_pair_ok(int64_t lp);
 // Whether clusters of two K2P pair CTAs (at the largest shared memory a plan
 // uses) fit on the current device at all.
 bool k2p_pairs_supported();
+// The CTA tile of CTA `rank` (0 leader, 1 peer) of pair tile t2: column tile
+// ct, position block pb (2q + rank), test indices [i0, i1), and the CTA
+// tile's index in the scratch (windows, the finish kernel's numbering).
+__host__ __device__ inline void k2p_pair_coords(int t2, int rank, int col_tiles, int pbs, int m, int64_t n, int& ct,
+                                                int& pb, int64_t& i0, int64_t& i1, int& tile) {
+  ct = t2 % col_tiles;
+  const int rest = t2 / col_tiles;
+  const int halves = pbs >> 1;
+  pb = 2 * (rest % halves) + rank;
+  const int r = rest / halves;
+  i0 = (int64_t)r * m;
+  i1 = i0 + m < n ? i0 + m : n;
+  tile = (r * pbs + pb) * col_tiles + ct;
+}
 // Scratch of the largest plan over every batch a ROM with max_batch accepts.
 size_t k2_scratch_need(int64_t n, int max_batch, int sm_count);
 size_t k2p_scratch_need(int64_t n, int64_t lp, int max_batch, int sm_count);

@@ -334,14 +334,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 1)
 // on it).  Each CTA's epilogue is the single-CTA one for its own block.
 __device__ __forceinline__ void k2p_pair_tile(const K2PDev& p, int t2, uint32_t rank, int& ct, int& pb, int64_t& i0,
                                               int64_t& i1, int& tile) {
-  ct = t2 % p.col_tiles;
-  const int rest = t2 / p.col_tiles;
-  const int halves = p.pbs >> 1;
-  pb = 2 * (rest % halves) + (int)rank;
-  const int r = rest / halves;
-  i0 = (int64_t)r * p.m;
-  i1 = i0 + p.m < p.n ? i0 + p.m : p.n;
-  tile = (r * p.pbs + pb) * p.col_tiles + ct;
+  k2p_pair_coords(t2, (int)rank, p.col_tiles, p.pbs, p.m, p.n, ct, pb, i0, i1, tile);
 }
 
 // Stops both CTAs of the pair: their waits return at the next check.

@@ -80,6 +80,24 @@ static void check_k2p(int64_t n, int64_t lp, int batch, int sm, int m, int ctas,
         "K2P block stride %d (blocks %d, ctas %d)", p.pbs, p.pblks, p.ctas);
   CHECK(p.ctas == 1 || (p.grid % 2 == 0 && p.grid >= 2 && p.grid <= p.tiles && p.tiles % 2 == 0), "K2P pair grid %d",
         p.grid);
+  if (p.ctas == 2 && n <= 1100 && batch % 61 == 1) {
+    // the two CTAs of every pair tile cover each CTA tile exactly once, with
+    // the tile numbering the finish kernel reads and in-range blocks and rows
+    std::vector<char> seen((size_t)p.tiles, 0);
+    bool ok = true;
+    for (int t2 = 0; t2 < p.tiles / 2 && ok; ++t2)
+      for (int rank = 0; rank < 2; ++rank) {
+        int ct, pb, tile;
+        int64_t i0, i1;
+        k2p_pair_coords(t2, rank, p.col_tiles, p.pbs, p.m, n, ct, pb, i0, i1, tile);
+        const int r = (int)(i0 / p.m);
+        ok = ok && tile >= 0 && tile < p.tiles && !seen[(size_t)tile] && pb < p.pbs && ct < p.col_tiles &&
+             i0 < n && i1 > i0 && i1 - i0 <= p.m && tile == (r * p.pbs + pb) * p.col_tiles + ct;
+        if (ok) seen[(size_t)tile] = 1;
+      }
+    for (char c : seen) ok = ok && c;
+    CHECK(ok, "K2P pair tiles n %ld b %d m %d", (long)n, batch, p.m);
+  }
   CHECK(p.smem <= SMEM_MAX, "K2P n %ld b %d m %d smem %zu", (long)n, batch, p.m, p.smem);
   CHECK(p.stages >= 2, "K2P stages %d", p.stages);
   CHECK(tmem_ok(p.tmem_cols) && p.tmem_cols >= 4 * p.btile, "K2P tmem %d", p.tmem_cols);
