@@ -232,11 +232,12 @@ int64_t grom_rom_bytes(const grom_rom* rom);
  * the expansion as double-single FP32 GEMMs (every operand a hi/lo FP32 pair,
  * error-free products and sums) on hi/lo copies of the factors made at
  * create; from N R B >= 2^24 on (N modes, R rank, B trajectories), and with
- * GROM_KERNEL_TENSOR, with K3O: every operand split into nine 6-bit integer
- * digit slices, the slice products on the tcgen05 tensor cores (exact in
- * FP32 for dot products of up to 4096 terms, so N and the expansion's 2R
- * (skew) or R at most 4096) and the slice pairs summed in double-single
- * arithmetic. */
+ * GROM_KERNEL_TENSOR, with K3O: every operand split into integer digit
+ * slices (eight of 7 bits for the projections of ROMs with N <= 1024, else
+ * nine of 6 bits), the slice products on the tcgen05 tensor cores (exact in
+ * FP32 for dot products of up to 1024 and 4096 terms respectively, so N and
+ * the expansion's 2R (skew) or R at most 4096) and the slice pairs summed in
+ * double-single arithmetic. */
 #define GROM_KERNEL_AUTO 0
 #define GROM_KERNEL_STREAM 1 /* K1: SIMT streaming kernel, up to 8 trajectories per pass, one
                                 launch per step (no persistent stepper); CP forms: the SIMT
@@ -247,6 +248,8 @@ int64_t grom_rom_bytes(const grom_rom* rom);
                                 form, one tcgen05 GEMM D_i = P_i^T U^T per test index i over
                                 the stored half, then c_i += D_i u_k and c_k -= D_i u_i for
                                 every stored pair (i, k); half the bytes and MMA work of K2.
+                                Rows of more than 128 stored positions run one 256-row MMA
+                                over each pair of SMs (a cluster of two CTAs, cta_group::2).
                                 CP forms, K3T: the projections [B C]^T X (skew: [V W U]^T X)
                                 and the expansion A Z (skew: [U, -W] Z) of the batch as two
                                 tcgen05 GEMMs (Sec. 3.1, eq. tc_ap; Sec. 3.3).  FP64 CP forms
