@@ -36,6 +36,10 @@
 //     window is written out once per tile.
 // A finish kernel adds, for every (k, b), the direct partials and subtracts
 // the window rows that cover k, in a fixed order (deterministic), in FP64.
+// Where a stored row has two or more position blocks the plans run the
+// SM-pair variant (k2p_pair_kernel, below): one 256-row MMA over a cluster of
+// two CTAs, each with its own block and half of the states operand; the same
+// epilogue, finish and bits.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
